@@ -1,0 +1,76 @@
+"""Entropy phase autofocus and its analytic adjoint, in FP64 (oracle; test infrastructure only).
+
+Model.  rc is range-compressed data [n_az][n_rg]; a per-pulse phase
+correction phi[n_az] gives v[n, r] = rc[n, r] exp(-j phi[n]).  The image is
+I = A v, with A the azimuth compression of ``oracle.sar`` (per range column,
+IDFT(DFT(.) . Ha)).  With q = |I|^2, S = sum q and p = q / S, the image
+entropy is
+
+    E = -sum p ln p = ln S - (1/S) sum q ln q        (0 ln 0 = 0).
+
+Gradient (derived here; the paper has no autofocus section):
+
+    dE/dq        = -(ln p + E) / S
+    G = dE/dI*   = -(ln p + E) / S * I               (G = 0 where q = 0)
+    dE/dv*       = A^H G,  A^H = IDFT(DFT(.) . conj(Ha)) per column
+    dE/dphi[n]   = 2 sum_r Im( conj((A^H G)[n, r]) * v[n, r] )
+
+the last line because dv/dphi = -j v and dE = 2 Re sum conj(dE/dv*) dv.
+Adding a constant to phi leaves |I| unchanged, so sum_n dE/dphi[n] = 0.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from . import sar as _sar
+
+
+def corrected(rc: np.ndarray, phi: np.ndarray) -> np.ndarray:
+    return np.asarray(rc, dtype=np.complex128) * np.exp(-1j * np.asarray(phi, dtype=np.float64))[:, None]
+
+
+def image(rc: np.ndarray, phi: np.ndarray, ha: np.ndarray) -> np.ndarray:
+    return _sar.azimuth_compress(corrected(rc, phi), ha)
+
+
+def entropy_of(img: np.ndarray) -> float:
+    q = np.abs(np.asarray(img, dtype=np.complex128)) ** 2
+    s = float(np.sum(q))
+    pos = q > 0
+    qlq = float(np.sum(q[pos] * np.log(q[pos])))
+    return float(np.log(s) - qlq / s)
+
+
+def entropy(rc: np.ndarray, phi: np.ndarray, ha: np.ndarray) -> float:
+    return entropy_of(image(rc, phi, ha))
+
+
+def entropy_and_grad(rc: np.ndarray, phi: np.ndarray, ha: np.ndarray):
+    """(E, dE/dphi) by the analytic adjoint above."""
+    v = corrected(rc, phi)
+    img = _sar.azimuth_compress(v, ha)
+    q = np.abs(img) ** 2
+    s = float(np.sum(q))
+    pos = q > 0
+    lnp = np.zeros_like(q)
+    lnp[pos] = np.log(q[pos] / s)
+    e = float(-np.sum(q[pos] / s * lnp[pos]))
+    g = np.where(pos, -(lnp + e) / s, 0.0) * img
+    back = _sar.azimuth_compress(g, np.conj(ha))
+    grad = 2.0 * np.sum(np.imag(np.conj(back) * v), axis=1)
+    return e, grad
+
+
+def central_difference(rc: np.ndarray, phi: np.ndarray, ha: np.ndarray, pulses, h: float = 1e-4):
+    """FP64 central finite differences of E with respect to phi at the given pulses."""
+    phi = np.asarray(phi, dtype=np.float64)
+    out = []
+    for n in pulses:
+        p = phi.copy()
+        p[n] += h
+        ep = entropy(rc, p, ha)
+        p[n] -= 2 * h
+        em = entropy(rc, p, ha)
+        out.append((ep - em) / (2 * h))
+    return np.asarray(out)

@@ -1,0 +1,76 @@
+"""Storage-format rounding, written from the formats' definitions (oracle).
+
+TEST INFRASTRUCTURE ONLY.
+
+* binary16 (IEEE 754 half): 1 sign, 5 exponent (bias 15), 10 fraction bits;
+  largest finite 65504; values at or beyond 65520 round to infinity.
+* OCP FP8 E4M3: 1 sign, 4 exponent (bias 7), 3 mantissa bits; no infinity,
+  largest finite 448, smallest subnormal 2^-9.
+* OCP FP8 E5M2: 1 sign, 5 exponent (bias 15), 2 mantissa bits; largest finite
+  57344, smallest subnormal 2^-16.
+
+All conversions round to nearest, ties to even.  The FP8 conversions are
+"satfinite": a finite value beyond the largest finite magnitude becomes that
+magnitude with its sign, and NaN stays NaN (Section VII: FP8 storage, FP32
+or wider compute).
+
+``round_binary16`` uses numpy's float16 cast, which is IEEE round-to-nearest-
+even; the tests pin it against hand-checked edge values (65504, 65519.99,
+65520, subnormals, ties).  The FP8 rounders are written out from the
+definition: pick the binade of |x| (never below the smallest normal binade),
+round |x| / quantum to the nearest even integer, scale back, then clamp.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+
+def round_binary16(x: np.ndarray) -> np.ndarray:
+    """Round real or complex values to binary16 and return them as float64/complex128."""
+    x = np.asarray(x)
+    with np.errstate(over="ignore"):
+        if np.iscomplexobj(x):
+            return (x.real.astype(np.float16).astype(np.float64)
+                    + 1j * x.imag.astype(np.float16).astype(np.float64))
+        return x.astype(np.float16).astype(np.float64)
+
+
+def round_binary32(x: np.ndarray) -> np.ndarray:
+    x = np.asarray(x)
+    if np.iscomplexobj(x):
+        return (x.real.astype(np.float32).astype(np.float64)
+                + 1j * x.imag.astype(np.float32).astype(np.float64))
+    return x.astype(np.float32).astype(np.float64)
+
+
+FP8_FORMATS = {
+    # name: (mantissa bits, minimum normal exponent, largest finite)
+    "e4m3": (3, -6, 448.0),
+    "e5m2": (2, -14, 57344.0),
+}
+
+
+def _round_fp8_real(x: np.ndarray, fmt: str) -> np.ndarray:
+    mbits, emin, vmax = FP8_FORMATS[fmt]
+    x = np.asarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    nan = np.isnan(x)
+    a = np.abs(np.where(nan, 0.0, x))
+    with np.errstate(divide="ignore"):
+        e = np.floor(np.log2(np.where(a > 0, a, 1.0)))
+    e = np.maximum(e, emin)
+    quantum = np.exp2(e - mbits)
+    q = np.round(a / quantum) * quantum          # np.round is ties-to-even
+    q = np.minimum(q, vmax)                       # satfinite
+    out[:] = np.copysign(q, x)
+    out[nan] = np.nan
+    return out
+
+
+def round_fp8(x: np.ndarray, fmt: str) -> np.ndarray:
+    """Round to OCP FP8 ('e4m3' or 'e5m2'), RN-even, satfinite; returns float64/complex128."""
+    x = np.asarray(x)
+    if np.iscomplexobj(x):
+        return _round_fp8_real(x.real, fmt) + 1j * _round_fp8_real(x.imag, fmt)
+    return _round_fp8_real(x, fmt)
