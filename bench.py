@@ -1,0 +1,472 @@
+#!/usr/bin/env python3
+"""Benchmark: batched FP16 block-floating-point FFT GFLOPS and HBM roofline on GB300.
+
+Workload (the Table II transform widened past L2): complex transforms of
+length 4096, FP16-BFP storage (half2), batch 65536 (1 GiB in, 1 GiB out, so
+no L2 flush is needed between steps).  One step = forward FFT + inverse FFT
+with the 1/N block shift (two launches of the row kernel), GFLOPS =
+2 * 5 N log2 N * batch / t (Section V's convention).
+
+Beside the headline line the JSON carries: the same workload in FP32
+storage, the exact Table II size (batch 256, L2 flushed between steps), SAR
+range compression (1024 x 4096) and the full 4096 x 4096 range-Doppler image,
+the FP16 SQNR against the FP32 path, the roofline of the dominant kernel,
+the oracle timed on the host cores, an end-to-end number through the C ABI
+with host buffers, and the SM clocks sampled during the timed region.
+
+--impl reference times the FP64 oracle (test infrastructure) on the host
+cores on a bounded sample of the same workload and prints the same line.
+
+Multi-GPU: one process per GPU (torchrun); every rank runs the same batch
+(weak scaling, replicas: the transforms are independent, no collective).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 4096
+BATCH = 65536
+LOG2N = 12
+FLOPS_PER_TRANSFORM = 5 * N * LOG2N
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2605_28451_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(kernel_tag: str):
+    """DRAM bytes per launch recorded by an ncu capture in profiles/, or None
+    when no capture exists or the kernel sources changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    want = _kernel_source_hash()
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == kernel_tag and parts[1] == want:
+            return float(parts[3])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.1)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if "Active" in s[2 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def _events_time(fn, steps, stream, per_launch=None):
+    """Run fn() `steps` times between events; returns total ms."""
+    import torch
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2605_28451_gb300 import bfpfft as B
+    from paper_2605_28451_gb300 import build as _b
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _b.build()
+    B.lib()
+    stream = torch.cuda.current_stream()
+    batch = args.batch
+
+    # ---- inputs resident in HBM (seeded, synthetic: re, im ~ N(0, 1)) -------------
+    g = torch.Generator(device=dev).manual_seed(1000 + rank)
+    x16 = torch.randn((batch, N, 2), device=dev, generator=g).to(torch.float16)
+    y16 = torch.empty_like(x16)
+    z16 = torch.empty_like(x16)
+    fwd16 = B.bfpfft_plan_create(N, batch, B.F16_BFP, B.FORWARD)
+    inv16 = B.bfpfft_plan_create(N, batch, B.F16_BFP, B.INVERSE)
+
+    def step16(evs=None):
+        if evs is not None:
+            evs[0].record(stream)
+        B.bfpfft_exec(fwd16, x16, y16, stream)
+        if evs is not None:
+            evs[1].record(stream)
+        B.bfpfft_exec(inv16, y16, z16, stream)
+        if evs is not None:
+            evs[2].record(stream)
+
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    with ClockSampler(local) as clocks:
+        for _ in range(args.warmup):
+            step16()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            step16(events[i])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in events]
+    inv_ms = [e[1].elapsed_time(e[2]) for e in events]
+    t_ms = t_start.elapsed_time(t_end) / args.steps
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    flops_step = 2.0 * FLOPS_PER_TRANSFORM * batch
+    value = world * flops_step / (t_ms * 1e-3) / 1e9
+
+    # ---- SQNR of the FP16 path against the FP32 path on the same input ----------
+    x32 = torch.view_as_complex(x16[:256].float().contiguous())
+    y32 = torch.empty_like(x32)
+    p32 = B.bfpfft_plan_create(N, 256, B.F32, B.FORWARD)
+    B.bfpfft_exec(p32, x32, y32, stream)
+    y16c = torch.view_as_complex(y16[:256].float().contiguous()).to(torch.complex128)
+    r = y32.to(torch.complex128)
+    alpha = (torch.vdot(y16c.flatten(), r.flatten()).real / torch.vdot(y16c.flatten(), y16c.flatten()).real)
+    sqnr16 = float(10 * torch.log10((r.abs() ** 2).sum() / ((r - alpha * y16c).abs() ** 2).sum()))
+
+    # ---- FP32 storage on the same workload ---------------------------------------
+    xf = torch.view_as_complex(x16.float().contiguous())
+    del x32, y32
+    yf = torch.empty_like(xf)
+    zf = torch.empty_like(xf)
+    fwd32 = B.bfpfft_plan_create(N, batch, B.F32, B.FORWARD)
+    inv32 = B.bfpfft_plan_create(N, batch, B.F32, B.INVERSE)
+
+    def step32():
+        B.bfpfft_exec(fwd32, xf, yf, stream)
+        B.bfpfft_exec(inv32, yf, zf, stream)
+
+    for _ in range(3):
+        step32()
+    k32 = max(3, args.steps // 2)
+    t32 = _events_time(step32, k32, stream) / k32
+    gflops32 = flops_step / (t32 * 1e-3) / 1e9
+    del xf, yf, zf
+
+    # ---- Table II size exactly: N = 4096, batch 256, L2 flushed between steps ------
+    small_x = x16[:256].contiguous()
+    small_y = torch.empty_like(small_x)
+    small_z = torch.empty_like(small_x)
+    pf = B.bfpfft_plan_create(N, 256, B.F16_BFP, B.FORWARD)
+    pi = B.bfpfft_plan_create(N, 256, B.F16_BFP, B.INVERSE)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    small = []
+    for i in range(30 + 5):
+        flush.fill_(i & 0xFF)
+        e0.record(stream)
+        B.bfpfft_exec(pf, small_x, small_y, stream)
+        B.bfpfft_exec(pi, small_y, small_z, stream)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= 5:
+            small.append(e0.elapsed_time(e1))
+    t_small = statistics.median(small)
+    gflops_small = 2.0 * FLOPS_PER_TRANSFORM * 256 / (t_small * 1e-3) / 1e9
+    del flush
+
+    # ---- SAR: range compression 1024 x 4096 and the 4096 x 4096 image ---------------
+    sar = _bench_sar(B, torch, dev, stream)
+
+    # ---- end to end through the C ABI with host buffers ---------------------------
+    e2e = _bench_e2e(B, torch, dev, stream, x16, fwd16, inv16, flops_step, args)
+
+    # ---- roofline of the dominant kernel (forward FP16 rows) -------------------------
+    peak, peak_kind = _peaks()
+    alg_bytes = 8.0 * N * batch                          # one FP16 read + one FP16 write per point
+    fwd_avg = sum(fwd_ms) / len(fwd_ms)
+    inv_avg = sum(inv_ms) / len(inv_ms)
+    achieved = alg_bytes / (fwd_avg * 1e-3) / 1e9
+    traffic = _profiled_traffic("fft_rows_f16_fwd_4096")
+
+    if rank == 0:
+        cpu = _cpu_baseline(seconds=args.cpu_seconds) if world == 1 else None
+        line = {
+            "metric": "batched FFT GFLOPS (5 N log2 N per transform), FP16-BFP storage, N=4096",
+            "value": round(value, 1),
+            "unit": "GFLOPS",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(t_ms, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f16 storage, f32 arithmetic",
+            "data": "synthetic (re, im ~ N(0,1), seeded)",
+            "config": {
+                "workload": f"forward + 1/N-shifted inverse FFT, N={N}, batch {batch} per GPU, FP16-BFP (half2)",
+                "l2": "inputs 1 GiB > L2, no flush needed",
+                "parallelism": f"replicas x{world}",
+            },
+            "roofline": {
+                "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "fft_rows_kernel<4096, half2, half2, forward>",
+                "bytes_per_launch": alg_bytes, "launch_ms": round(fwd_avg, 5), "peak_source": peak_kind,
+                "frac_of_8tbs_nominal": round(achieved / 8000.0, 4),
+            },
+            "fp16_sqnr_vs_fp32_db": round(sqnr16, 2),
+            "fp32_storage_gflops": round(gflops32, 1),
+            "fp16_over_fp32": round(value / world / gflops32, 3),
+            "inverse_launch_ms": round(inv_avg, 5),
+            "table2_batch256_l2_flushed": {"gflops": round(gflops_small, 1), "ms_median": round(t_small, 5)},
+            "sar": sar,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks.summary(),
+            "gpu_launches": 2 * args.steps,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _bench_sar(B, torch, dev, stream):
+    from paper_2605_28451_gb300 import synth
+    out = {}
+    for name, n_az, n_rg in (("range_compress_1024x4096", 1024, 4096), ("image_4096x4096", 4096, 4096)):
+        sc = synth.point_target_scene(n_az, n_rg)
+        raw = torch.from_numpy(sc.raw.astype("complex64")).to(dev)
+        hr = torch.empty(n_rg, dtype=torch.complex64, device=dev)
+        ha = torch.empty(n_az, dtype=torch.complex64, device=dev)
+        B.sar_make_filter(torch.from_numpy(sc.ref_range.astype("complex64")).to(dev), n_rg, False, hr, stream)
+        B.sar_make_filter(torch.from_numpy(sc.ref_azimuth.astype("complex64")).to(dev), n_az, True, ha, stream)
+        rc = torch.empty((n_rg, n_az, 2), dtype=torch.float16, device=dev)
+        img = torch.empty((n_az, n_rg, 2), dtype=torch.float16, device=dev)
+        flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+        full = name.startswith("image")
+
+        def step():
+            B.sar_range_compress(raw, B.F32, rc, B.F16_BFP, hr, n_az, n_rg, True, stream)
+            if full:
+                B.sar_azimuth_compress(rc, B.F16_BFP, 1, img, B.F16_BFP, ha, n_az, n_rg, stream)
+
+        for _ in range(3):
+            step()
+        ts = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for i in range(20):
+            flush.fill_(i & 0xFF)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        t = statistics.median(ts)
+        transforms = 2 * n_az + (2 * n_rg if full else 0)
+        flops = transforms * 5 * 4096 * 12
+        bytes_ = n_az * n_rg * (12 + (8 if full else 0))
+        out[name] = {"ms_median_l2_flushed": round(t, 4), "gflops": round(flops / (t * 1e-3) / 1e9, 1),
+                     "alg_gbs": round(bytes_ / (t * 1e-3) / 1e9, 1), "dtype": "complex64 in, FP16-BFP out",
+                     "naive_has_nonfinite": None}
+        if not full:
+            naive = torch.empty((n_az, n_rg, 2), dtype=torch.float16, device=dev)
+            B.sar_range_compress(raw, B.F32, naive, B.F16_NAIVE, hr, n_az, n_rg, False, stream)
+            torch.cuda.synchronize()
+            out[name]["naive_has_nonfinite"] = bool((~torch.isfinite(naive)).any().item())
+        del raw, rc, img, flush
+    return out
+
+
+def _bench_e2e(B, torch, dev, stream, x16, fwd, inv, flops_step, args):
+    """Same metric through the C ABI with pinned host input and output buffers;
+    the host->device and device->host copies are inside the timed region."""
+    host_in = torch.empty(x16.shape, dtype=x16.dtype, pin_memory=True)
+    host_in.copy_(x16)
+    host_out = torch.empty_like(host_in, pin_memory=True)
+    d_in = torch.empty_like(x16)
+    d_mid = torch.empty_like(x16)
+    d_out = torch.empty_like(x16)
+
+    def step():
+        d_in.copy_(host_in, non_blocking=True)
+        B.bfpfft_exec(fwd, d_in, d_mid, stream)
+        B.bfpfft_exec(inv, d_mid, d_out, stream)
+        host_out.copy_(d_out, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    k = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(k):
+        step()
+    torch.cuda.synchronize()
+    t = (time.perf_counter() - t0) / k
+    nbytes = x16.numel() * x16.element_size()
+    return {"value": round(flops_step / t / 1e9, 1), "unit": "GFLOPS", "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "ms_per_step": round(t * 1e3, 3)}
+
+
+def _cpu_baseline(seconds: float = 10.0):
+    """The FP64 oracle as it stands (numpy, one thread), timed on a bounded
+    sample of the workload: forward + inverse of as many N = 4096 lines as
+    fit in `seconds`, starting from 8 lines and doubling."""
+    import numpy as np
+
+    from oracle import fft as F
+    from paper_2605_28451_gb300 import synth
+    lines = 8
+    while True:
+        x = synth.complex_gaussian(lines, N, seed=0)
+        t0 = time.perf_counter()
+        F.ifft(F.fft(x))
+        dt = time.perf_counter() - t0
+        if dt >= seconds / 4 or lines >= 4096:
+            break
+        lines *= 2
+    reps = max(1, int(seconds / max(dt, 1e-3)))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        F.ifft(F.fft(x))
+    dt = (time.perf_counter() - t0) / reps
+    gflops = 2.0 * FLOPS_PER_TRANSFORM * lines / dt / 1e9
+    del np
+    return {"value": round(gflops, 3), "unit": "GFLOPS", "cores": 1, "kind": "oracle",
+            "sample": f"{lines} lines of N={N}, forward + inverse, {reps} reps, FP64 numpy radix-2"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+
+    from oracle import fft as F
+    from paper_2605_28451_gb300 import synth
+    lines = args.ref_lines
+    x = synth.complex_gaussian(lines, N, seed=0)
+    for _ in range(args.warmup):
+        F.ifft(F.fft(x))
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        F.ifft(F.fft(x))
+        ts.append(time.perf_counter() - t0)
+    t = sum(ts) / len(ts)
+    value = 2.0 * FLOPS_PER_TRANSFORM * lines / t / 1e9
+    sample = f"{lines} lines of N={N} per step (of the {BATCH}-line workload), forward + inverse, FP64 numpy radix-2"
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "batched FFT GFLOPS (5 N log2 N per transform), FP16-BFP storage, N=4096",
+        "value": round(value, 4), "unit": "GFLOPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (re, im ~ N(0,1), seeded)",
+        "config": {"workload": f"forward + 1/N-shifted inverse FFT, N={N}, batch {BATCH} per GPU, FP16-BFP (half2)",
+                   "parallelism": "host cores"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GFLOPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "GFLOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-lines", type=int, default=64)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

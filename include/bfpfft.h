@@ -1,0 +1,166 @@
+/*
+ * bfpfft -- block-floating-point FP16 FFT and SAR range-Doppler compression
+ * for NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * Paper: "Range, Not Precision: Block-Floating-Point Half-Precision FFT and
+ * SAR Imaging" (arXiv 2605.28451).  Section references below are to it.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every call returns an int status (enum bfpfft_status); no exception or
+ *   longjmp crosses this boundary.  bfpfft_error_string() names a status.
+ * - Complex data is interleaved (re, im), row-major: a batch of lines of n
+ *   points each, consecutive lines n points apart unless a call says otherwise.
+ *   Element types by dtype: BFPFFT_F32 -> float2 (8 B / point);
+ *   BFPFFT_F16_BFP and BFPFFT_F16_NAIVE -> __half2 (4 B / point);
+ *   BFPFFT_E4M3_BFP and BFPFFT_E5M2_BFP -> two FP8 bytes (2 B / point).
+ * - Device pointers are owned by the caller (e.g. torch tensors) and must be
+ *   16-byte aligned; a misaligned pointer returns BFPFFT_ERR_MISALIGNED.
+ *   In-place execution (in == out) is allowed wherever input and output have
+ *   the same element type and layout.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Exec calls only enqueue work; they return after the launch, and a launch
+ *   failure is reported as BFPFFT_ERR_CUDA.
+ * - Arithmetic is FP32 in registers and shared memory for every dtype; the
+ *   dtype fixes only the storage format in HBM (Section VI's "FP16 storage /
+ *   FP32 compute" mode).  Twiddle tables are generated on the GPU in FP64.
+ * - Supported lengths: powers of two with 16 <= n <= 16384 for the row
+ *   transforms; anything else returns BFPFFT_ERR_UNSUPPORTED.
+ */
+#ifndef BFPFFT_H_
+#define BFPFFT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum bfpfft_status {
+  BFPFFT_OK = 0,
+  BFPFFT_ERR_INVALID_ARG = 1,   /* null pointer, negative size, bad enum value */
+  BFPFFT_ERR_UNSUPPORTED = 2,   /* length / dtype / direction combination not provided */
+  BFPFFT_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+  BFPFFT_ERR_OOM = 4,           /* device allocation for a plan failed */
+  BFPFFT_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired */
+  BFPFFT_ERR_NONFINITE = 6,     /* informational: output holds Inf or NaN */
+  BFPFFT_ERR_MISALIGNED = 7     /* a buffer is not 16-byte aligned */
+};
+
+enum bfpfft_dtype {
+  BFPFFT_F32 = 0,        /* FP32 storage: the comparison path (Section V, Table II) */
+  BFPFFT_F16_BFP = 1,    /* FP16 storage with the fixed 1/N block shift (Eq. 1) */
+  BFPFFT_F16_NAIVE = 2,  /* FP16 storage without the shift (Section III-B's failing path) */
+  BFPFFT_E4M3_BFP = 3,   /* FP8 E4M3 storage, static block exponents (Section VII) */
+  BFPFFT_E5M2_BFP = 4    /* FP8 E5M2 storage, static block exponents (Section VII) */
+};
+
+enum bfpfft_direction {
+  BFPFFT_FORWARD = -1,   /* X[k] = sum_n x[n] exp(-2 pi i n k / N), unnormalised */
+  BFPFFT_INVERSE = +1    /* x[n] = (1/N) sum_k X[k] exp(+2 pi i n k / N) */
+};
+
+typedef struct bfpfft_plan_s* bfpfft_plan;
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int bfpfft_version(void);
+
+/* Static text for a status code; never NULL. */
+const char* bfpfft_error_string(int status);
+
+/*
+ * Create a plan for `batch` transforms of length `n` (Section V: batched
+ * radix-16 Stockham transforms, one line per thread group, all passes on
+ * chip).  direction = BFPFFT_INVERSE computes the normalised inverse DFT as
+ * conj(FFT(conj(z) * 1/N)): the 1/N is the fixed block shift folded into the
+ * pre-inverse conjugate (Section IV-A, Eq. 1).  With BFPFFT_F16_NAIVE the
+ * inverse instead stores the unnormalised result to FP16 and then scales by
+ * 1/N, which overflows to Inf once |N y| > 65504 (Section III-B).
+ * FP8 plans carry static block exponents, see bfpfft_plan_scale_exp().
+ * batch may be 0 (exec is then a no-op).  The plan allocates its twiddle
+ * table on the current device; it must be executed on that device.
+ * Errors: INVALID_ARG (out NULL, batch < 0, unknown dtype or direction),
+ * UNSUPPORTED (n not a power of two in [16, 16384]), OOM, CUDA.
+ * On error *out is set to NULL.
+ */
+int bfpfft_plan_create(bfpfft_plan* out, int64_t n, int64_t batch, int dtype, int direction);
+
+/*
+ * Enqueue the planned transforms on `stream`: in and out are device buffers of
+ * batch * n points in the plan's dtype.  in == out is allowed.
+ * Errors: INVALID_ARG (NULL plan or buffer), MISALIGNED, CUDA.
+ */
+int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream);
+
+/* Free a plan's device resources (synchronous).  NULL is accepted. */
+int bfpfft_plan_destroy(bfpfft_plan plan);
+
+/*
+ * Static block exponents of a plan: the true value of a stored input point is
+ * stored * 2^in_exp and that of a stored output point is stored * 2^out_exp.
+ * FP8 forward plans store the spectrum with out_exp = ceil(log2(n) / 2) (the
+ * unitary sqrt(N) growth of noise-like data); FP8 inverse plans expect that
+ * exponent on input and produce out_exp = 0.  Both are 0 for FP32 and FP16.
+ */
+int bfpfft_plan_scale_exp(bfpfft_plan plan, int* in_exp, int* out_exp);
+
+
+/* ---------------------------------------------------------------------------
+ * SAR range-Doppler compression (Section VI, Fig. 1).
+ *
+ * Matched-filter compression y = IDFT(DFT(x) . H) of every line, computed as
+ * conj(DFT(conj(DFT(x) . H) * 1/N)): forward transform, filter multiply and
+ * the 1/N block shift folded into the conjugate (Eq. 1), then the inverse,
+ * all in one kernel with the line held on chip.  FP32 arithmetic; the dtype
+ * arguments fix only the storage formats.  With an F16_NAIVE output the shift
+ * is dropped: the unnormalised inverse (O(N^2) for an unnormalised filter,
+ * Section III-B) is stored to FP16 before the 1/N, and overflows to Inf.
+ * Supported line lengths: powers of two in [256, 16384].
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Filter spectrum from a time-domain reference line: h_out = conj(DFT(ref)),
+ * divided by max_k |DFT(ref)[k]| when peak_normalise != 0 (|H| <= 1, the
+ * filter of Section III-B's magnitude argument).  ref and h_out are float2[n]
+ * device buffers; ref is the transmitted pulse placed circularly centred at
+ * index 0.  Errors: INVALID_ARG, MISALIGNED, UNSUPPORTED (n), CUDA.
+ * The first call for a given device and length allocates that length's
+ * twiddle table; make it before any stream capture.
+ */
+int sar_make_filter(const void* ref, int64_t n, int peak_normalise, void* h_out, void* stream);
+
+/*
+ * Range compression: for each of the n_az azimuth lines raw[eta][0..n_rg),
+ * out = IDFT(DFT(raw[eta]) . Hr).
+ *   raw        [n_az][n_rg], raw_dtype BFPFFT_F32 (complex64) or BFPFFT_F16_BFP (half2)
+ *   out        out_dtype BFPFFT_F32, BFPFFT_F16_BFP or BFPFFT_F16_NAIVE;
+ *              transpose_out = 0: [n_az][n_rg];  transpose_out = 1: [n_rg][n_az]
+ *              (the corner turn is done on chip by a thread-block cluster)
+ *   hr         float2[n_rg], the range filter spectrum
+ * n_az = 0 is a no-op.  out must not overlap raw when transpose_out = 1.
+ * Errors: INVALID_ARG, MISALIGNED, UNSUPPORTED (n_rg or dtypes), CUDA.
+ */
+int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype, const void* hr,
+                       int64_t n_az, int64_t n_rg, int transpose_out, void* stream);
+
+/*
+ * Azimuth compression: for each of the n_rg range columns,
+ * img[:, r] = IDFT(DFT(rc[:, r]) . Ha), lines of length n_az.
+ *   rc         rc_dtype BFPFFT_F32 or BFPFFT_F16_BFP;
+ *              rc_layout = 0: [n_az][n_rg] (columns are gathered on chip);
+ *              rc_layout = 1: [n_rg][n_az] (as written by sar_range_compress
+ *              with transpose_out = 1)
+ *   img        [n_az][n_rg], img_dtype BFPFFT_F32, BFPFFT_F16_BFP or BFPFFT_F16_NAIVE
+ *   ha         float2[n_az], the azimuth filter spectrum
+ * n_rg = 0 is a no-op.  img must not overlap rc.
+ * Errors: INVALID_ARG, MISALIGNED, UNSUPPORTED (n_az or dtypes), CUDA.
+ */
+int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img, int img_dtype,
+                         const void* ha, int64_t n_az, int64_t n_rg, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFPFFT_H_ */

@@ -1,0 +1,169 @@
+"""Thin ctypes binding of include/bfpfft.h.
+
+Argument marshalling only: every function here converts torch tensors to raw
+device pointers and the current CUDA stream, calls the C entry point of the
+same name, and turns a non-zero status into ``BfpfftError``.  There is no
+fallback: if the compiled library is missing, the first call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+# Status codes (enum bfpfft_status).
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_UNSUPPORTED = 2
+ERR_CUDA = 3
+ERR_OOM = 4
+ERR_TIMEOUT = 5
+ERR_NONFINITE = 6
+ERR_MISALIGNED = 7
+
+# Storage dtypes (enum bfpfft_dtype).
+F32 = 0
+F16_BFP = 1
+F16_NAIVE = 2
+E4M3_BFP = 3
+E5M2_BFP = 4
+
+FORWARD = -1
+INVERSE = +1
+
+BYTES_PER_POINT = {F32: 8, F16_BFP: 4, F16_NAIVE: 4, E4M3_BFP: 2, E5M2_BFP: 2}
+
+_c_int64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+
+# name -> (restype, argtypes); every exported symbol of include/bfpfft.h.
+SIGNATURES = {
+    "bfpfft_version": (ctypes.c_int, []),
+    "bfpfft_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "bfpfft_plan_create": (ctypes.c_int, [ctypes.POINTER(_vp), _c_int64, _c_int64, ctypes.c_int, ctypes.c_int]),
+    "bfpfft_exec": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "bfpfft_plan_destroy": (ctypes.c_int, [_vp]),
+    "bfpfft_plan_scale_exp": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "sar_make_filter": (ctypes.c_int, [_vp, _c_int64, ctypes.c_int, _vp, _vp]),
+    "sar_range_compress": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _c_int64, _c_int64,
+                                          ctypes.c_int, _vp]),
+    "sar_azimuth_compress": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _c_int64,
+                                            _c_int64, _vp]),
+}
+
+_lib = None
+
+
+class BfpfftError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({error_string(status)})")
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib():
+    """Load libbfpfft.so (built in-tree by build.build()); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_2605_28451_gb300.build.build(); "
+                               "there is no CPU fallback")
+        handle = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def error_string(status: int) -> str:
+    try:
+        return lib().bfpfft_error_string(int(status)).decode()
+    except Exception:  # library not loadable: still give a readable message
+        return "unknown"
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise BfpfftError(status, where)
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def bfpfft_version() -> int:
+    return lib().bfpfft_version()
+
+
+class Plan:
+    """Owning handle of a bfpfft_plan (destroyed with the object)."""
+
+    def __init__(self, handle: int, n: int, batch: int, dtype: int, direction: int):
+        self.handle, self.n, self.batch, self.dtype, self.direction = handle, n, batch, dtype, direction
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.bfpfft_plan_destroy(h)
+            self.handle = None
+
+
+def bfpfft_plan_create(n: int, batch: int, dtype: int, direction: int) -> Plan:
+    h = _vp()
+    _check(lib().bfpfft_plan_create(ctypes.byref(h), int(n), int(batch), int(dtype), int(direction)),
+           "bfpfft_plan_create")
+    return Plan(h.value, n, batch, dtype, direction)
+
+
+def bfpfft_exec(plan: Plan, inp, out, stream=None):
+    _check(lib().bfpfft_exec(plan.handle, _ptr(inp), _ptr(out), _stream(stream)), "bfpfft_exec")
+
+
+def bfpfft_plan_destroy(plan: Plan):
+    if plan.handle:
+        _check(lib().bfpfft_plan_destroy(plan.handle), "bfpfft_plan_destroy")
+        plan.handle = None
+
+
+def bfpfft_plan_scale_exp(plan: Plan):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib().bfpfft_plan_scale_exp(plan.handle, ctypes.byref(a), ctypes.byref(b)), "bfpfft_plan_scale_exp")
+    return a.value, b.value
+
+
+def sar_make_filter(ref, n: int, peak_normalise: bool, h_out, stream=None):
+    _check(lib().sar_make_filter(_ptr(ref), int(n), int(bool(peak_normalise)), _ptr(h_out), _stream(stream)),
+           "sar_make_filter")
+
+
+def sar_range_compress(raw, raw_dtype: int, out, out_dtype: int, hr, n_az: int, n_rg: int,
+                       transpose_out: bool = False, stream=None):
+    _check(lib().sar_range_compress(_ptr(raw), int(raw_dtype), _ptr(out), int(out_dtype), _ptr(hr), int(n_az),
+                                    int(n_rg), int(bool(transpose_out)), _stream(stream)), "sar_range_compress")
+
+
+def sar_azimuth_compress(rc, rc_dtype: int, rc_layout: int, img, img_dtype: int, ha, n_az: int, n_rg: int,
+                         stream=None):
+    _check(lib().sar_azimuth_compress(_ptr(rc), int(rc_dtype), int(rc_layout), _ptr(img), int(img_dtype), _ptr(ha),
+                                      int(n_az), int(n_rg), _stream(stream)), "sar_azimuth_compress")

@@ -1,0 +1,314 @@
+// Batched row transforms: one length-N line per thread group, all passes on chip.
+//
+// Method (Sections III-B, IV and V of the paper, re-designed for sm_103a):
+//
+//   forward   X = DFT(x)                                   (unnormalised)
+//   inverse   y = conj(DFT(conj(z) * 1/N))                 (Eq. 1: the 1/N block
+//                                                           shift folded into the
+//                                                           pre-inverse conjugate)
+//   compress  y = conj(DFT(conj(DFT(x) . H) * 1/N))        (matched filter,
+//                                                           Section III-B, Fig. 1)
+//
+// and the naive schedule of Section III-B, which drops the shift, stores the
+// unnormalised inverse to FP16 and only then scales by 1/N.
+//
+// Layout.  Lines are rows of N interleaved complex points, consecutive lines
+// `stride` points apart.  A group of T = N/16 threads owns one line; thread t
+// holds the 16 points x[t + T m], m = 0..15, in FP32 registers.  Loads and
+// stores of one warp touch consecutive points (coalesced), so every line is
+// read from HBM once and written once.
+//
+// Passes.  Stockham autosort, radix 16 for every pass but possibly the last
+// (radix 2, 4 or 8 when log2 N is not a multiple of 4).  A pass with radix R
+// and current sub-length Ns takes butterfly j = t + T b (b < 16/R) over the
+// points x[j + r N/R], multiplies point r by W_{Ns R}^{(j mod Ns) r}, runs the
+// R-point DFT in registers and writes point r to y[(j / Ns) Ns R + j mod Ns +
+// r Ns].  Between passes the line goes through shared memory in FP32 (one slot
+// of padding every 16 points keeps the stride-16 writes of the first pass free
+// of bank conflicts); after the last pass thread t holds X[t + T m] again, so
+// the forward result of a compress feeds the inverse without an exchange.
+//
+// Corner turns.  With TLOAD / TSTORE a line is a column of a row-major matrix
+// (point k of line l at k * stride + l).  The CTAs of a thread-block cluster
+// then move 8 lines at a time: each CTA reads (or writes) a slab of k for all
+// 8 lines as 32-byte segments and exchanges the points with the owning CTA
+// through distributed shared memory, so a transpose costs no extra HBM pass.
+//
+// Twiddles come from a per-length FP32 table W_N^i, i < N, generated on the
+// GPU in FP64 (sincospi) and rounded once -- never by recurrence, which the
+// paper identifies as the source of the ~42 dB "pure FP16" figure (Section
+// III-A).
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "complex_ops.cuh"
+#include "storage.cuh"
+
+namespace bfp {
+
+enum RowMode : int { kForward = 0, kInverse = 1, kCompress = 2 };
+
+struct RowArgs {
+  const void* in;
+  void* out;
+  const float2* tw;        // W_N^i for i in [0, N), FP32
+  const float2* h;         // filter spectrum [N] (compress only)
+  long long lines;         // number of lines
+  long long in_stride;     // points between consecutive input lines
+  long long out_stride;    // points between consecutive output lines
+  float in_scale;          // applied to loaded values (FP8 block exponent)
+  float out_scale;         // applied before the final rounding (FP8 block exponent)
+};
+
+constexpr int kPointsPerThread = 16;
+
+#ifndef BFP_MIN_BLOCKS
+#define BFP_MIN_BLOCKS 3
+#endif
+
+__host__ __device__ constexpr int pad16(int i) { return i + (i >> 4); }
+
+template <int N, bool TURN = false>
+struct RowShape {
+  static constexpr int P = kPointsPerThread;
+  static constexpr int T = N / P;                        // threads per line
+  static constexpr int kThreads = N <= 4096 ? 256 : T;   // threads per CTA
+  static constexpr int G = kThreads / T;                 // lines per CTA
+  // Corner-turn kernels stage whole lines in shared memory even for N = 16.
+  static constexpr int kSmemPerLine = (N > 16 || TURN) ? pad16(N) : 0;   // float2 slots
+  static constexpr size_t kSmemBytes = size_t(G) * kSmemPerLine * sizeof(float2);
+  // Cluster size of a corner-turn kernel: enough CTAs for 8 lines.
+  static constexpr int C = TURN ? (G >= 8 ? 1 : 8 / G) : 1;
+  static constexpr int kLinesPerCluster = C * G;
+  // Resident CTAs per SM requested from the register allocator.
+  static constexpr int kMinBlocks = kThreads >= 1024 ? 1 : (kThreads >= 512 ? 1 : BFP_MIN_BLOCKS);
+};
+
+template <int N, int Ns>
+struct StockhamPass {
+  static constexpr int P = kPointsPerThread;
+  static constexpr int T = N / P;
+  static constexpr int R = (N / Ns) >= 16 ? 16 : N / Ns;
+  static constexpr int B = P / R;
+  static constexpr bool kLast = (Ns * R == N);
+  static constexpr int kTwStride = N / (Ns * R);
+
+  __device__ __forceinline__ static void run(float2 (&v)[P], const float2* __restrict__ tw,
+                                             float2* __restrict__ sm, int t) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = t + T * b;
+      const int k = j & (Ns - 1);
+      float2 u[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) u[r] = v[b + B * r];
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[r] = cmul(u[r], __ldg(tw + k * r * kTwStride));
+      }
+      Dft<R>::run(u);
+      if (kLast) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b + B * r] = u[r];
+      } else {
+        const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[pad16(base + r * Ns)] = u[r];
+      }
+    }
+    if constexpr (!kLast) {
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < P; ++m) v[m] = sm[pad16(t + T * m)];
+      __syncthreads();
+      StockhamPass<N, Ns * R>::run(v, tw, sm, t);
+    }
+  }
+};
+
+// Full forward DFT of the line held in v (v[m] = x[t + T m] -> X[t + T m]).
+template <int N>
+__device__ __forceinline__ void line_dft(float2 (&v)[kPointsPerThread], const float2* __restrict__ tw,
+                                         float2* __restrict__ sm, int t) {
+  StockhamPass<N, 1>::run(v, tw, sm, t);
+}
+
+// Pointer to slot `idx` of line `l` of the cluster (l in [0, kLinesPerCluster)).
+template <class S>
+__device__ __forceinline__ float2* cluster_slot(float2* local_base, int l, int idx) {
+  float2* p = local_base + (l % S::G) * S::kSmemPerLine + idx;
+  if constexpr (S::C > 1) {
+    return cooperative_groups::this_cluster().map_shared_rank(p, l / S::G);
+  } else {
+    return p;
+  }
+}
+
+template <class S>
+__device__ __forceinline__ void cluster_barrier() {
+  if constexpr (S::C > 1) {
+    cooperative_groups::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+}
+
+template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, bool TLOAD, bool TSTORE>
+__global__ void __launch_bounds__(RowShape<N, TLOAD || TSTORE>::kThreads,
+                                  RowShape<N, TLOAD || TSTORE>::kMinBlocks)
+fft_rows_kernel(const RowArgs a) {
+  using S = RowShape<N, TLOAD || TSTORE>;
+  constexpr int P = S::P, T = S::T;
+  extern __shared__ float2 smem_rows[];
+  const int g = threadIdx.x / T;
+  const int t = threadIdx.x - g * T;
+  const long long line = (long long)blockIdx.x * S::G + g;
+  const bool active = line < a.lines;
+  float2* sm = smem_rows + g * S::kSmemPerLine;
+  const float inv_n = 1.0f / float(N);
+  // First line of this CTA's cluster (clusters are runs of C consecutive CTAs).
+  const long long line0 = (long long)(blockIdx.x / S::C) * S::kLinesPerCluster;
+  const int rank = int(blockIdx.x % S::C);
+  constexpr int kSlab = N / S::C;                        // points per CTA in a corner turn
+
+  float2 v[P];
+  if constexpr (TLOAD) {
+    // Gather: this CTA reads points [rank * kSlab, (rank + 1) * kSlab) of all
+    // cluster lines, 8 consecutive lines (one 32 B segment in FP16) per point.
+    const TIn* in = static_cast<const TIn*>(a.in);
+    // Every CTA of the cluster must be running before its shared memory is written.
+    cluster_barrier<S>();
+    for (int idx = threadIdx.x; idx < kSlab * S::kLinesPerCluster; idx += S::kThreads) {
+      const int l = idx % S::kLinesPerCluster;
+      const int k = rank * kSlab + idx / S::kLinesPerCluster;
+      const long long ln = line0 + l;
+      const float2 x = ln < a.lines ? Storage<TIn>::load(in + (long long)k * a.in_stride + ln)
+                                    : make_float2(0.f, 0.f);
+      *cluster_slot<S>(smem_rows, l, pad16(k)) = x;
+    }
+    cluster_barrier<S>();
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = sm[pad16(t + T * m)];
+    __syncthreads();
+  } else if (active) {
+    const TIn* in = static_cast<const TIn*>(a.in) + line * a.in_stride + t;
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = Storage<TIn>::load(in + T * m);
+  } else {
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = make_float2(0.f, 0.f);
+  }
+  if (SCALED) {
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = cscale(v[m], a.in_scale);
+  }
+  if (MODE == kInverse) {
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = NAIVE ? cconj(v[m]) : cscale(cconj(v[m]), inv_n);
+  }
+
+  line_dft<N>(v, a.tw, sm, t);
+
+  if (MODE == kCompress) {
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      const float2 p = cmul(v[m], __ldg(a.h + t + T * m));
+      v[m] = NAIVE ? cconj(p) : cscale(cconj(p), inv_n);
+    }
+    line_dft<N>(v, a.tw, sm, t);
+  }
+  if (MODE == kInverse || MODE == kCompress) {
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      v[m] = cconj(v[m]);
+      if (NAIVE) v[m] = naive_half_then_scale(v[m], inv_n);
+    }
+  }
+  if (SCALED) {
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = cscale(v[m], a.out_scale);
+  }
+  if constexpr (TSTORE) {
+    // Stage the line, then scatter slabs of all cluster lines as segments.
+    // The last pass read shared memory before a barrier, so the slots are free.
+#pragma unroll
+    for (int m = 0; m < P; ++m) sm[pad16(t + T * m)] = v[m];
+    cluster_barrier<S>();
+    TOut* out = static_cast<TOut*>(a.out);
+    for (int idx = threadIdx.x; idx < kSlab * S::kLinesPerCluster; idx += S::kThreads) {
+      const int l = idx % S::kLinesPerCluster;
+      const int k = rank * kSlab + idx / S::kLinesPerCluster;
+      const long long ln = line0 + l;
+      if (ln < a.lines) Storage<TOut>::store(out + (long long)k * a.out_stride + ln,
+                                             *cluster_slot<S>(smem_rows, l, pad16(k)));
+    }
+    // Keep this CTA's shared memory alive until every peer has read it.
+    cluster_barrier<S>();
+  } else if (active) {
+    TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;
+#pragma unroll
+    for (int m = 0; m < P; ++m) Storage<TOut>::store(out + T * m, v[m]);
+  }
+}
+
+template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, bool TLOAD = false,
+          bool TSTORE = false>
+cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
+  using S = RowShape<N, TLOAD || TSTORE>;
+  auto kern = fft_rows_kernel<N, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>;
+  if (S::kSmemBytes > 48 * 1024) {
+    static bool configured = false;   // attribute is per function; set once
+    if (!configured) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           int(S::kSmemBytes));
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+  }
+  if (a.lines <= 0) return cudaSuccess;
+  const long long clusters = (a.lines + S::kLinesPerCluster - 1) / S::kLinesPerCluster;
+  const long long grid = clusters * S::C;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if constexpr (S::C > 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(S::kThreads);
+    cfg.dynamicSmemBytes = S::kSmemBytes;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = S::C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
+    if (e != cudaSuccess) return e;
+  } else {
+    kern<<<dim3(unsigned(grid)), dim3(S::kThreads), S::kSmemBytes, stream>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// Dispatch on log2 N in [4, 14].
+template <class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, bool TLOAD = false, bool TSTORE = false>
+cudaError_t launch_rows(int log2n, const RowArgs& a, cudaStream_t stream) {
+  switch (log2n) {
+    case 4: return launch_rows_n<16, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
+    case 5: return launch_rows_n<32, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
+    case 6: return launch_rows_n<64, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
+    case 7: return launch_rows_n<128, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
+    case 8: return launch_rows_n<256, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
+    case 9: return launch_rows_n<512, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
+    case 10: return launch_rows_n<1024, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
+    case 11: return launch_rows_n<2048, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
+    case 12: return launch_rows_n<4096, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
+    case 13: return launch_rows_n<8192, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
+    case 14: return launch_rows_n<16384, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace bfp

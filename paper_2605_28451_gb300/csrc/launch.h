@@ -1,0 +1,31 @@
+// Host-side launch entry points of the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fft_rows.cuh"
+
+namespace bfp {
+
+// float2 -> float2 rows: mode in {kForward, kInverse, kCompress}.
+cudaError_t launch_rows_f32(int log2n, int mode, const RowArgs& a, cudaStream_t s);
+// __half2 -> __half2 rows; naive selects the unshifted inverse (Section III-B).
+cudaError_t launch_rows_f16(int log2n, int mode, bool naive, const RowArgs& a, cudaStream_t s);
+// Mixed-storage compress: float2 raw -> __half2 out, or __half2 raw -> float2 out.
+cudaError_t launch_compress_c64_to_f16(int log2n, bool naive, const RowArgs& a, cudaStream_t s);
+cudaError_t launch_compress_f16_to_c64(int log2n, const RowArgs& a, cudaStream_t s);
+// FP8 rows (fmt 0 = E4M3, 1 = E5M2); mode in {kForward, kInverse}.
+cudaError_t launch_rows_fp8(int log2n, int mode, int fmt, const RowArgs& a, cudaStream_t s);
+
+// SAR compression lines (Section VI, Fig. 1): float2 or __half2 in and out,
+// optional naive FP16 output, optional cluster corner turn on load / store.
+// Supported log2n: [kSarMinLog2, 14].
+constexpr int kSarMinLog2 = 8;
+cudaError_t launch_sar(int log2n, bool in16, bool out16, bool naive, bool tload, bool tstore,
+                       const RowArgs& a, cudaStream_t s);
+cudaError_t launch_sar_nn(int log2n, bool in16, bool out16, bool naive, const RowArgs& a, cudaStream_t s);
+cudaError_t launch_sar_nt(int log2n, bool in16, bool out16, bool naive, const RowArgs& a, cudaStream_t s);
+cudaError_t launch_sar_tt(int log2n, bool in16, bool out16, bool naive, const RowArgs& a, cudaStream_t s);
+
+
+}  // namespace bfp

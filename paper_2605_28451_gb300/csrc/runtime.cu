@@ -1,0 +1,310 @@
+// Plans, twiddle tables, argument checking and the C ABI of include/bfpfft.h.
+//
+// Nothing here does arithmetic of the method except the twiddle generator
+// (FP64 sincospi on the GPU, rounded once to FP32) and the small filter
+// normalisation kernel; every transform runs in the row kernels of
+// fft_rows.cuh, launched through launch.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "bfpfft.h"
+#include "launch.h"
+
+namespace {
+
+constexpr int kMinLog2 = 4;
+constexpr int kMaxLog2 = 14;
+
+int log2_exact(int64_t n) {
+  if (n <= 0 || (n & (n - 1)) != 0) return -1;
+  int l = 0;
+  while ((int64_t(1) << l) < n) ++l;
+  return l;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Host-side fault injection for the error paths: BFPFFT_FAULT=plan|alloc|launch
+// makes the named step fail without touching the GPU.
+bool fault(const char* step) {
+  const char* f = std::getenv("BFPFFT_FAULT");
+  return f != nullptr && std::strcmp(f, step) == 0;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return BFPFFT_OK;
+  if (e == cudaErrorMemoryAllocation) return BFPFFT_ERR_OOM;
+  return BFPFFT_ERR_CUDA;
+}
+
+// W_N^i = exp(-2 pi i / N * i) for i < N, evaluated in FP64 and rounded once.
+__global__ void twiddle_kernel(float2* tw, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    double s, c;
+    sincospi(-2.0 * double(i) / double(n), &s, &c);
+    tw[i] = make_float2(float(c), float(s));
+  }
+}
+
+// Per-device, per-length twiddle tables, created on first use and kept for
+// the life of the process (a few hundred KB per device at most).
+std::mutex g_tw_mutex;
+std::map<std::pair<int, int>, float2*> g_tw;
+
+int get_twiddles(int log2n, float2** out) {
+  *out = nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  std::lock_guard<std::mutex> lock(g_tw_mutex);
+  auto it = g_tw.find({dev, log2n});
+  if (it != g_tw.end()) {
+    *out = it->second;
+    return BFPFFT_OK;
+  }
+  if (fault("alloc")) return BFPFFT_ERR_OOM;
+  const int n = 1 << log2n;
+  float2* tw = nullptr;
+  e = cudaMalloc(&tw, sizeof(float2) * n);
+  if (e != cudaSuccess) return cuda_status(e);
+  twiddle_kernel<<<(n + 255) / 256, 256>>>(tw, n);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(tw);
+    return cuda_status(e);
+  }
+  g_tw[{dev, log2n}] = tw;
+  *out = tw;
+  return BFPFFT_OK;
+}
+
+bool valid_dtype(int d) { return d >= BFPFFT_F32 && d <= BFPFFT_E5M2_BFP; }
+
+// H = conj(H) / max_k |H[k]| (or conj only), one CTA.
+__global__ void conj_normalise_kernel(float2* h, int n, int peak_normalise) {
+  __shared__ float red[1024];
+  float m = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float2 v = h[i];
+    m = fmaxf(m, v.x * v.x + v.y * v.y);
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  const float scale = (peak_normalise && red[0] > 0.f) ? 1.0f / sqrtf(red[0]) : 1.0f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float2 v = h[i];
+    h[i] = make_float2(v.x * scale, -v.y * scale);
+  }
+}
+
+}  // namespace
+
+struct bfpfft_plan_s {
+  int64_t n;
+  int64_t batch;
+  int log2n;
+  int dtype;
+  int direction;
+  int device;
+  float2* tw;          // shared table from the per-device cache (not owned)
+  int in_exp;
+  int out_exp;
+};
+
+extern "C" {
+
+int bfpfft_version(void) { return 100; }
+
+const char* bfpfft_error_string(int status) {
+  switch (status) {
+    case BFPFFT_OK: return "ok";
+    case BFPFFT_ERR_INVALID_ARG: return "invalid argument";
+    case BFPFFT_ERR_UNSUPPORTED: return "unsupported length, dtype or direction";
+    case BFPFFT_ERR_CUDA: return "CUDA runtime error";
+    case BFPFFT_ERR_OOM: return "device out of memory";
+    case BFPFFT_ERR_TIMEOUT: return "device-side wait timed out";
+    case BFPFFT_ERR_NONFINITE: return "output holds Inf or NaN";
+    case BFPFFT_ERR_MISALIGNED: return "buffer not 16-byte aligned";
+    default: return "unknown status";
+  }
+}
+
+int bfpfft_plan_create(bfpfft_plan* out, int64_t n, int64_t batch, int dtype, int direction) {
+  if (out == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (batch < 0 || !valid_dtype(dtype)) return BFPFFT_ERR_INVALID_ARG;
+  if (direction != BFPFFT_FORWARD && direction != BFPFFT_INVERSE) return BFPFFT_ERR_INVALID_ARG;
+  const int l = log2_exact(n);
+  if (l < kMinLog2 || l > kMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
+  if (fault("plan")) return BFPFFT_ERR_CUDA;
+  bfpfft_plan p = new (std::nothrow) bfpfft_plan_s();
+  if (p == nullptr) return BFPFFT_ERR_OOM;
+  p->n = n;
+  p->batch = batch;
+  p->log2n = l;
+  p->dtype = dtype;
+  p->direction = direction;
+  p->in_exp = 0;
+  p->out_exp = 0;
+  if (dtype == BFPFFT_E4M3_BFP || dtype == BFPFFT_E5M2_BFP) {
+    const int s = (l + 1) / 2;            // ceil(log2(n) / 2)
+    if (direction == BFPFFT_FORWARD) p->out_exp = s; else p->in_exp = s;
+  }
+  cudaError_t e = cudaGetDevice(&p->device);
+  int st = e == cudaSuccess ? get_twiddles(l, &p->tw) : cuda_status(e);
+  if (st != BFPFFT_OK) {
+    delete p;
+    return st;
+  }
+  *out = p;
+  return BFPFFT_OK;
+}
+
+int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
+  if (plan == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (plan->batch == 0) return BFPFFT_OK;
+  if (in == nullptr || out == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (!aligned16(in) || !aligned16(out)) return BFPFFT_ERR_MISALIGNED;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
+  bfp::RowArgs a{};
+  a.in = in;
+  a.out = out;
+  a.tw = plan->tw;
+  a.h = nullptr;
+  a.lines = plan->batch;
+  a.in_stride = plan->n;
+  a.out_stride = plan->n;
+  a.in_scale = std::ldexp(1.0f, plan->in_exp);
+  a.out_scale = std::ldexp(1.0f, -plan->out_exp);
+  const int mode = plan->direction == BFPFFT_FORWARD ? bfp::kForward : bfp::kInverse;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  switch (plan->dtype) {
+    case BFPFFT_F32: e = bfp::launch_rows_f32(plan->log2n, mode, a, s); break;
+    case BFPFFT_F16_BFP: e = bfp::launch_rows_f16(plan->log2n, mode, false, a, s); break;
+    case BFPFFT_F16_NAIVE: e = bfp::launch_rows_f16(plan->log2n, mode, true, a, s); break;
+    case BFPFFT_E4M3_BFP: e = bfp::launch_rows_fp8(plan->log2n, mode, 0, a, s); break;
+    case BFPFFT_E5M2_BFP: e = bfp::launch_rows_fp8(plan->log2n, mode, 1, a, s); break;
+    default: return BFPFFT_ERR_UNSUPPORTED;
+  }
+  return cuda_status(e);
+}
+
+int bfpfft_plan_destroy(bfpfft_plan plan) {
+  delete plan;
+  return BFPFFT_OK;
+}
+
+int bfpfft_plan_scale_exp(bfpfft_plan plan, int* in_exp, int* out_exp) {
+  if (plan == nullptr || in_exp == nullptr || out_exp == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  *in_exp = plan->in_exp;
+  *out_exp = plan->out_exp;
+  return BFPFFT_OK;
+}
+
+int sar_make_filter(const void* ref, int64_t n, int peak_normalise, void* h_out, void* stream) {
+  if (ref == nullptr || h_out == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (!aligned16(ref) || !aligned16(h_out)) return BFPFFT_ERR_MISALIGNED;
+  const int l = log2_exact(n);
+  if (l < kMinLog2 || l > kMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
+  float2* tw = nullptr;
+  int st = get_twiddles(l, &tw);
+  if (st != BFPFFT_OK) return st;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
+  bfp::RowArgs a{};
+  a.in = ref;
+  a.out = h_out;
+  a.tw = tw;
+  a.lines = 1;
+  a.in_stride = n;
+  a.out_stride = n;
+  a.in_scale = 1.f;
+  a.out_scale = 1.f;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = bfp::launch_rows_f32(l, bfp::kForward, a, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  conj_normalise_kernel<<<1, 1024, 0, s>>>(static_cast<float2*>(h_out), int(n), peak_normalise);
+  return cuda_status(cudaGetLastError());
+}
+
+int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype, const void* hr,
+                       int64_t n_az, int64_t n_rg, int transpose_out, void* stream) {
+  if (n_az < 0) return BFPFFT_ERR_INVALID_ARG;
+  const int l = log2_exact(n_rg);
+  if (l < bfp::kSarMinLog2 || l > kMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
+  if (n_az == 0) return BFPFFT_OK;
+  if (raw == nullptr || out == nullptr || hr == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (!aligned16(raw) || !aligned16(out) || !aligned16(hr)) return BFPFFT_ERR_MISALIGNED;
+  if (raw_dtype != BFPFFT_F32 && raw_dtype != BFPFFT_F16_BFP) return BFPFFT_ERR_UNSUPPORTED;
+  if (out_dtype != BFPFFT_F32 && out_dtype != BFPFFT_F16_BFP && out_dtype != BFPFFT_F16_NAIVE)
+    return BFPFFT_ERR_UNSUPPORTED;
+  if (transpose_out != 0 && transpose_out != 1) return BFPFFT_ERR_INVALID_ARG;
+  float2* tw = nullptr;
+  int st = get_twiddles(l, &tw);
+  if (st != BFPFFT_OK) return st;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
+  bfp::RowArgs a{};
+  a.in = raw;
+  a.out = out;
+  a.tw = tw;
+  a.h = static_cast<const float2*>(hr);
+  a.lines = n_az;
+  a.in_stride = n_rg;
+  a.out_stride = transpose_out ? n_az : n_rg;
+  a.in_scale = 1.f;
+  a.out_scale = 1.f;
+  const bool naive = out_dtype == BFPFFT_F16_NAIVE;
+  const bool in16 = raw_dtype == BFPFFT_F16_BFP;
+  const bool out16 = out_dtype != BFPFFT_F32;
+  cudaError_t e = bfp::launch_sar(l, in16, out16, naive, /*tload=*/false, transpose_out != 0, a,
+                                  static_cast<cudaStream_t>(stream));
+  return cuda_status(e);
+}
+
+int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img, int img_dtype,
+                         const void* ha, int64_t n_az, int64_t n_rg, void* stream) {
+  if (n_rg < 0) return BFPFFT_ERR_INVALID_ARG;
+  const int l = log2_exact(n_az);
+  if (l < bfp::kSarMinLog2 || l > kMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
+  if (n_rg == 0) return BFPFFT_OK;
+  if (rc == nullptr || img == nullptr || ha == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (!aligned16(rc) || !aligned16(img) || !aligned16(ha)) return BFPFFT_ERR_MISALIGNED;
+  if (rc_dtype != BFPFFT_F32 && rc_dtype != BFPFFT_F16_BFP) return BFPFFT_ERR_UNSUPPORTED;
+  if (img_dtype != BFPFFT_F32 && img_dtype != BFPFFT_F16_BFP && img_dtype != BFPFFT_F16_NAIVE)
+    return BFPFFT_ERR_UNSUPPORTED;
+  if (rc_layout != 0 && rc_layout != 1) return BFPFFT_ERR_INVALID_ARG;
+  float2* tw = nullptr;
+  int st = get_twiddles(l, &tw);
+  if (st != BFPFFT_OK) return st;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
+  bfp::RowArgs a{};
+  a.in = rc;
+  a.out = img;
+  a.tw = tw;
+  a.h = static_cast<const float2*>(ha);
+  a.lines = n_rg;                                   // one line per range column
+  a.in_stride = rc_layout == 0 ? n_rg : n_az;       // [n_az][n_rg] column vs [n_rg][n_az] row
+  a.out_stride = n_rg;                              // image is [n_az][n_rg]
+  a.in_scale = 1.f;
+  a.out_scale = 1.f;
+  const bool naive = img_dtype == BFPFFT_F16_NAIVE;
+  cudaError_t e = bfp::launch_sar(l, rc_dtype == BFPFFT_F16_BFP, img_dtype != BFPFFT_F32, naive,
+                                  /*tload=*/rc_layout == 0, /*tstore=*/true, a,
+                                  static_cast<cudaStream_t>(stream));
+  return cuda_status(e);
+}
+
+}  // extern "C"

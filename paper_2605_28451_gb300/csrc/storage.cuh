@@ -1,0 +1,74 @@
+// Storage formats: load a complex point from HBM into FP32 registers and
+// round it back on the way out.
+//
+//   float2   FP32 complex, 8 B / point
+//   __half2  FP16 complex, 4 B / point (interleaved re, im; Section V's half2)
+//   Fp8x2<>  FP8 complex, 2 B / point (OCP E4M3 or E5M2, Section VII)
+//
+// Conversions round to nearest even; FP8 conversions saturate to the largest
+// finite value (satfinite).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+
+namespace bfp {
+
+struct E4M3 {};
+struct E5M2 {};
+
+template <class Fmt> struct alignas(2) Fp8x2 { __nv_fp8x2_storage_t bits; };
+
+template <class T> struct Storage;
+
+template <> struct Storage<float2> {
+  static constexpr int kBytes = 8;
+  __device__ __forceinline__ static float2 load(const float2* p) { return __ldcs(p); }
+  __device__ __forceinline__ static void store(float2* p, float2 v) { __stcs(p, v); }
+};
+
+template <> struct Storage<__half2> {
+  static constexpr int kBytes = 4;
+  __device__ __forceinline__ static float2 load(const __half2* p) {
+    const unsigned int u = __ldcs(reinterpret_cast<const unsigned int*>(p));
+    return __half22float2(*reinterpret_cast<const __half2*>(&u));
+  }
+  __device__ __forceinline__ static void store(__half2* p, float2 v) {
+    const __half2 h = __float22half2_rn(v);
+    __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
+  }
+};
+
+template <> struct Storage<Fp8x2<E4M3>> {
+  static constexpr int kBytes = 2;
+  __device__ __forceinline__ static float2 load(const Fp8x2<E4M3>* p) {
+    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2(p->bits, __NV_E4M3);
+    return __half22float2(*reinterpret_cast<const __half2*>(&h));
+  }
+  __device__ __forceinline__ static void store(Fp8x2<E4M3>* p, float2 v) {
+    p->bits = __nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E4M3);
+  }
+};
+
+template <> struct Storage<Fp8x2<E5M2>> {
+  static constexpr int kBytes = 2;
+  __device__ __forceinline__ static float2 load(const Fp8x2<E5M2>* p) {
+    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2(p->bits, __NV_E5M2);
+    return __half22float2(*reinterpret_cast<const __half2*>(&h));
+  }
+  __device__ __forceinline__ static void store(Fp8x2<E5M2>* p, float2 v) {
+    p->bits = __nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E5M2);
+  }
+};
+
+// Naive FP16 output of an unshifted inverse (Section III-B): the unnormalised
+// result is stored to half first (overflowing to +-Inf beyond 65504) and only
+// then multiplied by 1/N, in half.
+__device__ __forceinline__ float2 naive_half_then_scale(float2 v, float inv_n) {
+  const __half2 h = __float22half2_rn(v);
+  const __half2 s = __hmul2(h, __float2half2_rn(inv_n));
+  return __half22float2(s);
+}
+
+}  // namespace bfp

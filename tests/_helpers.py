@@ -1,0 +1,75 @@
+"""Test-side conversions between numpy complex arrays and device storage tensors."""
+
+import numpy as np
+
+from paper_2605_28451_gb300 import bfpfft as B
+
+
+def to_device(x: np.ndarray, dtype: int, device="cuda:0"):
+    """complex ndarray [..., n] -> device tensor in the storage format of `dtype`.
+
+    F32 -> complex64; F16_* -> float16 [..., n, 2]; FP8 -> uint8 [..., n, 2]
+    holding the bit patterns.  FP8 inputs must already be representable.
+    """
+    import torch
+    x = np.asarray(x)
+    if dtype == B.F32:
+        return torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).to(device)
+    pair = np.stack([x.real, x.imag], axis=-1)
+    if dtype in (B.F16_BFP, B.F16_NAIVE):
+        return torch.from_numpy(np.ascontiguousarray(pair.astype(np.float16))).to(device)
+    f8 = torch.float8_e4m3fn if dtype == B.E4M3_BFP else torch.float8_e5m2
+    t = torch.from_numpy(np.ascontiguousarray(pair.astype(np.float32))).to(f8)
+    back = t.to(torch.float32).numpy()
+    assert np.array_equal(back, pair.astype(np.float32)), "FP8 input not exactly representable"
+    return t.view(torch.uint8).to(device)
+
+
+def from_device(t, dtype: int) -> np.ndarray:
+    import torch
+    t = t.detach().cpu()
+    if dtype == B.F32:
+        return t.numpy().astype(np.complex128)
+    if dtype in (B.F16_BFP, B.F16_NAIVE):
+        a = t.numpy().astype(np.float64)
+    else:
+        f8 = torch.float8_e4m3fn if dtype == B.E4M3_BFP else torch.float8_e5m2
+        a = t.view(f8).to(torch.float32).numpy().astype(np.float64)
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def empty_like_storage(shape_pts, dtype: int, device="cuda:0"):
+    import torch
+    if dtype == B.F32:
+        return torch.empty(shape_pts, dtype=torch.complex64, device=device)
+    if dtype in (B.F16_BFP, B.F16_NAIVE):
+        return torch.empty(tuple(shape_pts) + (2,), dtype=torch.float16, device=device)
+    return torch.empty(tuple(shape_pts) + (2,), dtype=torch.uint8, device=device)
+
+
+def storage_round(x: np.ndarray, dtype: int) -> np.ndarray:
+    """The exact values a storage dtype holds for x (what the GPU receives)."""
+    from oracle import quant
+    if dtype == B.F32:
+        return quant.round_binary32(x)
+    if dtype in (B.F16_BFP, B.F16_NAIVE):
+        return quant.round_binary16(x)
+    return quant.round_fp8(x, "e4m3" if dtype == B.E4M3_BFP else "e5m2")
+
+
+def fp16_elementwise_ok(got: np.ndarray, ref: np.ndarray, fp32_rel: float = 1e-5):
+    """FP16 output = RN-even rounding of an FP32-computed value.
+
+    |got - ref| <= 2^-11 |ref| (half an FP16 ulp, normal range)
+                 + fp32_rel * rms(ref) (FP32 arithmetic of the passes)
+                 + 2^-25 (half the FP16 subnormal spacing), per component.
+    Returns (ok, worst ratio of error to bound).
+    """
+    rms = float(np.sqrt(np.mean(np.abs(ref) ** 2)))
+    out = 1.0
+    worst = 0.0
+    for g, r in ((got.real, ref.real), (got.imag, ref.imag)):
+        bound = 2.0 ** -11 * np.abs(r) * (1 + 1e-3) + fp32_rel * rms + 2.0 ** -25
+        ratio = np.abs(g - r) / bound
+        worst = max(worst, float(np.max(ratio)))
+    return worst <= out, worst

@@ -1,0 +1,87 @@
+"""The C-ABI library builds, loads and exports every symbol of include/*.h;
+host-side argument checks and fault injection return the documented status
+codes without touching a GPU (CPU only)."""
+
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2605_28451_gb300 import bfpfft as B
+from paper_2605_28451_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return B.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(B.SIGNATURES), "binding misses a declared function"
+
+
+def test_version_and_error_strings(lib):
+    assert B.bfpfft_version() >= 100
+    for st in range(8):
+        assert B.error_string(st) not in ("", "unknown status")
+    assert B.error_string(99) == "unknown status"
+
+
+@pytest.mark.parametrize("n", [0, 8, 12, 100, 32768, 65536, 1 << 20])
+def test_unsupported_lengths(lib, n):
+    with pytest.raises(B.BfpfftError) as e:
+        B.bfpfft_plan_create(n, 4, B.F16_BFP, B.FORWARD)
+    assert e.value.status == B.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("batch,dtype,direction", [(-1, B.F32, B.FORWARD), (4, 9, B.FORWARD),
+                                                   (4, B.F32, 0), (4, -1, B.INVERSE)])
+def test_invalid_plan_args(lib, batch, dtype, direction):
+    with pytest.raises(B.BfpfftError) as e:
+        B.bfpfft_plan_create(4096, batch, dtype, direction)
+    assert e.value.status == B.ERR_INVALID_ARG
+
+
+def test_null_plan_and_buffers(lib):
+    assert lib.bfpfft_exec(None, None, None, None) == B.ERR_INVALID_ARG
+    assert lib.bfpfft_plan_destroy(None) == B.OK
+    assert lib.bfpfft_plan_create(None, 4096, 1, 0, -1) == B.ERR_INVALID_ARG
+
+
+def test_sar_argument_checks(lib):
+    assert lib.sar_range_compress(16, 0, 16, 1, 16, -1, 4096, 0, None) == B.ERR_INVALID_ARG
+    assert lib.sar_range_compress(16, 0, 16, 1, 16, 8, 4095, 0, None) == B.ERR_UNSUPPORTED
+    assert lib.sar_range_compress(16, 0, 16, 1, 16, 8, 128, 0, None) == B.ERR_UNSUPPORTED
+    assert lib.sar_range_compress(16, 0, 16, 1, 16, 0, 4096, 0, None) == B.OK   # empty
+    assert lib.sar_range_compress(None, 0, 16, 1, 16, 8, 4096, 0, None) == B.ERR_INVALID_ARG
+    assert lib.sar_range_compress(17, 0, 16, 1, 16, 8, 4096, 0, None) == B.ERR_MISALIGNED
+    assert lib.sar_range_compress(16, 7, 16, 1, 16, 8, 4096, 0, None) == B.ERR_UNSUPPORTED
+    assert lib.sar_range_compress(16, 0, 16, 1, 16, 8, 4096, 2, None) == B.ERR_INVALID_ARG
+    assert lib.sar_azimuth_compress(16, 0, 3, 16, 1, 16, 4096, 8, None) == B.ERR_INVALID_ARG
+    assert lib.sar_azimuth_compress(16, 0, 0, 16, 1, 16, 4096, 0, None) == B.OK
+    assert lib.sar_make_filter(16, 100, 1, 16, None) == B.ERR_UNSUPPORTED
+    assert lib.sar_make_filter(16, 64, 1, 18, None) == B.ERR_MISALIGNED
+
+
+def test_fault_injection_plan(lib, monkeypatch):
+    monkeypatch.setenv("BFPFFT_FAULT", "plan")
+    with pytest.raises(B.BfpfftError) as e:
+        B.bfpfft_plan_create(4096, 4, B.F16_BFP, B.FORWARD)
+    assert e.value.status == B.ERR_CUDA

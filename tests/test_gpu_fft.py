@@ -1,0 +1,178 @@
+"""GPU parity of the batched FFT (bfpfft_plan_create / bfpfft_exec) against the FP64 oracle.
+
+Tolerances, stated against FP64 on the exact values the GPU receives:
+* FP32 storage: relative L2 error <= 1e-6 (and per element <= 1e-5 of the rms).
+* FP16 storage (block-floating-point): every element within half an FP16 ulp
+  of the oracle plus the FP32 arithmetic error (tests/_helpers.py), and
+  SQNR >= 55 dB at N = 4096 (Section III-A, Table II).
+* FP8 storage: every element equal to the oracle's rounding of the same
+  value, or one FP8 step away where FP32 arithmetic puts the value within
+  1e-5 (relative) of a rounding boundary.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import fft as F
+from oracle import metrics, quant
+from paper_2605_28451_gb300 import bfpfft as B
+from paper_2605_28451_gb300 import build, synth
+
+from _helpers import empty_like_storage, fp16_elementwise_ok, from_device, storage_round, to_device
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192, 16384]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(cuda_ready):
+    build.build()
+    B.lib()
+
+
+def run_fft(x_stored: np.ndarray, dtype: int, direction: int, inplace=False):
+    import torch
+    batch, n = x_stored.shape
+    plan = B.bfpfft_plan_create(n, batch, dtype, direction)
+    xin = to_device(x_stored, dtype)
+    out = xin if inplace else empty_like_storage((batch, n), dtype)
+    B.bfpfft_exec(plan, xin, out)
+    torch.cuda.synchronize()
+    return from_device(out, dtype)
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("batch", [1, 7])
+def test_f32_forward_and_inverse(n, batch):
+    x = storage_round(synth.complex_gaussian(batch, n, seed=n + batch), B.F32)
+    got = run_fft(x, B.F32, B.FORWARD)
+    ref = F.fft(x)
+    assert metrics.rel_l2(ref, got) <= 1e-6
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.sqrt(np.mean(np.abs(ref) ** 2))
+    y = storage_round(ref, B.F32)
+    got_i = run_fft(y, B.F32, B.INVERSE)
+    ref_i = F.ifft(y)
+    assert metrics.rel_l2(ref_i, got_i) <= 1e-6
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("batch", [3, 33])
+def test_f16_bfp_forward_and_inverse(n, batch):
+    x = storage_round(synth.complex_gaussian(batch, n, seed=100 + n + batch), B.F16_BFP)
+    got = run_fft(x, B.F16_BFP, B.FORWARD)
+    ref = F.fft(x)
+    ok, worst = fp16_elementwise_ok(got, ref)
+    assert ok, worst
+    spec = storage_round(ref, B.F16_BFP)
+    got_i = run_fft(spec, B.F16_BFP, B.INVERSE)
+    ref_i = F.ifft(spec)
+    ok, worst = fp16_elementwise_ok(got_i, ref_i)
+    assert ok, worst
+
+
+def test_f16_bfp_sqnr_at_4096_batch_256():
+    """The Table II workload: N = 4096, batch 256, re, im ~ N(0, 1), seed 0."""
+    x64 = synth.complex_gaussian(256, 4096, seed=0)
+    x = storage_round(x64, B.F16_BFP)
+    X = run_fft(x, B.F16_BFP, B.FORWARD)
+    ref = F.fft(x)
+    s_fwd = metrics.sqnr_db(ref, X)
+    assert s_fwd >= 55.0, s_fwd
+    y = run_fft(X, B.F16_BFP, B.INVERSE)
+    s_inv = metrics.sqnr_db(F.ifft(X), y)
+    assert s_inv >= 55.0, s_inv
+    assert metrics.rel_l2(x, y) <= 3e-3            # round trip
+    assert metrics.sqnr_db(x64, y) >= 50.0         # against the unrounded input too
+    X32 = run_fft(storage_round(x64, B.F32), B.F32, B.FORWARD)
+    assert metrics.rel_l2(F.fft(storage_round(x64, B.F32)), X32) <= 1e-6
+
+
+def test_naive_inverse_overflows_and_bfp_does_not():
+    """Section III-B: a flat spectrum of magnitude N (the matched product of a
+    discrete chirp with its unnormalised filter) has an unnormalised inverse of
+    N^2 ~ 1.7e7 at n = 0; stored to FP16 it is Inf.  With the 1/N shift the
+    same input gives N = 4096, finite."""
+    n = 4096
+    spec = np.full((2, n), float(n), dtype=complex)
+    naive = run_fft(spec, B.F16_NAIVE, B.INVERSE)
+    assert np.isinf(naive.real[:, 0]).all()
+    bfp = run_fft(spec, B.F16_BFP, B.INVERSE)
+    assert np.all(np.isfinite(bfp))
+    ok, worst = fp16_elementwise_ok(bfp, F.ifft(spec))
+    assert ok, worst
+
+
+def test_naive_inverse_matches_bfp_when_in_range():
+    x = storage_round(0.01 * synth.complex_gaussian(4, 1024, seed=7), B.F16_BFP)
+    naive = run_fft(x, B.F16_NAIVE, B.INVERSE)
+    ref = F.ifft(x)
+    assert np.all(np.isfinite(naive))
+    assert metrics.sqnr_db(ref, naive) >= 50.0
+
+
+def test_in_place_and_empty_batch():
+    import torch
+    x = storage_round(synth.complex_gaussian(5, 2048, seed=3), B.F16_BFP)
+    got = run_fft(x, B.F16_BFP, B.FORWARD, inplace=True)
+    ok, _ = fp16_elementwise_ok(got, F.fft(x))
+    assert ok
+    plan = B.bfpfft_plan_create(2048, 0, B.F16_BFP, B.FORWARD)
+    B.bfpfft_exec(plan, None, None)       # batch 0: a no-op, NULL buffers accepted
+    torch.cuda.synchronize()
+
+
+def test_misaligned_pointer_rejected():
+    import torch
+    buf = torch.zeros(4096 * 2 + 8, dtype=torch.float16, device="cuda:0")
+    plan = B.bfpfft_plan_create(4096, 1, B.F16_BFP, B.FORWARD)
+    with pytest.raises(B.BfpfftError) as e:
+        B.bfpfft_exec(plan, buf.data_ptr() + 4, buf.data_ptr() + 4)
+    assert e.value.status == B.ERR_MISALIGNED
+
+
+def test_large_batch_sampled_lines():
+    """The benchmark's launch configuration (N = 4096, batch 65536, FP16): the
+    oracle checks 8 sampled lines of the full-size output."""
+    import torch
+    n, batch = 4096, 65536
+    g = torch.Generator(device="cuda:0").manual_seed(0)
+    xin = torch.randn((batch, n, 2), device="cuda:0", generator=g).to(torch.float16)
+    out = torch.empty_like(xin)
+    plan = B.bfpfft_plan_create(n, batch, B.F16_BFP, B.FORWARD)
+    B.bfpfft_exec(plan, xin, out)
+    torch.cuda.synchronize()
+    rows = [0, 1, 4095, 4096, 30001, 65534, 65535, 12345]
+    xs = from_device(xin[rows], B.F16_BFP)
+    got = from_device(out[rows], B.F16_BFP)
+    ok, worst = fp16_elementwise_ok(got, F.fft(xs))
+    assert ok, worst
+
+
+@pytest.mark.parametrize("dtype,fmt", [(B.E4M3_BFP, "e4m3"), (B.E5M2_BFP, "e5m2")])
+@pytest.mark.parametrize("n", [256, 4096])
+def test_fp8_storage_matches_oracle_rounding(dtype, fmt, n):
+    x = quant.round_fp8(synth.complex_gaussian(16, n, seed=n), fmt)
+    plan = B.bfpfft_plan_create(n, 16, dtype, B.FORWARD)
+    in_exp, out_exp = B.bfpfft_plan_scale_exp(plan)
+    assert in_exp == 0 and out_exp == (int(np.log2(n)) + 1) // 2
+    got = run_fft(x, dtype, B.FORWARD)                   # stored = true * 2^-out_exp
+    exact = F.fft(x) * 2.0 ** -out_exp
+    expect = quant.round_fp8(exact, fmt)
+    _fp8_close(got, expect, exact, fmt)
+    # inverse of the stored spectrum back to the input scale
+    got_i = run_fft(got, dtype, B.INVERSE)
+    exact_i = F.ifft(got * 2.0 ** out_exp)
+    _fp8_close(got_i, quant.round_fp8(exact_i, fmt), exact_i, fmt)
+
+
+def _fp8_close(got, expect, exact, fmt):
+    for g, e, x in ((got.real, expect.real, exact.real), (got.imag, expect.imag, exact.imag)):
+        bad = g != e
+        if not bad.any():
+            continue
+        # a mismatch is allowed only next to a rounding boundary
+        lo = quant.round_fp8(x[bad] * (1 - 1e-5), fmt)
+        hi = quant.round_fp8(x[bad] * (1 + 1e-5), fmt)
+        assert np.all((g[bad] == lo) | (g[bad] == hi)), (g[bad][:5], e[bad][:5], x[bad][:5])
+        assert bad.mean() <= 1e-3

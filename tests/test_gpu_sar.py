@@ -1,0 +1,183 @@
+"""GPU parity of the SAR range-Doppler compression against the FP64 oracle.
+
+Stated against FP64: FP32 paths to relative L2 <= 1e-6; FP16-BFP outputs per
+element within half an FP16 ulp plus the FP32 arithmetic error; end-to-end
+FP16 image SQNR >= 40 dB; PSLR / ISLR / SNR within 0.1 dB and 3 dB widths
+within 0.1 cell of the oracle's image (Section VI, Table III).  The naive
+unshifted FP16 path must produce Inf or NaN (Section III-B).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import metrics, sar
+from paper_2605_28451_gb300 import bfpfft as B
+from paper_2605_28451_gb300 import build, synth
+
+from _helpers import empty_like_storage, fp16_elementwise_ok, from_device, storage_round, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(cuda_ready):
+    build.build()
+    B.lib()
+
+
+def gpu_filter(ref: np.ndarray, peak_normalise: bool):
+    import torch
+    n = ref.shape[0]
+    r = to_device(ref, B.F32)
+    h = torch.empty(n, dtype=torch.complex64, device="cuda:0")
+    B.sar_make_filter(r, n, peak_normalise, h)
+    torch.cuda.synchronize()
+    return h
+
+
+def gpu_range(raw_stored, raw_dtype, out_dtype, hr, transpose=False):
+    import torch
+    n_az, n_rg = raw_stored.shape
+    x = to_device(raw_stored, raw_dtype)
+    out = empty_like_storage((n_rg, n_az) if transpose else (n_az, n_rg), out_dtype)
+    B.sar_range_compress(x, raw_dtype, out, out_dtype, hr, n_az, n_rg, transpose)
+    torch.cuda.synchronize()
+    return from_device(out, out_dtype)
+
+
+def gpu_azimuth(rc_stored, rc_dtype, layout, img_dtype, ha, n_az, n_rg):
+    import torch
+    x = to_device(rc_stored, rc_dtype)
+    img = empty_like_storage((n_az, n_rg), img_dtype)
+    B.sar_azimuth_compress(x, rc_dtype, layout, img, img_dtype, ha, n_az, n_rg)
+    torch.cuda.synchronize()
+    return from_device(img, img_dtype)
+
+
+@pytest.mark.parametrize("n", [256, 4096, 16384])
+@pytest.mark.parametrize("norm", [False, True])
+def test_make_filter(n, norm):
+    ref = synth.centred_reference(synth.range_chirp()[: min(480, n // 2)], n)
+    h = gpu_filter(ref, norm).cpu().numpy().astype(np.complex128)
+    expect = sar.matched_filter(storage_round(ref, B.F32), norm)
+    assert metrics.rel_l2(expect, h) <= 1e-6
+
+
+@pytest.mark.parametrize("n_az", [8, 45])
+@pytest.mark.parametrize("n_rg", [256, 2048, 4096])
+@pytest.mark.parametrize("transpose", [False, True])
+@pytest.mark.parametrize("raw_dtype,out_dtype", [(B.F32, B.F32), (B.F32, B.F16_BFP), (B.F16_BFP, B.F16_BFP),
+                                                 (B.F16_BFP, B.F32)])
+def test_range_compress(n_az, n_rg, transpose, raw_dtype, out_dtype):
+    sc = synth.point_target_scene(n_az, n_rg, aperture=16, targets=[(n_az // 2, n_rg // 2, 1.0)],
+                                  noise_seed=n_az + n_rg)
+    ref_r = synth.centred_reference(synth.range_chirp()[: min(480, n_rg // 2)], n_rg)
+    hr = gpu_filter(ref_r, False)
+    raw = storage_round(sc.raw, raw_dtype)
+    got = gpu_range(raw, raw_dtype, out_dtype, hr, transpose)
+    if transpose:
+        got = got.T
+    expect = sar.range_compress(raw, hr.cpu().numpy().astype(np.complex128))
+    if out_dtype == B.F32:
+        assert metrics.rel_l2(expect, got) <= 1e-6
+    else:
+        ok, worst = fp16_elementwise_ok(got, expect)
+        assert ok, worst
+
+
+@pytest.mark.parametrize("n_az", [256, 4096])
+@pytest.mark.parametrize("n_rg", [8, 45])
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("rc_dtype,img_dtype", [(B.F32, B.F32), (B.F16_BFP, B.F16_BFP), (B.F16_BFP, B.F32)])
+def test_azimuth_compress(n_az, n_rg, layout, rc_dtype, img_dtype):
+    rng = np.random.default_rng(n_az + n_rg)
+    rc = rng.standard_normal((n_az, n_rg)) + 1j * rng.standard_normal((n_az, n_rg))
+    rc = storage_round(rc, rc_dtype)
+    ref_a = synth.centred_reference(synth.azimuth_chirp(min(1024, n_az // 2)), n_az)
+    ha = gpu_filter(ref_a, True)
+    stored = rc if layout == 0 else np.ascontiguousarray(rc.T)
+    got = gpu_azimuth(stored, rc_dtype, layout, img_dtype, ha, n_az, n_rg)
+    expect = sar.azimuth_compress(rc, ha.cpu().numpy().astype(np.complex128))
+    if img_dtype == B.F32:
+        assert metrics.rel_l2(expect, got) <= 1e-6
+    else:
+        ok, worst = fp16_elementwise_ok(got, expect)
+        assert ok, worst
+
+
+def _pipeline(raw_c64, hr, ha, n_az, n_rg, dtype):
+    """GPU range compression (corner-turned store) then azimuth compression."""
+    import torch
+    raw = to_device(raw_c64, B.F32)
+    rc = empty_like_storage((n_rg, n_az), dtype)
+    img = empty_like_storage((n_az, n_rg), dtype)
+    B.sar_range_compress(raw, B.F32, rc, dtype, hr, n_az, n_rg, True)
+    B.sar_azimuth_compress(rc, B.F16_BFP if dtype != B.F32 else B.F32, 1, img, dtype, ha, n_az, n_rg)
+    torch.cuda.synchronize()
+    return from_device(img, dtype)
+
+
+@pytest.fixture(scope="module")
+def small_scene():
+    n_az, n_rg, ap = 1024, 2048, 512
+    sc = synth.point_target_scene(n_az, n_rg, aperture=ap)
+    raw = storage_round(sc.raw, B.F32)
+    hr = gpu_filter(sc.ref_range, False)
+    ha = gpu_filter(sc.ref_azimuth, True)
+    hr64 = hr.cpu().numpy().astype(np.complex128)
+    ha64 = ha.cpu().numpy().astype(np.complex128)
+    img_ref = sar.range_doppler_image(raw, hr64, ha64)
+    return sc, raw, hr, ha, img_ref
+
+
+def test_end_to_end_fp16_image_quality(small_scene):
+    sc, raw, hr, ha, img_ref = small_scene
+    n_az, n_rg = raw.shape
+    img16 = _pipeline(raw, hr, ha, n_az, n_rg, B.F16_BFP)
+    img32 = _pipeline(raw, hr, ha, n_az, n_rg, B.F32)
+    assert np.all(np.isfinite(img16))
+    assert metrics.sqnr_db(img_ref, img16) >= 40.0
+    assert metrics.rel_l2(img_ref, img32) <= 1e-6
+    m_ref = metrics.point_target_metrics(img_ref, sc.targets)
+    m16 = metrics.point_target_metrics(img16, sc.targets)
+    for a, b in zip(m_ref, m16):
+        assert a["peak_cell"] == b["peak_cell"]
+        for k in ("pslr_range_db", "pslr_azimuth_db", "islr_range_db", "islr_azimuth_db", "snr_db"):
+            assert abs(a[k] - b[k]) <= 0.1, (k, a[k], b[k])
+        for k in ("width_range_cells", "width_azimuth_cells"):
+            assert abs(a[k] - b[k]) <= 0.1, (k, a[k], b[k])
+
+
+def test_naive_fp16_range_compression_overflows():
+    """Config 2 shape: 1024 azimuth lines x 4096 range samples.  The
+    unnormalised range inverse peaks at N * M = 1.97e6 > 65504 (Section III-B)."""
+    sc = synth.point_target_scene(1024, 4096)
+    raw = storage_round(sc.raw, B.F32)
+    hr = gpu_filter(sc.ref_range, False)
+    naive = gpu_range(raw, B.F32, B.F16_NAIVE, hr)
+    assert (~np.isfinite(naive)).any()
+    m = sar.stage_maxima(raw[sc.targets[0][0]:sc.targets[0][0] + 1], hr.cpu().numpy().astype(np.complex128))
+    assert m["naive_out"] > 65520.0 and m["bfp_out"] < 65504.0 / 2
+    bfp = gpu_range(raw, B.F32, B.F16_BFP, hr)
+    assert np.all(np.isfinite(bfp))
+    rows = [t[0] for t in sc.targets[:4]]
+    expect = sar.range_compress(raw[rows], hr.cpu().numpy().astype(np.complex128))
+    ok, worst = fp16_elementwise_ok(bfp[rows], expect)
+    assert ok, worst
+
+
+def test_full_size_image_sampled_columns():
+    """Config 3 at full size (4096 x 4096, FP16-BFP): the oracle range-compresses
+    every line and azimuth-compresses 32 sampled columns, including every
+    target column."""
+    n = 4096
+    sc = synth.point_target_scene(n, n)
+    raw = storage_round(sc.raw, B.F32)
+    hr = gpu_filter(sc.ref_range, False)
+    ha = gpu_filter(sc.ref_azimuth, True)
+    img16 = _pipeline(raw, hr, ha, n, n, B.F16_BFP)
+    assert np.all(np.isfinite(img16))
+    cols = sorted(set([t[1] for t in sc.targets] + list(np.random.default_rng(9).choice(n, 24, replace=False))))
+    rc = sar.range_compress(raw, hr.cpu().numpy().astype(np.complex128))
+    ref_cols = sar.azimuth_compress(rc[:, cols], ha.cpu().numpy().astype(np.complex128))
+    assert metrics.sqnr_db(ref_cols, img16[:, cols]) >= 40.0
