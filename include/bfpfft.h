@@ -105,6 +105,15 @@ int bfpfft_plan_destroy(bfpfft_plan plan);
  */
 int bfpfft_plan_scale_exp(bfpfft_plan plan, int* in_exp, int* out_exp);
 
+/*
+ * Read and clear the current device's status word after a device-wide
+ * synchronisation.  Kernels with bounded device-side waits (the pipelined row
+ * kernels that stream lines through shared memory with bulk asynchronous
+ * copies) record BFPFFT_ERR_TIMEOUT there instead of spinning forever;
+ * BFPFFT_OK means no wait expired since the last call.  Errors: INVALID_ARG
+ * (status NULL), CUDA.
+ */
+int bfpfft_device_status(int* status);
 
 /* ---------------------------------------------------------------------------
  * SAR range-Doppler compression (Section VI, Fig. 1).

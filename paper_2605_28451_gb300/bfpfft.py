@@ -46,6 +46,7 @@ SIGNATURES = {
     "bfpfft_exec": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "bfpfft_plan_destroy": (ctypes.c_int, [_vp]),
     "bfpfft_plan_scale_exp": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "bfpfft_device_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
     "sar_make_filter": (ctypes.c_int, [_vp, _c_int64, ctypes.c_int, _vp, _vp]),
     "sar_range_compress": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _c_int64, _c_int64,
                                           ctypes.c_int, _vp]),
@@ -150,6 +151,13 @@ def bfpfft_plan_scale_exp(plan: Plan):
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(lib().bfpfft_plan_scale_exp(plan.handle, ctypes.byref(a), ctypes.byref(b)), "bfpfft_plan_scale_exp")
     return a.value, b.value
+
+
+def bfpfft_device_status() -> int:
+    """Synchronise the device, then read and clear its status word."""
+    st = ctypes.c_int()
+    _check(lib().bfpfft_device_status(ctypes.byref(st)), "bfpfft_device_status")
+    return st.value
 
 
 def sar_make_filter(ref, n: int, peak_normalise: bool, h_out, stream=None):

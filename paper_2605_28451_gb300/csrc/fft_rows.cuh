@@ -43,6 +43,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include "async_copy.cuh"
 #include "complex_ops.cuh"
 #include "storage.cuh"
 
@@ -60,6 +61,8 @@ struct RowArgs {
   long long out_stride;    // points between consecutive output lines
   float in_scale;          // applied to loaded values (FP8 block exponent)
   float out_scale;         // applied before the final rounding (FP8 block exponent)
+  int* status;             // device status word (bounded waits record timeouts here)
+  int variant;             // 0: bulk-copy pipelined rows where possible, 1: plain rows
 };
 
 constexpr int kPointsPerThread = 16;
@@ -135,6 +138,45 @@ __device__ __forceinline__ void line_dft(float2 (&v)[kPointsPerThread], const fl
   StockhamPass<N, 1>::run(v, tw, sm, t);
 }
 
+// The per-line chain between load and store: block exponents, the inverse's
+// conj * 1/N (Eq. 1), the transform(s), the filter multiply of compress mode,
+// the final conjugate, and the naive FP16 rounding of Section III-B.
+template <int N, int MODE, bool NAIVE, bool SCALED>
+__device__ __forceinline__ void row_compute(float2 (&v)[kPointsPerThread], const RowArgs& a, float2* sm, int t) {
+  constexpr int P = kPointsPerThread, T = N / P;
+  const float inv_n = 1.0f / float(N);
+  if (SCALED) {
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = cscale(v[m], a.in_scale);
+  }
+  if (MODE == kInverse) {
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = NAIVE ? cconj(v[m]) : cscale(cconj(v[m]), inv_n);
+  }
+
+  line_dft<N>(v, a.tw, sm, t);
+
+  if (MODE == kCompress) {
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      const float2 p = cmul(v[m], __ldg(a.h + t + T * m));
+      v[m] = NAIVE ? cconj(p) : cscale(cconj(p), inv_n);
+    }
+    line_dft<N>(v, a.tw, sm, t);
+  }
+  if (MODE == kInverse || MODE == kCompress) {
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      v[m] = cconj(v[m]);
+      if (NAIVE) v[m] = naive_half_then_scale(v[m], inv_n);
+    }
+  }
+  if (SCALED) {
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = cscale(v[m], a.out_scale);
+  }
+}
+
 // Pointer to slot `idx` of line `l` of the cluster (l in [0, kLinesPerCluster)).
 template <class S>
 __device__ __forceinline__ float2* cluster_slot(float2* local_base, int l, int idx) {
@@ -167,7 +209,6 @@ fft_rows_kernel(const RowArgs a) {
   const long long line = (long long)blockIdx.x * S::G + g;
   const bool active = line < a.lines;
   float2* sm = smem_rows + g * S::kSmemPerLine;
-  const float inv_n = 1.0f / float(N);
   // First line of this CTA's cluster (clusters are runs of C consecutive CTAs).
   const long long line0 = (long long)(blockIdx.x / S::C) * S::kLinesPerCluster;
   const int rank = int(blockIdx.x % S::C);
@@ -200,36 +241,8 @@ fft_rows_kernel(const RowArgs a) {
 #pragma unroll
     for (int m = 0; m < P; ++m) v[m] = make_float2(0.f, 0.f);
   }
-  if (SCALED) {
-#pragma unroll
-    for (int m = 0; m < P; ++m) v[m] = cscale(v[m], a.in_scale);
-  }
-  if (MODE == kInverse) {
-#pragma unroll
-    for (int m = 0; m < P; ++m) v[m] = NAIVE ? cconj(v[m]) : cscale(cconj(v[m]), inv_n);
-  }
+  row_compute<N, MODE, NAIVE, SCALED>(v, a, sm, t);
 
-  line_dft<N>(v, a.tw, sm, t);
-
-  if (MODE == kCompress) {
-#pragma unroll
-    for (int m = 0; m < P; ++m) {
-      const float2 p = cmul(v[m], __ldg(a.h + t + T * m));
-      v[m] = NAIVE ? cconj(p) : cscale(cconj(p), inv_n);
-    }
-    line_dft<N>(v, a.tw, sm, t);
-  }
-  if (MODE == kInverse || MODE == kCompress) {
-#pragma unroll
-    for (int m = 0; m < P; ++m) {
-      v[m] = cconj(v[m]);
-      if (NAIVE) v[m] = naive_half_then_scale(v[m], inv_n);
-    }
-  }
-  if (SCALED) {
-#pragma unroll
-    for (int m = 0; m < P; ++m) v[m] = cscale(v[m], a.out_scale);
-  }
   if constexpr (TSTORE) {
     // Stage the line, then scatter slabs of all cluster lines as segments.
     // The last pass read shared memory before a barrier, so the slots are free.
@@ -253,10 +266,128 @@ fft_rows_kernel(const RowArgs a) {
   }
 }
 
+
+// Persistent, software-pipelined variant for dense rows (stride == N, no
+// corner turn).  Each CTA walks groups of G lines grid-stride; one thread
+// keeps STAGES groups in flight with bulk asynchronous copies (TMA) into
+// shared-memory stages while the CTA transforms the current group, so HBM
+// reads overlap the butterflies.  Stores go straight from registers to HBM
+// (coalesced).  Waits are bounded: on expiry the CTA records a timeout in
+// a.status, drains its own outstanding copies (again bounded) and returns.
+template <int N, class TIn, int STAGES>
+struct TmaLayout {
+  using S = RowShape<N>;
+  static constexpr size_t kStageBytes = size_t(S::G) * N * sizeof(TIn);
+  static constexpr size_t kBarBytes = 128;
+  static constexpr size_t kXchBytes = size_t(S::G) * S::kSmemPerLine * sizeof(float2);
+  static constexpr size_t kBytes = kBarBytes + STAGES * kStageBytes + kXchBytes;
+};
+
+template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, int STAGES>
+__global__ void __launch_bounds__(RowShape<N>::kThreads, RowShape<N>::kMinBlocks)
+fft_rows_tma_kernel(const RowArgs a) {
+  using S = RowShape<N>;
+  using L = TmaLayout<N, TIn, STAGES>;
+  constexpr int P = S::P, T = S::T, G = S::G;
+  extern __shared__ __align__(128) unsigned char smem_tma[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_tma);
+  unsigned char* stages = smem_tma + L::kBarBytes;
+  float2* xch = reinterpret_cast<float2*>(stages + STAGES * L::kStageBytes);
+  const int g = threadIdx.x / T;
+  const int t = threadIdx.x - g * T;
+  float2* sm = xch + g * S::kSmemPerLine;
+  const long long groups = (a.lines + G - 1) / G;
+  const TIn* src = static_cast<const TIn*>(a.in);
+
+  auto issue = [&](long long grp, int stage) {
+    const long long first = grp * G;
+    const long long valid = a.lines - first < G ? a.lines - first : G;
+    const uint32_t bytes = uint32_t(valid * N * sizeof(TIn));
+    mbar_arrive_expect_tx(&bars[stage], bytes);
+    bulk_load(stages + stage * L::kStageBytes, src + first * N, bytes, &bars[stage]);
+  };
+
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+    fence_proxy_async_shared();
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) {
+      const long long grp = blockIdx.x + (long long)s * gridDim.x;
+      if (grp < groups) issue(grp, s);
+    }
+  }
+  __syncthreads();
+
+  int it = 0;
+  for (long long grp = blockIdx.x; grp < groups; grp += gridDim.x, ++it) {
+    const int stage = it % STAGES;
+    const uint32_t parity = (it / STAGES) & 1;
+    const bool arrived = mbar_wait_bounded(&bars[stage], parity, a.status);
+    float2 v[P];
+    const TIn* st = reinterpret_cast<const TIn*>(stages + stage * L::kStageBytes) + g * N + t;
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = Storage<TIn>::load_smem(st + T * m);
+    // All threads agree on a timeout; the stage is free once everyone has read it.
+    if (__syncthreads_or(!arrived)) {
+      if (threadIdx.x == 0) {
+        for (int k = 1; k < STAGES; ++k) {             // drain copies still in flight
+          const long long later = grp + (long long)k * gridDim.x;
+          if (later < groups) mbar_wait_bounded(&bars[(it + k) % STAGES], ((it + k) / STAGES) & 1, nullptr);
+        }
+      }
+      __syncthreads();
+      return;
+    }
+    if (threadIdx.x == 0) {
+      const long long nxt = grp + (long long)STAGES * gridDim.x;
+      if (nxt < groups) {
+        fence_proxy_async_shared();
+        issue(nxt, stage);
+      }
+    }
+    row_compute<N, MODE, NAIVE, SCALED>(v, a, sm, t);
+    const long long line = grp * G + g;
+    if (line < a.lines) {
+      TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;
+#pragma unroll
+      for (int m = 0; m < P; ++m) Storage<TOut>::store(out + T * m, v[m]);
+    }
+  }
+}
+
+template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED>
+cudaError_t launch_rows_tma_n(const RowArgs& a, cudaStream_t stream) {
+  using S = RowShape<N>;
+  constexpr int kStages = 2;
+  using L = TmaLayout<N, TIn, kStages>;
+  auto kern = fft_rows_tma_kernel<N, TIn, TOut, MODE, NAIVE, SCALED, kStages>;
+  static int grid_cap = 0;   // resident CTAs on this device (computed once)
+  if (grid_cap == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::kBytes));
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::kThreads, L::kBytes);
+    if (e != cudaSuccess) return e;
+    grid_cap = (per_sm > 0 ? per_sm : 1) * sms;
+  }
+  if (a.lines <= 0) return cudaSuccess;
+  const long long groups = (a.lines + S::G - 1) / S::G;
+  const int grid = int(groups < grid_cap ? groups : grid_cap);
+  kern<<<dim3(grid), dim3(S::kThreads), L::kBytes, stream>>>(a);
+  return cudaGetLastError();
+}
+
 template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, bool TLOAD = false,
           bool TSTORE = false>
 cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
   using S = RowShape<N, TLOAD || TSTORE>;
+  if constexpr (!TLOAD && !TSTORE && N >= 256) {
+    if (a.variant == 0 && a.in_stride == N && a.out_stride == N)
+      return launch_rows_tma_n<N, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
+  }
   auto kern = fft_rows_kernel<N, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>;
   if (S::kSmemBytes > 48 * 1024) {
     static bool configured = false;   // attribute is per function; set once

@@ -87,6 +87,49 @@ int get_twiddles(int log2n, float2** out) {
   return BFPFFT_OK;
 }
 
+// One device status word per device (bounded device-side waits record
+// BFPFFT_ERR_TIMEOUT here); read and cleared by bfpfft_device_status().
+std::map<int, int*> g_status;
+
+int get_status_word(int** out) {
+  *out = nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  std::lock_guard<std::mutex> lock(g_tw_mutex);
+  auto it = g_status.find(dev);
+  if (it != g_status.end()) {
+    *out = it->second;
+    return BFPFFT_OK;
+  }
+  int* w = nullptr;
+  e = cudaMalloc(&w, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(w, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_status(e);
+  g_status[dev] = w;
+  *out = w;
+  return BFPFFT_OK;
+}
+
+// Kernel variant: BFPFFT_ROWS=plain forces the non-pipelined row kernel.
+int rows_variant() {
+  const char* v = std::getenv("BFPFFT_ROWS");
+  return (v != nullptr && std::strcmp(v, "plain") == 0) ? 1 : 0;
+}
+
+// Common RowArgs set-up: twiddles, status word, unit scales.
+int row_args(int log2n, bfp::RowArgs* a) {
+  std::memset(a, 0, sizeof(*a));
+  int st = get_twiddles(log2n, const_cast<float2**>(&a->tw));
+  if (st != BFPFFT_OK) return st;
+  st = get_status_word(&a->status);
+  if (st != BFPFFT_OK) return st;
+  a->in_scale = 1.f;
+  a->out_scale = 1.f;
+  a->variant = rows_variant();
+  return BFPFFT_OK;
+}
+
 bool valid_dtype(int d) { return d >= BFPFFT_F32 && d <= BFPFFT_E5M2_BFP; }
 
 // H = conj(H) / max_k |H[k]| (or conj only), one CTA.
@@ -120,6 +163,7 @@ struct bfpfft_plan_s {
   int direction;
   int device;
   float2* tw;          // shared table from the per-device cache (not owned)
+  int* status;         // the device's status word (not owned)
   int in_exp;
   int out_exp;
 };
@@ -165,6 +209,7 @@ int bfpfft_plan_create(bfpfft_plan* out, int64_t n, int64_t batch, int dtype, in
   }
   cudaError_t e = cudaGetDevice(&p->device);
   int st = e == cudaSuccess ? get_twiddles(l, &p->tw) : cuda_status(e);
+  if (st == BFPFFT_OK) st = get_status_word(&p->status);
   if (st != BFPFFT_OK) {
     delete p;
     return st;
@@ -184,6 +229,8 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
   a.out = out;
   a.tw = plan->tw;
   a.h = nullptr;
+  a.status = plan->status;
+  a.variant = rows_variant();
   a.lines = plan->batch;
   a.in_stride = plan->n;
   a.out_stride = plan->n;
@@ -215,24 +262,31 @@ int bfpfft_plan_scale_exp(bfpfft_plan plan, int* in_exp, int* out_exp) {
   return BFPFFT_OK;
 }
 
+int bfpfft_device_status(int* status) {
+  if (status == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  int* w = nullptr;
+  int st = get_status_word(&w);
+  if (st != BFPFFT_OK) return st;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(status, w, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(w, 0, sizeof(int));
+  return cuda_status(e);
+}
+
 int sar_make_filter(const void* ref, int64_t n, int peak_normalise, void* h_out, void* stream) {
   if (ref == nullptr || h_out == nullptr) return BFPFFT_ERR_INVALID_ARG;
   if (!aligned16(ref) || !aligned16(h_out)) return BFPFFT_ERR_MISALIGNED;
   const int l = log2_exact(n);
   if (l < kMinLog2 || l > kMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
-  float2* tw = nullptr;
-  int st = get_twiddles(l, &tw);
+  bfp::RowArgs a;
+  int st = row_args(l, &a);
   if (st != BFPFFT_OK) return st;
   if (fault("launch")) return BFPFFT_ERR_CUDA;
-  bfp::RowArgs a{};
   a.in = ref;
   a.out = h_out;
-  a.tw = tw;
   a.lines = 1;
   a.in_stride = n;
   a.out_stride = n;
-  a.in_scale = 1.f;
-  a.out_scale = 1.f;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = bfp::launch_rows_f32(l, bfp::kForward, a, s);
   if (e != cudaSuccess) return cuda_status(e);
@@ -252,20 +306,16 @@ int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype,
   if (out_dtype != BFPFFT_F32 && out_dtype != BFPFFT_F16_BFP && out_dtype != BFPFFT_F16_NAIVE)
     return BFPFFT_ERR_UNSUPPORTED;
   if (transpose_out != 0 && transpose_out != 1) return BFPFFT_ERR_INVALID_ARG;
-  float2* tw = nullptr;
-  int st = get_twiddles(l, &tw);
+  bfp::RowArgs a;
+  int st = row_args(l, &a);
   if (st != BFPFFT_OK) return st;
   if (fault("launch")) return BFPFFT_ERR_CUDA;
-  bfp::RowArgs a{};
   a.in = raw;
   a.out = out;
-  a.tw = tw;
   a.h = static_cast<const float2*>(hr);
   a.lines = n_az;
   a.in_stride = n_rg;
   a.out_stride = transpose_out ? n_az : n_rg;
-  a.in_scale = 1.f;
-  a.out_scale = 1.f;
   const bool naive = out_dtype == BFPFFT_F16_NAIVE;
   const bool in16 = raw_dtype == BFPFFT_F16_BFP;
   const bool out16 = out_dtype != BFPFFT_F32;
@@ -286,20 +336,16 @@ int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img,
   if (img_dtype != BFPFFT_F32 && img_dtype != BFPFFT_F16_BFP && img_dtype != BFPFFT_F16_NAIVE)
     return BFPFFT_ERR_UNSUPPORTED;
   if (rc_layout != 0 && rc_layout != 1) return BFPFFT_ERR_INVALID_ARG;
-  float2* tw = nullptr;
-  int st = get_twiddles(l, &tw);
+  bfp::RowArgs a;
+  int st = row_args(l, &a);
   if (st != BFPFFT_OK) return st;
   if (fault("launch")) return BFPFFT_ERR_CUDA;
-  bfp::RowArgs a{};
   a.in = rc;
   a.out = img;
-  a.tw = tw;
   a.h = static_cast<const float2*>(ha);
   a.lines = n_rg;                                   // one line per range column
   a.in_stride = rc_layout == 0 ? n_rg : n_az;       // [n_az][n_rg] column vs [n_rg][n_az] row
   a.out_stride = n_rg;                              // image is [n_az][n_rg]
-  a.in_scale = 1.f;
-  a.out_scale = 1.f;
   const bool naive = img_dtype == BFPFFT_F16_NAIVE;
   cudaError_t e = bfp::launch_sar(l, rc_dtype == BFPFFT_F16_BFP, img_dtype != BFPFFT_F32, naive,
                                   /*tload=*/rc_layout == 0, /*tstore=*/true, a,

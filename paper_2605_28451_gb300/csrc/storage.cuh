@@ -26,6 +26,7 @@ template <> struct Storage<float2> {
   static constexpr int kBytes = 8;
   __device__ __forceinline__ static float2 load(const float2* p) { return __ldcs(p); }
   __device__ __forceinline__ static void store(float2* p, float2 v) { __stcs(p, v); }
+  __device__ __forceinline__ static float2 load_smem(const float2* p) { return *p; }
 };
 
 template <> struct Storage<__half2> {
@@ -38,6 +39,7 @@ template <> struct Storage<__half2> {
     const __half2 h = __float22half2_rn(v);
     __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
   }
+  __device__ __forceinline__ static float2 load_smem(const __half2* p) { return __half22float2(*p); }
 };
 
 template <> struct Storage<Fp8x2<E4M3>> {
@@ -49,6 +51,7 @@ template <> struct Storage<Fp8x2<E4M3>> {
   __device__ __forceinline__ static void store(Fp8x2<E4M3>* p, float2 v) {
     p->bits = __nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E4M3);
   }
+  __device__ __forceinline__ static float2 load_smem(const Fp8x2<E4M3>* p) { return load(p); }
 };
 
 template <> struct Storage<Fp8x2<E5M2>> {
@@ -60,6 +63,7 @@ template <> struct Storage<Fp8x2<E5M2>> {
   __device__ __forceinline__ static void store(Fp8x2<E5M2>* p, float2 v) {
     p->bits = __nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E5M2);
   }
+  __device__ __forceinline__ static float2 load_smem(const Fp8x2<E5M2>* p) { return load(p); }
 };
 
 // Naive FP16 output of an unshifted inverse (Section III-B): the unnormalised

@@ -1,0 +1,66 @@
+"""Run one hot-path case a few times, for profiling under ncu.
+
+    python -m paper_2605_28451_gb300.profile_cases <case> [--batch B] [--reps R]
+
+Cases (FP16-BFP unless named otherwise, N = 4096 lines):
+  fft16_fwd, fft16_inv   batched transform, batch B (default 16384: 256 MiB in)
+  fft32_fwd              the same in FP32 storage
+  range16                range compression of a 1024 x 4096 complex64 scene to FP16, corner-turned
+  image16                range + azimuth compression of a 4096 x 4096 scene to an FP16 image
+Inputs are seeded and synthetic.  Nothing is checked here; the tests do that.
+"""
+
+from __future__ import annotations
+
+import argparse
+
+import torch
+
+from . import bfpfft as B
+from . import build, synth
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case")
+    ap.add_argument("--batch", type=int, default=16384)
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+    build.build()
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream()
+    n = 4096
+    g = torch.Generator(device=dev).manual_seed(0)
+    if args.case in ("fft16_fwd", "fft16_inv", "fft32_fwd"):
+        dtype = B.F32 if args.case == "fft32_fwd" else B.F16_BFP
+        direction = B.INVERSE if args.case == "fft16_inv" else B.FORWARD
+        x = torch.randn((args.batch, n, 2), device=dev, generator=g)
+        x = x if dtype == B.F32 else x.to(torch.float16)
+        y = torch.empty_like(x)
+        plan = B.bfpfft_plan_create(n, args.batch, dtype, direction)
+        for _ in range(args.reps):
+            B.bfpfft_exec(plan, x, y, stream)
+    elif args.case in ("range16", "image16"):
+        n_az = 1024 if args.case == "range16" else n
+        sc = synth.point_target_scene(n_az, n)
+        raw = torch.from_numpy(sc.raw.astype("complex64")).to(dev)
+        hr = torch.empty(n, dtype=torch.complex64, device=dev)
+        ha = torch.empty(n_az, dtype=torch.complex64, device=dev)
+        B.sar_make_filter(torch.from_numpy(sc.ref_range.astype("complex64")).to(dev), n, False, hr, stream)
+        B.sar_make_filter(torch.from_numpy(sc.ref_azimuth.astype("complex64")).to(dev), n_az, True, ha, stream)
+        rc = torch.empty((n, n_az, 2), dtype=torch.float16, device=dev)
+        img = torch.empty((n_az, n, 2), dtype=torch.float16, device=dev)
+        for _ in range(args.reps):
+            B.sar_range_compress(raw, B.F32, rc, B.F16_BFP, hr, n_az, n, True, stream)
+            if args.case == "image16":
+                B.sar_azimuth_compress(rc, B.F16_BFP, 1, img, B.F16_BFP, ha, n_az, n, stream)
+    else:
+        raise SystemExit(f"unknown case {args.case}")
+    torch.cuda.synchronize()
+    status = B.bfpfft_device_status()
+    if status != B.OK:
+        raise SystemExit(f"device status {status}")
+
+
+if __name__ == "__main__":
+    main()

@@ -44,7 +44,7 @@ def run_fft(x_stored: np.ndarray, dtype: int, direction: int, inplace=False):
 
 @pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("batch", [1, 7])
-def test_f32_forward_and_inverse(n, batch):
+def test_f32_forward_and_inverse(n, batch, rows_variant):
     x = storage_round(synth.complex_gaussian(batch, n, seed=n + batch), B.F32)
     got = run_fft(x, B.F32, B.FORWARD)
     ref = F.fft(x)
@@ -56,9 +56,22 @@ def test_f32_forward_and_inverse(n, batch):
     assert metrics.rel_l2(ref_i, got_i) <= 1e-6
 
 
-@pytest.mark.parametrize("n", SIZES)
-@pytest.mark.parametrize("batch", [3, 33])
-def test_f16_bfp_forward_and_inverse(n, batch):
+@pytest.fixture(params=["pipelined", "plain"])
+def rows_variant(request, monkeypatch):
+    """Both row-kernel variants: the bulk-copy pipelined persistent kernel
+    (default for dense rows) and the plain one-group-per-CTA kernel."""
+    if request.param == "plain":
+        monkeypatch.setenv("BFPFFT_ROWS", "plain")
+    else:
+        monkeypatch.delenv("BFPFFT_ROWS", raising=False)
+    yield request.param
+    assert B.bfpfft_device_status() == B.OK
+
+
+@pytest.mark.parametrize("n,batch", [(n, b) for n in SIZES for b in (3, 33)] + [(256, 20000), (4096, 1000)])
+def test_f16_bfp_forward_and_inverse(n, batch, rows_variant):
+    """Ragged batches; the last two cases make every persistent CTA of the
+    pipelined kernel walk several groups and end on a partial group."""
     x = storage_round(synth.complex_gaussian(batch, n, seed=100 + n + batch), B.F16_BFP)
     got = run_fft(x, B.F16_BFP, B.FORWARD)
     ref = F.fft(x)
@@ -151,7 +164,7 @@ def test_large_batch_sampled_lines():
 
 @pytest.mark.parametrize("dtype,fmt", [(B.E4M3_BFP, "e4m3"), (B.E5M2_BFP, "e5m2")])
 @pytest.mark.parametrize("n", [256, 4096])
-def test_fp8_storage_matches_oracle_rounding(dtype, fmt, n):
+def test_fp8_storage_matches_oracle_rounding(dtype, fmt, n, rows_variant):
     x = quant.round_fp8(synth.complex_gaussian(16, n, seed=n), fmt)
     plan = B.bfpfft_plan_create(n, 16, dtype, B.FORWARD)
     in_exp, out_exp = B.bfpfft_plan_scale_exp(plan)
