@@ -168,6 +168,32 @@ int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype,
 int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img, int img_dtype,
                          const void* ha, int64_t n_az, int64_t n_rg, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * FP64 metric reductions on the GPU (Section IV-B, Section VI).
+ * ------------------------------------------------------------------------- */
+
+/* Device workspace bytes bfp_sqnr_sums() needs, for any count. */
+size_t bfp_sqnr_workspace_bytes(void);
+
+/*
+ * The five FP64 sums of the scale-aligned SQNR between a reference `ref` and
+ * a test array `test`, `count` complex points each (dtypes BFPFFT_F32 or
+ * BFPFFT_F16_*; the two may differ), written to the device buffer
+ * sums_out = double[5]:
+ *   [0] sum |ref|^2   [1] sum |test|^2   [2] Re sum conj(test) ref
+ *   [3] sum |ref - test|^2   [4] number of test points with a non-finite part
+ * Non-finite test points are counted and left out of [0..3].  The aligned SQNR
+ * (optimal real scale, Section IV-B) is 10 log10([0] / ([0] - [2]^2 / [1])),
+ * the unaligned one 10 log10([0] / [3]).  The reduction is two-stage with a
+ * fixed summation order (bitwise reproducible).  workspace: caller-owned
+ * device scratch of ws_bytes >= bfp_sqnr_workspace_bytes(); its contents are
+ * overwritten.  count = 0 writes zeros.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG (NULL pointer, count < 0, workspace too small),
+ * UNSUPPORTED (dtype), MISALIGNED, CUDA.
+ */
+int bfp_sqnr_sums(const void* ref, int ref_dtype, const void* test, int test_dtype, int64_t count,
+                  void* sums_out, void* workspace, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

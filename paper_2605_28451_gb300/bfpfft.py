@@ -52,6 +52,9 @@ SIGNATURES = {
                                           ctypes.c_int, _vp]),
     "sar_azimuth_compress": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _c_int64,
                                             _c_int64, _vp]),
+    "bfp_sqnr_workspace_bytes": (ctypes.c_size_t, []),
+    "bfp_sqnr_sums": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _c_int64, _vp, _vp, ctypes.c_size_t,
+                                     _vp]),
 }
 
 _lib = None
@@ -175,3 +178,26 @@ def sar_azimuth_compress(rc, rc_dtype: int, rc_layout: int, img, img_dtype: int,
                          stream=None):
     _check(lib().sar_azimuth_compress(_ptr(rc), int(rc_dtype), int(rc_layout), _ptr(img), int(img_dtype), _ptr(ha),
                                       int(n_az), int(n_rg), _stream(stream)), "sar_azimuth_compress")
+
+
+def bfp_sqnr_workspace_bytes() -> int:
+    return int(lib().bfp_sqnr_workspace_bytes())
+
+
+def bfp_sqnr_sums(ref, ref_dtype: int, test, test_dtype: int, count: int, sums_out, workspace, ws_bytes: int,
+                  stream=None):
+    _check(lib().bfp_sqnr_sums(_ptr(ref), int(ref_dtype), _ptr(test), int(test_dtype), int(count), _ptr(sums_out),
+                               _ptr(workspace), int(ws_bytes), _stream(stream)), "bfp_sqnr_sums")
+
+
+def sqnr_from_sums(s) -> dict:
+    """Aligned / unaligned SQNR in dB from the five sums of bfp_sqnr_sums (host arithmetic on 5 numbers)."""
+    import math
+    s0, s1, s2, s3, bad = (float(v) for v in s)
+    err_aligned = s0 - s2 * s2 / s1 if s1 > 0 else s0
+    cap = 300.0
+
+    def db(num, den):
+        return cap if den <= 0 else min(cap, 10.0 * math.log10(num / den))
+    return {"aligned_db": db(s0, err_aligned), "unaligned_db": db(s0, s3), "nonfinite": int(bad),
+            "alpha": s2 / s1 if s1 > 0 else float("nan")}

@@ -29,6 +29,7 @@ SOURCES = [
     "sar_nn.cu",
     "sar_nt.cu",
     "sar_tt.cu",
+    "metrics.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -34,10 +34,12 @@
 // 8 lines as 32-byte segments and exchanges the points with the owning CTA
 // through distributed shared memory, so a transpose costs no extra HBM pass.
 //
-// Twiddles come from a per-length FP32 table W_N^i, i < N, generated on the
-// GPU in FP64 (sincospi) and rounded once -- never by recurrence, which the
-// paper identifies as the source of the ~42 dB "pure FP16" figure (Section
-// III-A).
+// Twiddles come from a per-length FP32 table generated on the GPU in FP64
+// (sincospi) and rounded once -- never by recurrence, which the paper
+// identifies as the source of the ~42 dB "pure FP16" figure (Section III-A).
+// The table is pass-major: for every pass after the first (sub-length Ns,
+// radix R) it holds W_{Ns R}^{k r} at offset (Ns - 16) + (r - 1) Ns + k,
+// r in [1, R), k in [0, Ns); N - 16 entries in all.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -96,7 +98,6 @@ struct StockhamPass {
   static constexpr int R = (N / Ns) >= 16 ? 16 : N / Ns;
   static constexpr int B = P / R;
   static constexpr bool kLast = (Ns * R == N);
-  static constexpr int kTwStride = N / (Ns * R);
 
   __device__ __forceinline__ static void run(float2 (&v)[P], const float2* __restrict__ tw,
                                              float2* __restrict__ sm, int t) {
@@ -108,8 +109,11 @@ struct StockhamPass {
 #pragma unroll
       for (int r = 0; r < R; ++r) u[r] = v[b + B * r];
       if (Ns > 1) {
+        // Pass-major table: W_{Ns R}^{k r} at (Ns - 16) + (r - 1) Ns + k, so the
+        // lanes of a warp (consecutive k) read consecutive twiddles.
+        const float2* twp = tw + (Ns - 16) + k;
 #pragma unroll
-        for (int r = 1; r < R; ++r) u[r] = cmul(u[r], __ldg(tw + k * r * kTwStride));
+        for (int r = 1; r < R; ++r) u[r] = cmul(u[r], __ldg(twp + (r - 1) * Ns));
       }
       Dft<R>::run(u);
       if (kLast) {
@@ -157,12 +161,25 @@ __device__ __forceinline__ void row_compute(float2 (&v)[kPointsPerThread], const
   line_dft<N>(v, a.tw, sm, t);
 
   if (MODE == kCompress) {
+    // Filter loads in groups of four: keeps the compiler from hoisting all
+    // sixteen next to the line (register pressure at 3 CTAs / SM).
 #pragma unroll
-    for (int m = 0; m < P; ++m) {
-      const float2 p = cmul(v[m], __ldg(a.h + t + T * m));
-      v[m] = NAIVE ? cconj(p) : cscale(cconj(p), inv_n);
+    for (int m0 = 0; m0 < P; m0 += 4) {
+      float2 h[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) h[i] = __ldg(a.h + t + T * (m0 + i));
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float2 p = cmul(v[m0 + i], h[i]);
+        v[m0 + i] = NAIVE ? cconj(p) : cscale(cconj(p), inv_n);
+      }
+      asm volatile("" ::: "memory");
     }
-    line_dft<N>(v, a.tw, sm, t);
+    // An opaque copy of t keeps the compiler from holding the first
+    // transform's address arithmetic live for reuse in the second.
+    int t2;
+    asm volatile("mov.b32 %0, %1;" : "=r"(t2) : "r"(t));
+    line_dft<N>(v, a.tw, sm, t2);
   }
   if (MODE == kInverse || MODE == kCompress) {
 #pragma unroll
@@ -274,6 +291,8 @@ fft_rows_kernel(const RowArgs a) {
 // reads overlap the butterflies.  Stores go straight from registers to HBM
 // (coalesced).  Waits are bounded: on expiry the CTA records a timeout in
 // a.status, drains its own outstanding copies (again bounded) and returns.
+constexpr size_t kTmaSmemBudget = 200 * 1024;   // leave room below the 227 KB per-CTA limit
+
 template <int N, class TIn, int STAGES>
 struct TmaLayout {
   using S = RowShape<N>;
@@ -346,7 +365,9 @@ fft_rows_tma_kernel(const RowArgs a) {
         issue(nxt, stage);
       }
     }
-    row_compute<N, MODE, NAIVE, SCALED>(v, a, sm, t);
+    int ti;   // opaque per iteration: no address arithmetic carried across the loop
+    asm volatile("mov.b32 %0, %1;" : "=r"(ti) : "r"(t));
+    row_compute<N, MODE, NAIVE, SCALED>(v, a, sm, ti);
     const long long line = grp * G + g;
     if (line < a.lines) {
       TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;
@@ -384,7 +405,7 @@ template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, bool 
           bool TSTORE = false>
 cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
   using S = RowShape<N, TLOAD || TSTORE>;
-  if constexpr (!TLOAD && !TSTORE && N >= 256) {
+  if constexpr (!TLOAD && !TSTORE && N >= 256 && TmaLayout<N, TIn, 2>::kBytes <= kTmaSmemBudget) {
     if (a.variant == 0 && a.in_stride == N && a.out_stride == N)
       return launch_rows_tma_n<N, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
   }

@@ -16,6 +16,7 @@
 
 #include "bfpfft.h"
 #include "launch.h"
+#include "metrics.h"
 
 namespace {
 
@@ -44,14 +45,23 @@ int cuda_status(cudaError_t e) {
   return BFPFFT_ERR_CUDA;
 }
 
-// W_N^i = exp(-2 pi i / N * i) for i < N, evaluated in FP64 and rounded once.
+// Pass-major twiddle table of a length-n transform (radix-16 passes, the last
+// one radix n / Ns): for every pass after the first, with sub-length Ns and
+// radix R, entry (Ns - 16) + (r - 1) Ns + k holds W_{Ns R}^{k r} =
+// exp(-2 pi i k r / (Ns R)) for r in [1, R), k in [0, Ns).  Evaluated in FP64
+// (sincospi of an exact dyadic fraction) and rounded once to FP32.
 __global__ void twiddle_kernel(float2* tw, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
-    double s, c;
-    sincospi(-2.0 * double(i) / double(n), &s, &c);
-    tw[i] = make_float2(float(c), float(s));
-  }
+  if (i >= n - 16) return;
+  int ns = 16;
+  while (ns * 16 < n && i >= ns * 16 - 16) ns *= 16;
+  const int radix = (n / ns) >= 16 ? 16 : n / ns;
+  const int local = i - (ns - 16);
+  const int r = local / ns + 1;
+  const int k = local - (r - 1) * ns;
+  double s, c;
+  sincospi(-2.0 * double(k * r) / double(ns * radix), &s, &c);
+  tw[i] = make_float2(float(c), float(s));
 }
 
 // Per-device, per-length twiddle tables, created on first use and kept for
@@ -350,6 +360,28 @@ int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img,
   cudaError_t e = bfp::launch_sar(l, rc_dtype == BFPFFT_F16_BFP, img_dtype != BFPFFT_F32, naive,
                                   /*tload=*/rc_layout == 0, /*tstore=*/true, a,
                                   static_cast<cudaStream_t>(stream));
+  return cuda_status(e);
+}
+
+size_t bfp_sqnr_workspace_bytes(void) { return bfp::kMetricWorkspaceBytes; }
+
+int bfp_sqnr_sums(const void* ref, int ref_dtype, const void* test, int test_dtype, int64_t count, void* sums_out,
+                  void* workspace, size_t ws_bytes, void* stream) {
+  if (count < 0) return BFPFFT_ERR_INVALID_ARG;
+  if (ref_dtype != BFPFFT_F32 && ref_dtype != BFPFFT_F16_BFP && ref_dtype != BFPFFT_F16_NAIVE)
+    return BFPFFT_ERR_UNSUPPORTED;
+  if (test_dtype != BFPFFT_F32 && test_dtype != BFPFFT_F16_BFP && test_dtype != BFPFFT_F16_NAIVE)
+    return BFPFFT_ERR_UNSUPPORTED;
+  if (ref == nullptr || test == nullptr || sums_out == nullptr || workspace == nullptr)
+    return BFPFFT_ERR_INVALID_ARG;
+  if (!aligned16(ref) || !aligned16(test) || !aligned16(sums_out) || !aligned16(workspace))
+    return BFPFFT_ERR_MISALIGNED;
+  if (ws_bytes < size_t(bfp::metric_blocks(count)) * bfp::kMetricSums * sizeof(double))
+    return BFPFFT_ERR_INVALID_ARG;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
+  cudaError_t e = bfp::launch_sqnr_sums(ref, ref_dtype != BFPFFT_F32, test, test_dtype != BFPFFT_F32, count,
+                                        static_cast<double*>(workspace), static_cast<double*>(sums_out),
+                                        static_cast<cudaStream_t>(stream));
   return cuda_status(e);
 }
 
