@@ -169,6 +169,41 @@ int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img,
                          const void* ha, int64_t n_az, int64_t n_rg, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Entropy phase autofocus with a hand-written adjoint.
+ *
+ * The paper has no autofocus section; this builds standard SAR entropy
+ * autofocus on its azimuth compression (Fig. 1).  For range-compressed data
+ * rc[r][n] (range bin r, pulse n) and a per-pulse phase correction phi[n]:
+ *   v = rc . exp(-j phi[n]),  I[r] = IDFT(DFT(v[r]) . Ha),  q = |I|^2,
+ *   S = sum q,  E = -sum (q/S) ln(q/S) = ln S - (1/S) sum q ln q,
+ *   dE/dphi[n] = 2 sum_r Im( conj((A^H G)[r][n]) v[r][n] ),
+ *   G = -(ln(q/S) + E) / S . I,  A^H = IDFT(DFT(.) . conj(Ha)).
+ * The image is never stored: the gradient pass recomputes the forward
+ * transforms.  FP32 arithmetic; FP64 sums across CTAs.
+ * Layout: rc is [n_rg][n_az] (each row one range bin's azimuth line, as written
+ * by sar_range_compress with transpose_out = 1), dtype BFPFFT_F32 or
+ * BFPFFT_F16_BFP; phi float[n_az], Ha float2[n_az] (device).
+ * stats_out: device double[4] = {S, sum q ln q, E, ln S}.
+ * workspace: caller-owned device scratch of at least
+ * sar_autofocus_workspace_bytes(n_az) bytes (overwritten).
+ * Supported n_az: powers of two in [256, 8192].  Asynchronous on `stream`.
+ * Errors: INVALID_ARG (NULL, n_rg < 0, workspace too small), UNSUPPORTED,
+ * MISALIGNED, CUDA.
+ * ------------------------------------------------------------------------- */
+
+/* Workspace bytes for the autofocus calls at azimuth length n_az (0 if unsupported). */
+size_t sar_autofocus_workspace_bytes(int64_t n_az);
+
+/* Entropy only (forward pass): writes stats_out. */
+int sar_autofocus_entropy(const void* rc, int rc_dtype, const float* phi, const void* ha, int64_t n_az,
+                          int64_t n_rg, void* stats_out, void* workspace, size_t ws_bytes, void* stream);
+
+/* Entropy (stats_out) and its gradient grad_out = dE/dphi (device float[n_az]). */
+int sar_autofocus_grad(const void* rc, int rc_dtype, const float* phi, const void* ha, int64_t n_az,
+                       int64_t n_rg, float* grad_out, void* stats_out, void* workspace, size_t ws_bytes,
+                       void* stream);
+
+/* ---------------------------------------------------------------------------
  * FP64 metric reductions on the GPU (Section IV-B, Section VI).
  * ------------------------------------------------------------------------- */
 

@@ -52,6 +52,11 @@ SIGNATURES = {
                                           ctypes.c_int, _vp]),
     "sar_azimuth_compress": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _c_int64,
                                             _c_int64, _vp]),
+    "sar_autofocus_workspace_bytes": (ctypes.c_size_t, [_c_int64]),
+    "sar_autofocus_entropy": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_int64, _c_int64, _vp, _vp,
+                                             ctypes.c_size_t, _vp]),
+    "sar_autofocus_grad": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_int64, _c_int64, _vp, _vp, _vp,
+                                          ctypes.c_size_t, _vp]),
     "bfp_sqnr_workspace_bytes": (ctypes.c_size_t, []),
     "bfp_sqnr_sums": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _c_int64, _vp, _vp, ctypes.c_size_t,
                                      _vp]),
@@ -201,3 +206,21 @@ def sqnr_from_sums(s) -> dict:
         return cap if den <= 0 else min(cap, 10.0 * math.log10(num / den))
     return {"aligned_db": db(s0, err_aligned), "unaligned_db": db(s0, s3), "nonfinite": int(bad),
             "alpha": s2 / s1 if s1 > 0 else float("nan")}
+
+
+def sar_autofocus_workspace_bytes(n_az: int) -> int:
+    return int(lib().sar_autofocus_workspace_bytes(int(n_az)))
+
+
+def sar_autofocus_entropy(rc, rc_dtype: int, phi, ha, n_az: int, n_rg: int, stats_out, workspace, ws_bytes: int,
+                          stream=None):
+    _check(lib().sar_autofocus_entropy(_ptr(rc), int(rc_dtype), _ptr(phi), _ptr(ha), int(n_az), int(n_rg),
+                                       _ptr(stats_out), _ptr(workspace), int(ws_bytes), _stream(stream)),
+           "sar_autofocus_entropy")
+
+
+def sar_autofocus_grad(rc, rc_dtype: int, phi, ha, n_az: int, n_rg: int, grad_out, stats_out, workspace,
+                       ws_bytes: int, stream=None):
+    _check(lib().sar_autofocus_grad(_ptr(rc), int(rc_dtype), _ptr(phi), _ptr(ha), int(n_az), int(n_rg),
+                                    _ptr(grad_out), _ptr(stats_out), _ptr(workspace), int(ws_bytes),
+                                    _stream(stream)), "sar_autofocus_grad")

@@ -30,6 +30,7 @@ SOURCES = [
     "sar_nt.cu",
     "sar_tt.cu",
     "metrics.cu",
+    "autofocus.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

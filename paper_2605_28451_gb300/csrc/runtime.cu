@@ -17,6 +17,7 @@
 #include "bfpfft.h"
 #include "launch.h"
 #include "metrics.h"
+#include "autofocus.h"
 
 namespace {
 
@@ -361,6 +362,47 @@ int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img,
                                   /*tload=*/rc_layout == 0, /*tstore=*/true, a,
                                   static_cast<cudaStream_t>(stream));
   return cuda_status(e);
+}
+
+size_t sar_autofocus_workspace_bytes(int64_t n_az) {
+  const int l = log2_exact(n_az);
+  if (l < bfp::kAfMinLog2 || l > bfp::kAfMaxLog2) return 0;
+  return bfp::af_workspace_bytes(n_az);
+}
+
+static int autofocus_common(const void* rc, int rc_dtype, const float* phi, const void* ha, int64_t n_az,
+                            int64_t n_rg, float* grad_out, void* stats_out, void* workspace, size_t ws_bytes,
+                            void* stream) {
+  if (n_rg < 0) return BFPFFT_ERR_INVALID_ARG;
+  const int l = log2_exact(n_az);
+  if (l < bfp::kAfMinLog2 || l > bfp::kAfMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
+  if (rc_dtype != BFPFFT_F32 && rc_dtype != BFPFFT_F16_BFP) return BFPFFT_ERR_UNSUPPORTED;
+  if (rc == nullptr || phi == nullptr || ha == nullptr || stats_out == nullptr || workspace == nullptr)
+    return BFPFFT_ERR_INVALID_ARG;
+  if (!aligned16(rc) || !aligned16(ha) || !aligned16(stats_out) || !aligned16(workspace) ||
+      (grad_out != nullptr && !aligned16(grad_out)))
+    return BFPFFT_ERR_MISALIGNED;
+  if (ws_bytes < bfp::af_workspace_bytes(n_az)) return BFPFFT_ERR_INVALID_ARG;
+  bfp::RowArgs a;
+  int st = row_args(l, &a);
+  if (st != BFPFFT_OK) return st;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
+  cudaError_t e = bfp::launch_autofocus(l, rc_dtype == BFPFFT_F16_BFP, rc, phi, static_cast<const float2*>(ha),
+                                        a.tw, n_rg, static_cast<double*>(stats_out), grad_out, workspace,
+                                        static_cast<cudaStream_t>(stream));
+  return cuda_status(e);
+}
+
+int sar_autofocus_entropy(const void* rc, int rc_dtype, const float* phi, const void* ha, int64_t n_az,
+                          int64_t n_rg, void* stats_out, void* workspace, size_t ws_bytes, void* stream) {
+  return autofocus_common(rc, rc_dtype, phi, ha, n_az, n_rg, nullptr, stats_out, workspace, ws_bytes, stream);
+}
+
+int sar_autofocus_grad(const void* rc, int rc_dtype, const float* phi, const void* ha, int64_t n_az,
+                       int64_t n_rg, float* grad_out, void* stats_out, void* workspace, size_t ws_bytes,
+                       void* stream) {
+  if (grad_out == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  return autofocus_common(rc, rc_dtype, phi, ha, n_az, n_rg, grad_out, stats_out, workspace, ws_bytes, stream);
 }
 
 size_t bfp_sqnr_workspace_bytes(void) { return bfp::kMetricWorkspaceBytes; }

@@ -187,3 +187,19 @@ def uneven_batch(lengths: np.ndarray, seed: int = 30):
     rng = np.random.default_rng(seed)
     data = rng.standard_normal(total) + 1j * rng.standard_normal(total)
     return data, offsets
+
+
+def range_compressed_scene(n_az: int, n_rg: int, aperture: int, targets, noise_std: float = 0.05,
+                           seed: int = 2) -> np.ndarray:
+    """Ideally range-compressed echoes [n_az][n_rg]: target (eta, r, a) puts
+    a * s_a[eta' - eta + L_a/2] into range bin r over its aperture, plus complex
+    AWGN of standard deviation noise_std per component."""
+    sa = azimuth_chirp(aperture)
+    rc = np.zeros((n_az, n_rg), dtype=np.complex128)
+    for eta, r, a in targets:
+        e0 = eta - aperture // 2
+        es, ee = max(e0, 0), min(e0 + aperture, n_az)
+        rc[es:ee, r] += a * sa[es - e0:ee - e0]
+    rng = np.random.default_rng(seed)
+    rc += noise_std * (rng.standard_normal((n_az, n_rg)) + 1j * rng.standard_normal((n_az, n_rg)))
+    return rc
