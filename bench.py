@@ -258,6 +258,9 @@ def run_ours(args):
     # ---- SAR: range compression 1024 x 4096 and the 4096 x 4096 image ---------------
     sar = _bench_sar(B, torch, dev, stream)
 
+    # ---- autofocus: entropy + adjoint gradient on a 4096 x 4096 FP16 scene -----------
+    autofocus = _bench_autofocus(B, torch, dev, stream)
+
     # ---- end to end through the C ABI with host buffers ---------------------------
     e2e = _bench_e2e(B, torch, dev, stream, x16, fwd16, inv16, flops_step, args)
 
@@ -302,6 +305,7 @@ def run_ours(args):
             "inverse_launch_ms": round(inv_avg, 5),
             "table2_batch256_l2_flushed": {"gflops": round(gflops_small, 1), "ms_median": round(t_small, 5)},
             "sar": sar,
+            "autofocus_4096x4096": autofocus,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks.summary(),
@@ -357,6 +361,43 @@ def _bench_sar(B, torch, dev, stream):
             out[name]["naive_has_nonfinite"] = bool((~torch.isfinite(naive)).any().item())
         del raw, rc, img, flush
     return out
+
+
+def _bench_autofocus(B, torch, dev, stream):
+    """One autofocus gradient step (entropy pass + adjoint pass) on 4096 range
+    bins x 4096 pulses of FP16 range-compressed data."""
+    from paper_2605_28451_gb300 import autofocus as GA
+    from paper_2605_28451_gb300 import synth
+    n = 4096
+    g = torch.Generator(device=dev).manual_seed(5)
+    rc = torch.randn((n, n, 2), device=dev, generator=g).to(torch.float16)
+    ref = synth.centred_reference(synth.azimuth_chirp(1024), n)
+    ha = torch.empty(n, dtype=torch.complex64, device=dev)
+    B.sar_make_filter(torch.from_numpy(ref.astype("complex64")).to(dev), n, True, ha, stream)
+    phi = torch.from_numpy(synth.phase_error(n).astype("float32")).to(dev)
+    ws = GA.Workspace(n, dev)
+    grad = torch.empty(n, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        B.sar_autofocus_grad(rc, B.F16_BFP, phi, ha, n, n, grad, ws.stats, ws.buf, ws.bytes, stream)
+
+    for _ in range(3):
+        step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for i in range(10):
+        flush.fill_(i & 0xFF)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    t = statistics.median(ts)
+    # entropy pass: 2 transforms per range bin; gradient pass: 4 (recomputed forward + adjoint)
+    flops = 6 * n * 5 * n * 12
+    return {"ms_median_l2_flushed": round(t, 4), "gflops": round(flops / (t * 1e-3) / 1e9, 1),
+            "alg_gbs": round(3 * 4 * n * n / (t * 1e-3) / 1e9, 1), "dtype": "FP16-BFP rc, FP32 arithmetic"}
 
 
 def _bench_e2e(B, torch, dev, stream, x16, fwd, inv, flops_step, args):
