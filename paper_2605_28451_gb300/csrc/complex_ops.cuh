@@ -14,8 +14,43 @@
 
 namespace bfp {
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Packed FP32 (sm_100-family f32x2): one instruction adds or subtracts both
+// components of a complex value held as a 64-bit register pair.
+#ifndef BFP_F32X2
+#define BFP_F32X2 1
+#endif
+
+__device__ __forceinline__ unsigned long long as_u64(float2 a) { return *reinterpret_cast<unsigned long long*>(&a); }
+__device__ __forceinline__ float2 as_f2(unsigned long long u) { return *reinterpret_cast<float2*>(&u); }
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+#if BFP_F32X2
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(as_u64(a)), "l"(as_u64(b)));
+  return as_f2(r);
+#else
+  return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+#if BFP_F32X2
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(as_u64(a)), "l"(as_u64(b)));
+  return as_f2(r);
+#else
+  return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
+// Both components times the same real factor.
+__device__ __forceinline__ float2 cmul_real2(float2 a, float s) {
+#if BFP_F32X2
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(as_u64(a)), "l"(as_u64(make_float2(s, s))));
+  return as_f2(r);
+#else
+  return make_float2(a.x * s, a.y * s);
+#endif
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -30,21 +65,24 @@ constexpr float kS1 = 0.38268343236508977173f;   // sin(pi/8)
 constexpr float kR2 = 0.70710678118654752440f;   // sqrt(1/2)
 
 // (x + iy) * W16^2 = sqrt(1/2) * ((x + y) + i (y - x))
-__device__ __forceinline__ float2 mul_w16_2(float2 a) { return make_float2((a.x + a.y) * kR2, (a.y - a.x) * kR2); }
+__device__ __forceinline__ float2 mul_w16_2(float2 a) { return cmul_real2(make_float2(a.x + a.y, a.y - a.x), kR2); }
 // (x + iy) * W16^6 = sqrt(1/2) * ((y - x) - i (x + y))
-__device__ __forceinline__ float2 mul_w16_6(float2 a) { return make_float2((a.y - a.x) * kR2, -(a.x + a.y) * kR2); }
+__device__ __forceinline__ float2 mul_w16_6(float2 a) { return cmul_real2(make_float2(a.y - a.x, -a.x - a.y), kR2); }
 __device__ __forceinline__ float2 mul_w16_1(float2 a) { return cmul(a, make_float2(kC1, -kS1)); }
 __device__ __forceinline__ float2 mul_w16_3(float2 a) { return cmul(a, make_float2(kS1, -kC1)); }
 __device__ __forceinline__ float2 mul_w16_9(float2 a) { return cmul(a, make_float2(-kC1, kS1)); }
 
 // 4-point forward DFT in place: (a0, a1, a2, a3) -> (X0, X1, X2, X3).
+// e = -i (a1 - a3) is formed with two scalar subtractions straight into the
+// swapped order, so every other step is one packed add or subtract.
 __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
   const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
-  const float2 t2 = cadd(a1, a3), t3 = cmul_mi(csub(a1, a3));
+  const float2 t2 = cadd(a1, a3);
+  const float2 e = make_float2(a1.y - a3.y, a3.x - a1.x);
   a0 = cadd(t0, t2);
   a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
+  a1 = cadd(t1, e);
+  a3 = csub(t1, e);
 }
 
 template <int R> struct Dft;
