@@ -229,6 +229,34 @@ size_t bfp_sqnr_workspace_bytes(void);
 int bfp_sqnr_sums(const void* ref, int ref_dtype, const void* test, int test_dtype, int64_t count,
                   void* sums_out, void* workspace, size_t ws_bytes, void* stream);
 
+/*
+ * bfp_sqnr_sums_noalloc -- the sums of bfp_sqnr_sums without any workspace.
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot allocate device memory: for example a radar processing chain that
+ * fixes its whole device-memory budget at start-up and forbids allocation
+ * afterwards for predictable latency, or a host application whose own memory
+ * pool owns every device byte and has no way to lend the library a
+ * workspace.  The caller passes only inputs and the output.
+ *
+ * Arguments and results are those of bfp_sqnr_sums (ref, test: `count`
+ * complex points, dtypes BFPFFT_F32 or BFPFFT_F16_*; sums_out: device
+ * double[5]).  The partial sums live in a fixed 160 KB array inside the
+ * library that every GPU loading the library keeps until the process exits;
+ * this call allocates nothing (no cudaMalloc, no cudaFree).
+ * Limit: count <= bfp_sqnr_sums_noalloc_max_count() = 16,777,216 points;
+ * larger counts return BFPFFT_ERR_UNSUPPORTED without launching anything.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (different
+ * streams, no ordering between them) race and may return wrong sums; calls
+ * ordered on one stream are safe.  Stage 1 rewrites every partial the call
+ * reads, so leftovers from an earlier call never leak into a result.
+ * Errors: INVALID_ARG, UNSUPPORTED (count or dtype), MISALIGNED, CUDA.
+ */
+long long bfp_sqnr_sums_noalloc_max_count(void);
+int bfp_sqnr_sums_noalloc(const void* ref, int ref_dtype, const void* test, int test_dtype, int64_t count,
+                          void* sums_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

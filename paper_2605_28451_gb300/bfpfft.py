@@ -58,6 +58,8 @@ SIGNATURES = {
     "sar_autofocus_grad": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_int64, _c_int64, _vp, _vp, _vp,
                                           ctypes.c_size_t, _vp]),
     "bfp_sqnr_workspace_bytes": (ctypes.c_size_t, []),
+    "bfp_sqnr_sums_noalloc_max_count": (ctypes.c_longlong, []),
+    "bfp_sqnr_sums_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _c_int64, _vp, _vp]),
     "bfp_sqnr_sums": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _c_int64, _vp, _vp, ctypes.c_size_t,
                                      _vp]),
 }
@@ -224,3 +226,13 @@ def sar_autofocus_grad(rc, rc_dtype: int, phi, ha, n_az: int, n_rg: int, grad_ou
     _check(lib().sar_autofocus_grad(_ptr(rc), int(rc_dtype), _ptr(phi), _ptr(ha), int(n_az), int(n_rg),
                                     _ptr(grad_out), _ptr(stats_out), _ptr(workspace), int(ws_bytes),
                                     _stream(stream)), "sar_autofocus_grad")
+
+
+def bfp_sqnr_sums_noalloc_max_count() -> int:
+    return int(lib().bfp_sqnr_sums_noalloc_max_count())
+
+
+def bfp_sqnr_sums_noalloc(ref, ref_dtype: int, test, test_dtype: int, count: int, sums_out, stream=None):
+    """bfp_sqnr_sums with the library's built-in scratch: no workspace, no allocation."""
+    _check(lib().bfp_sqnr_sums_noalloc(_ptr(ref), int(ref_dtype), _ptr(test), int(test_dtype), int(count),
+                                       _ptr(sums_out), _stream(stream)), "bfp_sqnr_sums_noalloc")

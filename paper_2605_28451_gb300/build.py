@@ -31,6 +31,7 @@ SOURCES = [
     "sar_tt.cu",
     "metrics.cu",
     "autofocus.cu",
+    "metrics_noalloc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

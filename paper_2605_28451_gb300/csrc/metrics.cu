@@ -104,6 +104,16 @@ int metric_blocks(long long count) {
   return int(b);
 }
 
+cudaError_t launch_sqnr_sums_blocks(const void* ref, bool ref16, const void* test, bool test16, long long count,
+                                    double* partials, int blocks, double* out, cudaStream_t s) {
+  if (ref16) {
+    if (test16) return launch_typed<__half2, __half2>(ref, test, count, partials, blocks, out, s);
+    return launch_typed<__half2, float2>(ref, test, count, partials, blocks, out, s);
+  }
+  if (test16) return launch_typed<float2, __half2>(ref, test, count, partials, blocks, out, s);
+  return launch_typed<float2, float2>(ref, test, count, partials, blocks, out, s);
+}
+
 cudaError_t launch_sqnr_sums(const void* ref, bool ref16, const void* test, bool test16, long long count,
                              double* partials, double* out, cudaStream_t s) {
   const int blocks = metric_blocks(count);

@@ -17,4 +17,9 @@ int metric_blocks(long long count);
 cudaError_t launch_sqnr_sums(const void* ref, bool ref16, const void* test, bool test16, long long count,
                              double* partials, double* out, cudaStream_t s);
 
+// The same reduction with an explicit stage-1 block count (1 .. any); partials
+// must hold blocks * kMetricSums doubles.
+cudaError_t launch_sqnr_sums_blocks(const void* ref, bool ref16, const void* test, bool test16, long long count,
+                                    double* partials, int blocks, double* out, cudaStream_t s);
+
 }  // namespace bfp

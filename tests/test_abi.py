@@ -19,7 +19,7 @@ def declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names += re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(\w+)\s*\(", text, flags=re.M)
+        names += re.findall(r"^\s*(?:[A-Za-z_]\w*[\s\*]+)+(\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 
