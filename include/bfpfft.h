@@ -24,7 +24,7 @@
  * - Arithmetic is FP32 in registers and shared memory for every dtype; the
  *   dtype fixes only the storage format in HBM (Section VI's "FP16 storage /
  *   FP32 compute" mode).  Twiddle tables are generated on the GPU in FP64.
- * - Supported lengths: powers of two with 16 <= n <= 16384 for the row
+ * - Supported lengths: powers of two with 16 <= n <= 65536 for the row
  *   transforms; anything else returns BFPFFT_ERR_UNSUPPORTED.
  */
 #ifndef BFPFFT_H_
@@ -81,7 +81,7 @@ const char* bfpfft_error_string(int status);
  * batch may be 0 (exec is then a no-op).  The plan allocates its twiddle
  * table on the current device; it must be executed on that device.
  * Errors: INVALID_ARG (out NULL, batch < 0, unknown dtype or direction),
- * UNSUPPORTED (n not a power of two in [16, 16384]), OOM, CUDA.
+ * UNSUPPORTED (n not a power of two in [16, 65536]), OOM, CUDA.
  * On error *out is set to NULL.
  */
 int bfpfft_plan_create(bfpfft_plan* out, int64_t n, int64_t batch, int dtype, int direction);

@@ -45,6 +45,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "async_copy.cuh"
 #include "complex_ops.cuh"
 #include "storage.cuh"
@@ -64,7 +66,17 @@ struct RowArgs {
   float in_scale;          // applied to loaded values (FP8 block exponent)
   float out_scale;         // applied before the final rounding (FP8 block exponent)
   int* status;             // device status word (bounded waits record timeouts here)
-  int variant;             // 0: bulk-copy pipelined rows where possible, 1: plain rows
+  int variant;             // RowVariant
+};
+
+// Row-kernel variants for dense rows of length <= 4096 (chosen by
+// BFPFFT_ROWS or the tuner): bulk-copy pipelined persistent kernel or plain
+// one-group-per-CTA kernel, with an FP32 or FP16 shared-memory exchange in
+// one buffer or two (ping-pong).  FP16 exchanges apply to FP16 storage only;
+// anything not applicable falls back to kRowsTma.
+enum RowVariant : int {
+  kRowsTma = 0, kRowsPlain = 1, kRowsPlainPP = 2, kRowsPlainH = 3, kRowsPlainHPP = 4,
+  kRowsTmaPP = 5, kRowsTmaH = 6, kRowsTmaHPP = 7
 };
 
 constexpr int kPointsPerThread = 16;
@@ -91,6 +103,98 @@ struct RowShape {
   static constexpr int kMinBlocks = kThreads >= 1024 ? 1 : (kThreads >= 512 ? 1 : BFP_MIN_BLOCKS);
 };
 
+// Where a line lives between passes.  Every policy offers load / store of
+// point i for exchange number Q (Q = 0 after the first pass, 1 after the
+// second, ...), a barrier after the stores (sync) and a barrier before the
+// next stores may overwrite what was just loaded (sync_war).
+//
+//   LocalXch          this CTA's shared memory, FP32, one buffer
+//   LocalXchPP        FP32, two buffers used alternately: the next pass writes
+//                     the other buffer, so no barrier is needed before it
+//   LocalXchH         FP16 (half2) in shared memory: the paper's own layout
+//                     (Section V: half2 threadgroup memory); every exchange is
+//                     an FP16 storage point, so the inverse relies on the 1/N
+//                     shift (Eq. 1) to keep intermediates in range
+//   LocalXchHPP       FP16, two buffers
+//   ClusterXch<SLAB>  a line spread over the CTAs of a thread-block cluster,
+//                     SLAB points per CTA, through distributed shared memory
+struct LocalXch {
+  float2* sm;
+  template <int Q> __device__ __forceinline__ float2 load(int i) const { return sm[pad16(i)]; }
+  template <int Q> __device__ __forceinline__ void store(int i, float2 v) const { sm[pad16(i)] = v; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ void sync_war() const { __syncthreads(); }
+};
+
+template <int LINE>   // padded slots of one buffer
+struct LocalXchPP {
+  float2* sm;
+  template <int Q> __device__ __forceinline__ float2 load(int i) const { return sm[(Q & 1) * LINE + pad16(i)]; }
+  template <int Q> __device__ __forceinline__ void store(int i, float2 v) const { sm[(Q & 1) * LINE + pad16(i)] = v; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ void sync_war() const {}
+};
+
+struct LocalXchH {
+  __half2* sm;
+  template <int Q> __device__ __forceinline__ float2 load(int i) const { return __half22float2(sm[pad16(i)]); }
+  template <int Q> __device__ __forceinline__ void store(int i, float2 v) const { sm[pad16(i)] = __float22half2_rn(v); }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ void sync_war() const { __syncthreads(); }
+};
+
+template <int LINE>
+struct LocalXchHPP {
+  __half2* sm;
+  template <int Q> __device__ __forceinline__ float2 load(int i) const {
+    return __half22float2(sm[(Q & 1) * LINE + pad16(i)]);
+  }
+  template <int Q> __device__ __forceinline__ void store(int i, float2 v) const {
+    sm[(Q & 1) * LINE + pad16(i)] = __float22half2_rn(v);
+  }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ void sync_war() const {}
+};
+
+template <int SLAB>
+struct ClusterXch {
+  float2* base;   // this CTA's slab (same offset in every CTA of the cluster)
+  __device__ __forceinline__ float2* at(int i) const {
+    return cooperative_groups::this_cluster().map_shared_rank(base + pad16(i % SLAB), i / SLAB);
+  }
+  template <int Q> __device__ __forceinline__ float2 load(int i) const { return *at(i); }
+  template <int Q> __device__ __forceinline__ void store(int i, float2 v) const { *at(i) = v; }
+  __device__ __forceinline__ void sync() const { cooperative_groups::this_cluster().sync(); }
+  __device__ __forceinline__ void sync_war() const { cooperative_groups::this_cluster().sync(); }
+};
+
+__host__ __device__ constexpr int ilog16(int ns) { return ns <= 1 ? 0 : 1 + ilog16(ns / 16); }
+
+// Exchange variants of the single-CTA row kernels.
+enum XchVariant : int { kXchF32 = 0, kXchF32PP = 1, kXchF16 = 2, kXchF16PP = 3 };
+
+template <int N, int XV> struct XchSel;
+template <int N> struct XchSel<N, kXchF32> {
+  static constexpr size_t kLineBytes = size_t(N > 16 ? pad16(N) : 0) * sizeof(float2);
+  __device__ __forceinline__ static LocalXch make(unsigned char* p) { return LocalXch{reinterpret_cast<float2*>(p)}; }
+};
+template <int N> struct XchSel<N, kXchF32PP> {
+  static constexpr size_t kLineBytes = 2 * size_t(pad16(N)) * sizeof(float2);
+  __device__ __forceinline__ static LocalXchPP<pad16(N)> make(unsigned char* p) {
+    return LocalXchPP<pad16(N)>{reinterpret_cast<float2*>(p)};
+  }
+};
+template <int N> struct XchSel<N, kXchF16> {
+  static constexpr size_t kLineBytes = size_t(pad16(N)) * sizeof(__half2);
+  __device__ __forceinline__ static LocalXchH make(unsigned char* p) { return LocalXchH{reinterpret_cast<__half2*>(p)}; }
+};
+template <int N> struct XchSel<N, kXchF16PP> {
+  static constexpr size_t kLineBytes = 2 * size_t(pad16(N)) * sizeof(__half2);
+  __device__ __forceinline__ static LocalXchHPP<pad16(N)> make(unsigned char* p) {
+    return LocalXchHPP<pad16(N)>{reinterpret_cast<__half2*>(p)};
+  }
+};
+
 template <int N, int Ns>
 struct StockhamPass {
   static constexpr int P = kPointsPerThread;
@@ -98,9 +202,10 @@ struct StockhamPass {
   static constexpr int R = (N / Ns) >= 16 ? 16 : N / Ns;
   static constexpr int B = P / R;
   static constexpr bool kLast = (Ns * R == N);
+  static constexpr int kQ = ilog16(Ns);   // exchange number written by this pass
 
-  __device__ __forceinline__ static void run(float2 (&v)[P], const float2* __restrict__ tw,
-                                             float2* __restrict__ sm, int t) {
+  template <class X>
+  __device__ __forceinline__ static void run(float2 (&v)[P], const float2* __restrict__ tw, const X& x, int t) {
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int j = t + T * b;
@@ -122,31 +227,45 @@ struct StockhamPass {
       } else {
         const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) sm[pad16(base + r * Ns)] = u[r];
+        for (int r = 0; r < R; ++r) x.template store<kQ>(base + r * Ns, u[r]);
       }
     }
     if constexpr (!kLast) {
-      __syncthreads();
+      x.sync();
 #pragma unroll
-      for (int m = 0; m < P; ++m) v[m] = sm[pad16(t + T * m)];
-      __syncthreads();
-      StockhamPass<N, Ns * R>::run(v, tw, sm, t);
+      for (int m = 0; m < P; ++m) v[m] = x.template load<kQ>(t + T * m);
+      x.sync_war();
+      StockhamPass<N, Ns * R>::run(v, tw, x, t);
     }
   }
 };
 
 // Full forward DFT of the line held in v (v[m] = x[t + T m] -> X[t + T m]).
+template <int N, class X>
+__device__ __forceinline__ void line_dft(float2 (&v)[kPointsPerThread], const float2* __restrict__ tw,
+                                         const X& x, int t) {
+  StockhamPass<N, 1>::run(v, tw, x, t);
+}
+
 template <int N>
 __device__ __forceinline__ void line_dft(float2 (&v)[kPointsPerThread], const float2* __restrict__ tw,
                                          float2* __restrict__ sm, int t) {
-  StockhamPass<N, 1>::run(v, tw, sm, t);
+  StockhamPass<N, 1>::run(v, tw, LocalXch{sm}, t);
 }
 
 // The per-line chain between load and store: block exponents, the inverse's
 // conj * 1/N (Eq. 1), the transform(s), the filter multiply of compress mode,
 // the final conjugate, and the naive FP16 rounding of Section III-B.
+template <int N, int MODE, bool NAIVE, bool SCALED, class X = LocalXch>
+__device__ __forceinline__ void row_compute_x(float2 (&v)[kPointsPerThread], const RowArgs& a, const X& xch, int t);
+
 template <int N, int MODE, bool NAIVE, bool SCALED>
 __device__ __forceinline__ void row_compute(float2 (&v)[kPointsPerThread], const RowArgs& a, float2* sm, int t) {
+  row_compute_x<N, MODE, NAIVE, SCALED>(v, a, LocalXch{sm}, t);
+}
+
+template <int N, int MODE, bool NAIVE, bool SCALED, class X>
+__device__ __forceinline__ void row_compute_x(float2 (&v)[kPointsPerThread], const RowArgs& a, const X& xch, int t) {
   constexpr int P = kPointsPerThread, T = N / P;
   const float inv_n = 1.0f / float(N);
   if (SCALED) {
@@ -158,7 +277,7 @@ __device__ __forceinline__ void row_compute(float2 (&v)[kPointsPerThread], const
     for (int m = 0; m < P; ++m) v[m] = NAIVE ? cconj(v[m]) : cscale(cconj(v[m]), inv_n);
   }
 
-  line_dft<N>(v, a.tw, sm, t);
+  line_dft<N>(v, a.tw, xch, t);
 
   if (MODE == kCompress) {
     // Filter loads in groups of four: keeps the compiler from hoisting all
@@ -179,7 +298,7 @@ __device__ __forceinline__ void row_compute(float2 (&v)[kPointsPerThread], const
     // transform's address arithmetic live for reuse in the second.
     int t2;
     asm volatile("mov.b32 %0, %1;" : "=r"(t2) : "r"(t));
-    line_dft<N>(v, a.tw, sm, t2);
+    line_dft<N>(v, a.tw, xch, t2);
   }
   if (MODE == kInverse || MODE == kCompress) {
 #pragma unroll
@@ -214,10 +333,11 @@ __device__ __forceinline__ void cluster_barrier() {
   }
 }
 
-template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, bool TLOAD, bool TSTORE>
+template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, bool TLOAD, bool TSTORE, int XV = kXchF32>
 __global__ void __launch_bounds__(RowShape<N, TLOAD || TSTORE>::kThreads,
                                   RowShape<N, TLOAD || TSTORE>::kMinBlocks)
 fft_rows_kernel(const RowArgs a) {
+  static_assert(XV == kXchF32 || (!TLOAD && !TSTORE), "corner turns stage lines in FP32");
   using S = RowShape<N, TLOAD || TSTORE>;
   constexpr int P = S::P, T = S::T;
   extern __shared__ float2 smem_rows[];
@@ -258,7 +378,12 @@ fft_rows_kernel(const RowArgs a) {
 #pragma unroll
     for (int m = 0; m < P; ++m) v[m] = make_float2(0.f, 0.f);
   }
-  row_compute<N, MODE, NAIVE, SCALED>(v, a, sm, t);
+  if constexpr (XV == kXchF32) {
+    row_compute<N, MODE, NAIVE, SCALED>(v, a, sm, t);
+  } else {
+    unsigned char* base = reinterpret_cast<unsigned char*>(smem_rows) + g * XchSel<N, XV>::kLineBytes;
+    row_compute_x<N, MODE, NAIVE, SCALED>(v, a, XchSel<N, XV>::make(base), t);
+  }
 
   if constexpr (TSTORE) {
     // Stage the line, then scatter slabs of all cluster lines as segments.
@@ -293,28 +418,28 @@ fft_rows_kernel(const RowArgs a) {
 // a.status, drains its own outstanding copies (again bounded) and returns.
 constexpr size_t kTmaSmemBudget = 200 * 1024;   // leave room below the 227 KB per-CTA limit
 
-template <int N, class TIn, int STAGES>
+template <int N, class TIn, int STAGES, int XV = kXchF32>
 struct TmaLayout {
   using S = RowShape<N>;
   static constexpr size_t kStageBytes = size_t(S::G) * N * sizeof(TIn);
   static constexpr size_t kBarBytes = 128;
-  static constexpr size_t kXchBytes = size_t(S::G) * S::kSmemPerLine * sizeof(float2);
+  static constexpr size_t kXchBytes = size_t(S::G) * XchSel<N, XV>::kLineBytes;
   static constexpr size_t kBytes = kBarBytes + STAGES * kStageBytes + kXchBytes;
 };
 
-template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, int STAGES>
+template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, int STAGES, int XV = kXchF32>
 __global__ void __launch_bounds__(RowShape<N>::kThreads, RowShape<N>::kMinBlocks)
 fft_rows_tma_kernel(const RowArgs a) {
   using S = RowShape<N>;
-  using L = TmaLayout<N, TIn, STAGES>;
+  using L = TmaLayout<N, TIn, STAGES, XV>;
   constexpr int P = S::P, T = S::T, G = S::G;
   extern __shared__ __align__(128) unsigned char smem_tma[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_tma);
   unsigned char* stages = smem_tma + L::kBarBytes;
-  float2* xch = reinterpret_cast<float2*>(stages + STAGES * L::kStageBytes);
+  unsigned char* xch = stages + STAGES * L::kStageBytes;
   const int g = threadIdx.x / T;
   const int t = threadIdx.x - g * T;
-  float2* sm = xch + g * S::kSmemPerLine;
+  unsigned char* xg = xch + g * XchSel<N, XV>::kLineBytes;
   const long long groups = (a.lines + G - 1) / G;
   const TIn* src = static_cast<const TIn*>(a.in);
 
@@ -367,7 +492,7 @@ fft_rows_tma_kernel(const RowArgs a) {
     }
     int ti;   // opaque per iteration: no address arithmetic carried across the loop
     asm volatile("mov.b32 %0, %1;" : "=r"(ti) : "r"(t));
-    row_compute<N, MODE, NAIVE, SCALED>(v, a, sm, ti);
+    row_compute_x<N, MODE, NAIVE, SCALED>(v, a, XchSel<N, XV>::make(xg), ti);
     const long long line = grp * G + g;
     if (line < a.lines) {
       TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;
@@ -377,12 +502,12 @@ fft_rows_tma_kernel(const RowArgs a) {
   }
 }
 
-template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED>
+template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, int XV = kXchF32>
 cudaError_t launch_rows_tma_n(const RowArgs& a, cudaStream_t stream) {
   using S = RowShape<N>;
   constexpr int kStages = 2;
-  using L = TmaLayout<N, TIn, kStages>;
-  auto kern = fft_rows_tma_kernel<N, TIn, TOut, MODE, NAIVE, SCALED, kStages>;
+  using L = TmaLayout<N, TIn, kStages, XV>;
+  auto kern = fft_rows_tma_kernel<N, TIn, TOut, MODE, NAIVE, SCALED, kStages, XV>;
   static int grid_cap = 0;   // resident CTAs on this device (computed once)
   if (grid_cap == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::kBytes));
@@ -401,12 +526,135 @@ cudaError_t launch_rows_tma_n(const RowArgs& a, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+
+// Lines longer than one CTA's share (N >= 8192): a line spans a thread-block
+// cluster of C CTAs of CTA_T threads, each CTA holding a slab of N / C points
+// of every exchange in its shared memory; the passes read and write the other
+// CTAs' slabs through distributed shared memory and synchronise with cluster
+// barriers.  Each line is still read from and written to HBM exactly once.
+template <int N>
+struct ClusterShape {
+  static constexpr int CTA_T = N <= 32768 ? 256 : 512;
+  static constexpr int T = N / kPointsPerThread;   // threads per line
+  static constexpr int C = T / CTA_T;              // CTAs per line (cluster size, <= 8)
+  static constexpr int SLAB = N / C;               // points per CTA
+  static constexpr size_t kSmemBytes = size_t(pad16(SLAB)) * sizeof(float2);
+  static constexpr int kMinBlocks = CTA_T >= 512 ? 1 : BFP_MIN_BLOCKS;
+  static_assert(C >= 2 && C <= 8, "cluster size");
+};
+
+template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED>
+__global__ void __launch_bounds__(ClusterShape<N>::CTA_T, ClusterShape<N>::kMinBlocks)
+fft_cluster_kernel(const RowArgs a) {
+  using S = ClusterShape<N>;
+  constexpr int P = kPointsPerThread, T = S::T;
+  extern __shared__ float2 smem_cl[];
+  auto cluster = cooperative_groups::this_cluster();
+  const int rank = int(cluster.block_rank());
+  const long long line = blockIdx.x / S::C;
+  const int t = rank * S::CTA_T + threadIdx.x;
+  const ClusterXch<S::SLAB> xch{smem_cl};
+  float2 v[P];
+  const TIn* in = static_cast<const TIn*>(a.in) + line * a.in_stride + t;
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = Storage<TIn>::load(in + T * m);
+  // Every CTA of the cluster must be running before its slab is written.
+  cluster.sync();
+  row_compute_x<N, MODE, NAIVE, SCALED>(v, a, xch, t);
+  // The last exchange ended with a cluster barrier after its reads: no CTA
+  // touches another's slab from here on.
+  TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;
+#pragma unroll
+  for (int m = 0; m < P; ++m) Storage<TOut>::store(out + T * m, v[m]);
+}
+
+template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED>
+cudaError_t launch_cluster_n(const RowArgs& a, cudaStream_t stream) {
+  using S = ClusterShape<N>;
+  auto kern = fft_cluster_kernel<N, TIn, TOut, MODE, NAIVE, SCALED>;
+  static bool configured = false;
+  if (!configured) {
+    if (S::kSmemBytes > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::kSmemBytes));
+      if (e != cudaSuccess) return e;
+    }
+    configured = true;
+  }
+  if (a.lines <= 0) return cudaSuccess;
+  const long long grid = a.lines * S::C;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(S::CTA_T);
+  cfg.dynamicSmemBytes = S::kSmemBytes;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = S::C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// Plain (one group per CTA, no prefetch) row kernel with an exchange variant.
+template <int N, class TIn, class TOut, int MODE, bool NAIVE, int XV>
+cudaError_t launch_rows_plain_x(const RowArgs& a, cudaStream_t stream) {
+  using S = RowShape<N>;
+  constexpr size_t kBytes = size_t(S::G) * XchSel<N, XV>::kLineBytes;
+  auto kern = fft_rows_kernel<N, TIn, TOut, MODE, NAIVE, false, false, false, XV>;
+  static bool configured = false;
+  if (!configured) {
+    if (kBytes > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBytes));
+      if (e != cudaSuccess) return e;
+    }
+    configured = true;
+  }
+  if (a.lines <= 0) return cudaSuccess;
+  const long long grid = (a.lines + S::G - 1) / S::G;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  kern<<<dim3(unsigned(grid)), dim3(S::kThreads), kBytes, stream>>>(a);
+  return cudaGetLastError();
+}
+
 template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, bool TLOAD = false,
           bool TSTORE = false>
 cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
+  if constexpr (!TLOAD && !TSTORE && N >= 8192) {
+    return launch_cluster_n<N, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
+  } else {
   using S = RowShape<N, TLOAD || TSTORE>;
+  // Exchange variants for dense forward / inverse rows (FP16 exchange only
+  // for FP16 storage): see RowVariant.
+  if constexpr (!TLOAD && !TSTORE && !SCALED && MODE != kCompress && N >= 256 && N <= 4096 &&
+                std::is_same<TIn, TOut>::value) {
+    if (a.in_stride == N && a.out_stride == N) {
+      constexpr bool kHalf = std::is_same<TIn, __half2>::value;
+      switch (a.variant) {
+        case kRowsPlainPP: return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF32PP>(a, stream);
+        case kRowsTmaPP: return launch_rows_tma_n<N, TIn, TOut, MODE, NAIVE, SCALED, kXchF32PP>(a, stream);
+        case kRowsPlainH:
+          if constexpr (kHalf) return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF16>(a, stream);
+          break;
+        case kRowsPlainHPP:
+          if constexpr (kHalf) return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF16PP>(a, stream);
+          break;
+        case kRowsTmaH:
+          if constexpr (kHalf) return launch_rows_tma_n<N, TIn, TOut, MODE, NAIVE, SCALED, kXchF16>(a, stream);
+          break;
+        case kRowsTmaHPP:
+          if constexpr (kHalf) return launch_rows_tma_n<N, TIn, TOut, MODE, NAIVE, SCALED, kXchF16PP>(a, stream);
+          break;
+        default: break;
+      }
+    }
+  }
   if constexpr (!TLOAD && !TSTORE && N >= 256 && TmaLayout<N, TIn, 2>::kBytes <= kTmaSmemBudget) {
-    if (a.variant == 0 && a.in_stride == N && a.out_stride == N)
+    if (a.variant != kRowsPlain && a.in_stride == N && a.out_stride == N)
       return launch_rows_tma_n<N, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
   }
   auto kern = fft_rows_kernel<N, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>;
@@ -442,9 +690,10 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
     kern<<<dim3(unsigned(grid)), dim3(S::kThreads), S::kSmemBytes, stream>>>(a);
   }
   return cudaGetLastError();
+  }
 }
 
-// Dispatch on log2 N in [4, 14].
+// Dispatch on log2 N in [4, 16] (N >= 32768 only for dense rows).
 template <class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, bool TLOAD = false, bool TSTORE = false>
 cudaError_t launch_rows(int log2n, const RowArgs& a, cudaStream_t stream) {
   switch (log2n) {
@@ -459,6 +708,12 @@ cudaError_t launch_rows(int log2n, const RowArgs& a, cudaStream_t stream) {
     case 12: return launch_rows_n<4096, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
     case 13: return launch_rows_n<8192, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
     case 14: return launch_rows_n<16384, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
+    case 15:
+      if constexpr (!TLOAD && !TSTORE) return launch_cluster_n<32768, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
+      else return cudaErrorInvalidValue;
+    case 16:
+      if constexpr (!TLOAD && !TSTORE) return launch_cluster_n<65536, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
+      else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

@@ -22,7 +22,8 @@
 namespace {
 
 constexpr int kMinLog2 = 4;
-constexpr int kMaxLog2 = 14;
+constexpr int kMaxLog2 = 16;       // plain transforms; SAR and autofocus lines stop earlier
+constexpr int kSarMaxLog2 = 14;
 
 int log2_exact(int64_t n) {
   if (n <= 0 || (n & (n - 1)) != 0) return -1;
@@ -122,10 +123,18 @@ int get_status_word(int** out) {
   return BFPFFT_OK;
 }
 
-// Kernel variant: BFPFFT_ROWS=plain forces the non-pipelined row kernel.
+// Row-kernel variant from BFPFFT_ROWS (tma, plain, pp, h16, h16pp, tma_pp,
+// tma_h16, tma_h16pp); unset or unknown -> the pipelined kernel.
 int rows_variant() {
   const char* v = std::getenv("BFPFFT_ROWS");
-  return (v != nullptr && std::strcmp(v, "plain") == 0) ? 1 : 0;
+  if (v == nullptr) return bfp::kRowsTma;
+  static const struct { const char* name; int code; } kNames[] = {
+      {"tma", bfp::kRowsTma},         {"plain", bfp::kRowsPlain},    {"pp", bfp::kRowsPlainPP},
+      {"h16", bfp::kRowsPlainH},      {"h16pp", bfp::kRowsPlainHPP}, {"tma_pp", bfp::kRowsTmaPP},
+      {"tma_h16", bfp::kRowsTmaH},    {"tma_h16pp", bfp::kRowsTmaHPP}};
+  for (const auto& k : kNames)
+    if (std::strcmp(v, k.name) == 0) return k.code;
+  return bfp::kRowsTma;
 }
 
 // Common RowArgs set-up: twiddles, status word, unit scales.
@@ -309,7 +318,7 @@ int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype,
                        int64_t n_az, int64_t n_rg, int transpose_out, void* stream) {
   if (n_az < 0) return BFPFFT_ERR_INVALID_ARG;
   const int l = log2_exact(n_rg);
-  if (l < bfp::kSarMinLog2 || l > kMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
+  if (l < bfp::kSarMinLog2 || l > kSarMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
   if (n_az == 0) return BFPFFT_OK;
   if (raw == nullptr || out == nullptr || hr == nullptr) return BFPFFT_ERR_INVALID_ARG;
   if (!aligned16(raw) || !aligned16(out) || !aligned16(hr)) return BFPFFT_ERR_MISALIGNED;
@@ -339,7 +348,7 @@ int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img,
                          const void* ha, int64_t n_az, int64_t n_rg, void* stream) {
   if (n_rg < 0) return BFPFFT_ERR_INVALID_ARG;
   const int l = log2_exact(n_az);
-  if (l < bfp::kSarMinLog2 || l > kMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
+  if (l < bfp::kSarMinLog2 || l > kSarMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
   if (n_rg == 0) return BFPFFT_OK;
   if (rc == nullptr || img == nullptr || ha == nullptr) return BFPFFT_ERR_INVALID_ARG;
   if (!aligned16(rc) || !aligned16(img) || !aligned16(ha)) return BFPFFT_ERR_MISALIGNED;

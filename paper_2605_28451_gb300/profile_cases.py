@@ -25,7 +25,9 @@ def main():
     ap.add_argument("case")
     ap.add_argument("--batch", type=int, default=16384)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--time", action="store_true", help="print the median ms per rep (CUDA events)")
     args = ap.parse_args()
+    times = []
     build.build()
     dev = torch.device("cuda:0")
     stream = torch.cuda.current_stream()
@@ -39,7 +41,12 @@ def main():
         y = torch.empty_like(x)
         plan = B.bfpfft_plan_create(n, args.batch, dtype, direction)
         for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
             B.bfpfft_exec(plan, x, y, stream)
+            e1.record(stream)
+            times.append((e0, e1))
+        bytes_per_rep = args.batch * n * (16 if dtype == B.F32 else 8)
     elif args.case in ("range16", "image16"):
         n_az = 1024 if args.case == "range16" else n
         sc = synth.point_target_scene(n_az, n)
@@ -51,12 +58,23 @@ def main():
         rc = torch.empty((n, n_az, 2), dtype=torch.float16, device=dev)
         img = torch.empty((n_az, n, 2), dtype=torch.float16, device=dev)
         for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
             B.sar_range_compress(raw, B.F32, rc, B.F16_BFP, hr, n_az, n, True, stream)
             if args.case == "image16":
                 B.sar_azimuth_compress(rc, B.F16_BFP, 1, img, B.F16_BFP, ha, n_az, n, stream)
+            e1.record(stream)
+            times.append((e0, e1))
+        bytes_per_rep = n_az * n * (12 if args.case == "range16" else 20)
     else:
         raise SystemExit(f"unknown case {args.case}")
     torch.cuda.synchronize()
+    if args.time and times:
+        import os
+        import statistics
+        ms = statistics.median(a.elapsed_time(b) for a, b in times[1:] or times)
+        print(f"{args.case} variant={os.environ.get('BFPFFT_ROWS', 'default')} ms={ms:.5f} "
+              f"alg_GBps={bytes_per_rep / (ms * 1e-3) / 1e9:.1f}")
     status = B.bfpfft_device_status()
     if status != B.OK:
         raise SystemExit(f"device status {status}")

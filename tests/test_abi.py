@@ -44,7 +44,7 @@ def test_version_and_error_strings(lib):
     assert B.error_string(99) == "unknown status"
 
 
-@pytest.mark.parametrize("n", [0, 8, 12, 100, 32768, 65536, 1 << 20])
+@pytest.mark.parametrize("n", [0, 8, 12, 100, 131072, 1 << 20])
 def test_unsupported_lengths(lib, n):
     with pytest.raises(B.BfpfftError) as e:
         B.bfpfft_plan_create(n, 4, B.F16_BFP, B.FORWARD)
