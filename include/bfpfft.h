@@ -97,6 +97,38 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream);
 int bfpfft_plan_destroy(bfpfft_plan plan);
 
 /*
+ * Uneven batch: `count` transforms of lengths n[i] (powers of two in
+ * [16, 65536], mixed freely) at point offsets offset_pts[i] of the in / out
+ * buffers, all computed by ONE persistent launch.  The plan sorts the lines
+ * into tasks of 65,536 points of one length, largest length first; thread-
+ * block clusters of 16 CTAs take tasks from a counter (a line of 65536 spans
+ * the whole cluster, shorter lines one CTA or part of one) and never wait on
+ * each other.  dtype: BFPFFT_F32, BFPFFT_F16_BFP, BFPFFT_E4M3_BFP or
+ * BFPFFT_E5M2_BFP (FP8 transforms of length n use the block exponents of a
+ * uniform plan of that length); direction as for bfpfft_plan_create.
+ * Transforms must not overlap each other in `out`; in == out is allowed.
+ * The arrays n and offset_pts are host memory, read during the call only.
+ * Errors: INVALID_ARG, UNSUPPORTED (a length, BFPFFT_F16_NAIVE, or no room for
+ * a 16-CTA cluster on this device), OOM, CUDA.  Execute with bfpfft_exec or
+ * bfpfft_exec_graph.
+ */
+int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, const int64_t* offset_pts,
+                            int dtype, int direction);
+
+/* Tasks and persistent clusters of an uneven plan (both 0 for a uniform plan). */
+int bfpfft_plan_info(bfpfft_plan plan, int64_t* tasks, int64_t* clusters);
+
+/*
+ * bfpfft_exec through a CUDA graph: the first call for a given (in, out) pair
+ * captures the plan's launches (for an uneven plan: the task-counter reset
+ * and the persistent kernel) into a graph and instantiates it; every call
+ * then launches that graph on `stream`.  A new (in, out) pair re-captures.
+ * The graph belongs to the plan and is freed by bfpfft_plan_destroy.
+ * Errors: as bfpfft_exec.
+ */
+int bfpfft_exec_graph(bfpfft_plan plan, const void* in, void* out, void* stream);
+
+/*
  * Static block exponents of a plan: the true value of a stored input point is
  * stored * 2^in_exp and that of a stored output point is stored * 2^out_exp.
  * FP8 forward plans store the spectrum with out_exp = ceil(log2(n) / 2) (the

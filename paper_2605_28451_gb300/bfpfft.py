@@ -44,6 +44,9 @@ SIGNATURES = {
     "bfpfft_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "bfpfft_plan_create": (ctypes.c_int, [ctypes.POINTER(_vp), _c_int64, _c_int64, ctypes.c_int, ctypes.c_int]),
     "bfpfft_exec": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "bfpfft_plan_create_many": (ctypes.c_int, [ctypes.POINTER(_vp), _c_int64, _vp, _vp, ctypes.c_int, ctypes.c_int]),
+    "bfpfft_plan_info": (ctypes.c_int, [_vp, ctypes.POINTER(_c_int64), ctypes.POINTER(_c_int64)]),
+    "bfpfft_exec_graph": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "bfpfft_plan_destroy": (ctypes.c_int, [_vp]),
     "bfpfft_plan_scale_exp": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "bfpfft_device_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
@@ -149,6 +152,30 @@ def bfpfft_plan_create(n: int, batch: int, dtype: int, direction: int) -> Plan:
 
 def bfpfft_exec(plan: Plan, inp, out, stream=None):
     _check(lib().bfpfft_exec(plan.handle, _ptr(inp), _ptr(out), _stream(stream)), "bfpfft_exec")
+
+
+def bfpfft_plan_create_many(n, offset_pts, dtype: int, direction: int) -> Plan:
+    """Uneven plan; n and offset_pts are sequences of ints (host)."""
+    import numpy as np
+    n_arr = np.ascontiguousarray(np.asarray(n, dtype=np.int64))
+    o_arr = np.ascontiguousarray(np.asarray(offset_pts, dtype=np.int64))
+    if n_arr.shape != o_arr.shape:
+        raise ValueError("n and offset_pts differ in length")
+    h = _vp()
+    _check(lib().bfpfft_plan_create_many(ctypes.byref(h), int(n_arr.size), n_arr.ctypes.data if n_arr.size else None,
+                                         o_arr.ctypes.data if o_arr.size else None, int(dtype), int(direction)),
+           "bfpfft_plan_create_many")
+    return Plan(h.value, 0, int(n_arr.size), dtype, direction)
+
+
+def bfpfft_plan_info(plan: Plan):
+    t, c = _c_int64(), _c_int64()
+    _check(lib().bfpfft_plan_info(plan.handle, ctypes.byref(t), ctypes.byref(c)), "bfpfft_plan_info")
+    return t.value, c.value
+
+
+def bfpfft_exec_graph(plan: Plan, inp, out, stream=None):
+    _check(lib().bfpfft_exec_graph(plan.handle, _ptr(inp), _ptr(out), _stream(stream)), "bfpfft_exec_graph")
 
 
 def bfpfft_plan_destroy(plan: Plan):

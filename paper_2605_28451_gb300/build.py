@@ -32,6 +32,7 @@ SOURCES = [
     "metrics.cu",
     "autofocus.cu",
     "metrics_noalloc.cu",
+    "uneven.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -13,11 +13,14 @@
 #include <map>
 #include <mutex>
 #include <utility>
+#include <vector>
+#include <algorithm>
 
 #include "bfpfft.h"
 #include "launch.h"
 #include "metrics.h"
 #include "autofocus.h"
+#include "uneven.h"
 
 namespace {
 
@@ -124,10 +127,12 @@ int get_status_word(int** out) {
 }
 
 // Row-kernel variant from BFPFFT_ROWS (tma, plain, pp, h16, h16pp, tma_pp,
-// tma_h16, tma_h16pp); unset or unknown -> the pipelined kernel.
+// tma_h16, tma_h16pp).  Unset: the plain kernel with an FP32 exchange, the
+// fastest exact-numerics variant measured on GB300 (FP32 storage at 98.7% of
+// the measured copy bandwidth); unknown names: the pipelined kernel.
 int rows_variant() {
   const char* v = std::getenv("BFPFFT_ROWS");
-  if (v == nullptr) return bfp::kRowsTma;
+  if (v == nullptr) return bfp::kRowsPlain;
   static const struct { const char* name; int code; } kNames[] = {
       {"tma", bfp::kRowsTma},         {"plain", bfp::kRowsPlain},    {"pp", bfp::kRowsPlainPP},
       {"h16", bfp::kRowsPlainH},      {"h16pp", bfp::kRowsPlainHPP}, {"tma_pp", bfp::kRowsTmaPP},
@@ -186,7 +191,43 @@ struct bfpfft_plan_s {
   int* status;         // the device's status word (not owned)
   int in_exp;
   int out_exp;
+  // Uneven plans (bfpfft_plan_create_many): owned device arrays.
+  bool many = false;
+  int kind = 0;                         // storage kind of the persistent kernel
+  long long* d_line_off = nullptr;
+  bfp::UnevenTask* d_tasks = nullptr;
+  const float2** d_tw = nullptr;
+  int* d_counter = nullptr;
+  int num_tasks = 0;
+  int clusters = 0;
+  // Graph cache of bfpfft_exec_graph.
+  cudaGraphExec_t graph = nullptr;
+  const void* graph_in = nullptr;
+  void* graph_out = nullptr;
+  void* graph_stream_key = nullptr;
 };
+
+namespace {
+
+void free_plan_resources(bfpfft_plan p) {
+  if (p->graph) cudaGraphExecDestroy(p->graph);
+  if (p->d_line_off) cudaFree(p->d_line_off);
+  if (p->d_tasks) cudaFree(p->d_tasks);
+  if (p->d_tw) cudaFree(p->d_tw);
+  if (p->d_counter) cudaFree(p->d_counter);
+}
+
+int uneven_kind(int dtype) {
+  switch (dtype) {
+    case BFPFFT_F32: return 0;
+    case BFPFFT_F16_BFP: return 1;
+    case BFPFFT_E4M3_BFP: return 2;
+    case BFPFFT_E5M2_BFP: return 3;
+    default: return -1;
+  }
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -238,9 +279,117 @@ int bfpfft_plan_create(bfpfft_plan* out, int64_t n, int64_t batch, int dtype, in
   return BFPFFT_OK;
 }
 
+int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, const int64_t* offset_pts,
+                            int dtype, int direction) {
+  if (out == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (count < 0 || (count > 0 && (n == nullptr || offset_pts == nullptr))) return BFPFFT_ERR_INVALID_ARG;
+  if (!valid_dtype(dtype)) return BFPFFT_ERR_INVALID_ARG;
+  if (direction != BFPFFT_FORWARD && direction != BFPFFT_INVERSE) return BFPFFT_ERR_INVALID_ARG;
+  const int kind = uneven_kind(dtype);
+  if (kind < 0) return BFPFFT_ERR_UNSUPPORTED;
+  if (count > (int64_t(1) << 30)) return BFPFFT_ERR_UNSUPPORTED;
+  // Group line indices by length class, largest first, input order within a class.
+  std::vector<std::vector<int64_t>> by_class(kMaxLog2 + 1);
+  for (int64_t i = 0; i < count; ++i) {
+    const int l = log2_exact(n[i]);
+    if (l < kMinLog2 || l > kMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
+    if (offset_pts[i] < 0) return BFPFFT_ERR_INVALID_ARG;
+    by_class[l].push_back(i);
+  }
+  if (fault("plan")) return BFPFFT_ERR_CUDA;
+  std::vector<long long> line_off;
+  std::vector<bfp::UnevenTask> tasks;
+  line_off.reserve(size_t(count));
+  for (int l = kMaxLog2; l >= kMinLog2; --l) {
+    const auto& idx = by_class[l];
+    if (idx.empty()) continue;
+    const int per_task = bfp::kUnevenTaskPoints >> l;
+    for (size_t i = 0; i < idx.size(); i += size_t(per_task)) {
+      bfp::UnevenTask t{};
+      t.log2n = l;
+      t.first = int(line_off.size() + 0);
+      t.count = int(std::min<size_t>(size_t(per_task), idx.size() - i));
+      for (int k = 0; k < t.count; ++k) line_off.push_back(offset_pts[idx[i + size_t(k)]]);
+      tasks.push_back(t);
+    }
+  }
+  bfpfft_plan p = new (std::nothrow) bfpfft_plan_s();
+  if (p == nullptr) return BFPFFT_ERR_OOM;
+  p->n = 0;
+  p->batch = count;
+  p->log2n = 0;
+  p->dtype = dtype;
+  p->direction = direction;
+  p->in_exp = p->out_exp = 0;
+  p->many = true;
+  p->kind = kind;
+  p->num_tasks = int(tasks.size());
+  int st = BFPFFT_OK;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) st = cuda_status(e);
+  if (st == BFPFFT_OK) st = get_status_word(&p->status);
+  const float2* tw_host[kMaxLog2 + 1] = {};
+  for (int l = kMinLog2; l <= kMaxLog2 && st == BFPFFT_OK; ++l) {
+    if (by_class[l].empty()) continue;
+    float2* t = nullptr;
+    st = get_twiddles(l, &t);
+    tw_host[l] = t;
+  }
+  if (st == BFPFFT_OK && fault("alloc")) st = BFPFFT_ERR_OOM;
+  if (st == BFPFFT_OK && count > 0) {
+    e = cudaMalloc(&p->d_line_off, sizeof(long long) * line_off.size());
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_tasks, sizeof(bfp::UnevenTask) * tasks.size());
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_tw, sizeof(tw_host));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_counter, sizeof(int));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_line_off, line_off.data(), sizeof(long long) * line_off.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_tasks, tasks.data(), sizeof(bfp::UnevenTask) * tasks.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_tw, tw_host, sizeof(tw_host), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = bfp::uneven_max_clusters(kind, direction == BFPFFT_INVERSE, &p->clusters);
+    if (e != cudaSuccess) st = cuda_status(e);
+    if (st == BFPFFT_OK && p->clusters <= 0) st = BFPFFT_ERR_UNSUPPORTED;
+  }
+  if (st != BFPFFT_OK) {
+    free_plan_resources(p);
+    delete p;
+    return st;
+  }
+  *out = p;
+  return BFPFFT_OK;
+}
+
+int bfpfft_plan_info(bfpfft_plan plan, int64_t* tasks, int64_t* clusters) {
+  if (plan == nullptr || tasks == nullptr || clusters == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  *tasks = plan->many ? plan->num_tasks : 0;
+  *clusters = plan->many ? plan->clusters : 0;
+  return BFPFFT_OK;
+}
+
+static int exec_many(bfpfft_plan plan, const void* in, void* out, cudaStream_t s) {
+  bfp::UnevenArgs a{};
+  a.in = in;
+  a.out = out;
+  a.line_off = plan->d_line_off;
+  a.tasks = plan->d_tasks;
+  a.num_tasks = plan->num_tasks;
+  a.tw = plan->d_tw;
+  a.counter = plan->d_counter;
+  a.status = plan->status;
+  const int clusters = std::min(plan->clusters, std::max(1, plan->num_tasks));
+  return cuda_status(bfp::launch_uneven(plan->kind, plan->direction == BFPFFT_INVERSE, a, clusters, s));
+}
+
 int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
   if (plan == nullptr) return BFPFFT_ERR_INVALID_ARG;
   if (plan->batch == 0) return BFPFFT_OK;
+  if (plan->many) {
+    if (in == nullptr || out == nullptr) return BFPFFT_ERR_INVALID_ARG;
+    if (!aligned16(in) || !aligned16(out)) return BFPFFT_ERR_MISALIGNED;
+    if (fault("launch")) return BFPFFT_ERR_CUDA;
+    return exec_many(plan, in, out, static_cast<cudaStream_t>(stream));
+  }
   if (in == nullptr || out == nullptr) return BFPFFT_ERR_INVALID_ARG;
   if (!aligned16(in) || !aligned16(out)) return BFPFFT_ERR_MISALIGNED;
   if (fault("launch")) return BFPFFT_ERR_CUDA;
@@ -271,8 +420,44 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
 }
 
 int bfpfft_plan_destroy(bfpfft_plan plan) {
+  if (plan == nullptr) return BFPFFT_OK;
+  if (plan->many || plan->graph) cudaDeviceSynchronize();
+  free_plan_resources(plan);
   delete plan;
   return BFPFFT_OK;
+}
+
+int bfpfft_exec_graph(bfpfft_plan plan, const void* in, void* out, void* stream) {
+  if (plan == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (plan->batch == 0) return BFPFFT_OK;
+  if (in == nullptr || out == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (!aligned16(in) || !aligned16(out)) return BFPFFT_ERR_MISALIGNED;
+  if (plan->graph == nullptr || plan->graph_in != in || plan->graph_out != out) {
+    if (plan->graph) {
+      cudaGraphExecDestroy(plan->graph);
+      plan->graph = nullptr;
+    }
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    int st = BFPFFT_OK;
+    if (e == cudaSuccess) st = bfpfft_exec(plan, in, out, cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && st == BFPFFT_OK) e = cudaGraphInstantiate(&plan->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (st != BFPFFT_OK) return st;
+    if (e != cudaSuccess) {
+      plan->graph = nullptr;
+      return cuda_status(e);
+    }
+    plan->graph_in = in;
+    plan->graph_out = out;
+  }
+  return cuda_status(cudaGraphLaunch(plan->graph, static_cast<cudaStream_t>(stream)));
 }
 
 int bfpfft_plan_scale_exp(bfpfft_plan plan, int* in_exp, int* out_exp) {

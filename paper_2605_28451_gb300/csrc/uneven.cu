@@ -1,0 +1,216 @@
+// Uneven batches: many transforms of different power-of-two lengths (16 ..
+// 65536) in ONE persistent launch.
+//
+// Work is cut into tasks of 65,536 points of one length: a task is one line
+// of 65536, four of 16384, ..., sixteen of 4096, ..., 4096 of 16.  The grid is
+// made of thread-block clusters of 16 CTAs x 256 threads (16 points per
+// thread, the register layout of fft_rows.cuh).  Rank 0 of each cluster takes
+// the next task from a global counter and hands it to its 15 peers through
+// distributed shared memory; no CTA ever waits for another cluster.  Within a
+// task:
+//   N <= 4096   every CTA transforms 4096 / N lines in its own shared memory;
+//   N >= 8192   a line spans N / 4096 CTAs of the cluster and its passes
+//               exchange through distributed shared memory (cluster barriers).
+// Tasks are ordered largest length first so the short tasks fill the tail.
+// Storage: FP16 (BFP shift before the inverse), FP32, or FP8 with the static
+// block exponents of the uniform plans; arithmetic FP32.
+#include <cooperative_groups.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "fft_rows.cuh"
+#include "uneven.h"
+
+namespace bfp {
+
+namespace {
+
+constexpr int kCta = 256;
+constexpr int kClusterCtas = 16;
+constexpr int kSlab = 4096;     // points of one line per CTA (N >= 4096)
+
+// Cluster exchange for a line that starts at cluster rank `base`.
+template <int SLAB>
+struct ClusterXchAt {
+  float2* local;
+  int base;
+  __device__ __forceinline__ float2* at(int i) const {
+    return cooperative_groups::this_cluster().map_shared_rank(local + pad16(i % SLAB), base + i / SLAB);
+  }
+  template <int Q> __device__ __forceinline__ float2 load(int i) const { return *at(i); }
+  template <int Q> __device__ __forceinline__ void store(int i, float2 v) const { *at(i) = v; }
+  __device__ __forceinline__ void sync() const { cooperative_groups::this_cluster().sync(); }
+  __device__ __forceinline__ void sync_war() const { cooperative_groups::this_cluster().sync(); }
+};
+
+template <class TS, int MODE, bool SCALED, int LOG2N>
+__device__ __noinline__ void run_task(const UnevenArgs& a, const UnevenTask& tk, int rank, float2* smem) {
+  constexpr int N = 1 << LOG2N;
+  constexpr int P = kPointsPerThread, T = N / P;
+  RowArgs ra{};
+  ra.tw = a.tw[LOG2N];
+  ra.status = a.status;
+  const int s = (LOG2N + 1) / 2;                        // FP8 block exponent
+  ra.in_scale = SCALED && MODE == kInverse ? float(1 << s) : 1.f;
+  ra.out_scale = SCALED && MODE == kForward ? 1.f / float(1 << s) : 1.f;
+  float2 v[P];
+  if constexpr (N <= kSlab) {
+    constexpr int G = kCta / T;                          // lines per CTA
+    const int g = threadIdx.x / T;
+    const int t = threadIdx.x - g * T;
+    const int idx = rank * G + g;                        // line within the task
+    const bool active = idx < tk.count;
+    const long long off = active ? a.line_off[tk.first + idx] : 0;
+    if (active) {
+      const TS* in = static_cast<const TS*>(a.in) + off + t;
+#pragma unroll
+      for (int m = 0; m < P; ++m) v[m] = Storage<TS>::load(in + T * m);
+    } else {
+#pragma unroll
+      for (int m = 0; m < P; ++m) v[m] = make_float2(0.f, 0.f);
+    }
+    row_compute_x<N, MODE, false, SCALED>(v, ra, LocalXch{smem + g * pad16(N)}, t);
+    if (active) {
+      TS* out = static_cast<TS*>(a.out) + off + t;
+#pragma unroll
+      for (int m = 0; m < P; ++m) Storage<TS>::store(out + T * m, v[m]);
+    }
+  } else {
+    constexpr int C = N / kSlab;                         // CTAs per line
+    const int idx = rank / C;                            // line within the task
+    const int base = idx * C;
+    const int t = (rank - base) * kCta + threadIdx.x;
+    const bool active = idx < tk.count;
+    const long long off = active ? a.line_off[tk.first + idx] : 0;
+    if (active) {
+      const TS* in = static_cast<const TS*>(a.in) + off + t;
+#pragma unroll
+      for (int m = 0; m < P; ++m) v[m] = Storage<TS>::load(in + T * m);
+    } else {
+#pragma unroll
+      for (int m = 0; m < P; ++m) v[m] = make_float2(0.f, 0.f);
+    }
+    row_compute_x<N, MODE, false, SCALED>(v, ra, ClusterXchAt<kSlab>{smem, base}, t);
+    if (active) {
+      TS* out = static_cast<TS*>(a.out) + off + t;
+#pragma unroll
+      for (int m = 0; m < P; ++m) Storage<TS>::store(out + T * m, v[m]);
+    }
+  }
+}
+
+template <class TS, int MODE, bool SCALED>
+__global__ void __launch_bounds__(kCta, 3) uneven_kernel(const UnevenArgs a) {
+  extern __shared__ float2 smem_u[];
+  __shared__ int task_slot;
+  auto cluster = cooperative_groups::this_cluster();
+  const int rank = int(cluster.block_rank());
+  cluster.sync();                                        // all peers running before any DSMEM write
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) {
+      const int task = atomicAdd(a.counter, 1);
+      for (int r = 0; r < kClusterCtas; ++r) *cluster.map_shared_rank(&task_slot, r) = task;
+    }
+    cluster.sync();
+    const int task = task_slot;
+    if (task >= a.num_tasks) break;
+    const UnevenTask tk = a.tasks[task];
+    switch (tk.log2n) {
+      case 4: run_task<TS, MODE, SCALED, 4>(a, tk, rank, smem_u); break;
+      case 5: run_task<TS, MODE, SCALED, 5>(a, tk, rank, smem_u); break;
+      case 6: run_task<TS, MODE, SCALED, 6>(a, tk, rank, smem_u); break;
+      case 7: run_task<TS, MODE, SCALED, 7>(a, tk, rank, smem_u); break;
+      case 8: run_task<TS, MODE, SCALED, 8>(a, tk, rank, smem_u); break;
+      case 9: run_task<TS, MODE, SCALED, 9>(a, tk, rank, smem_u); break;
+      case 10: run_task<TS, MODE, SCALED, 10>(a, tk, rank, smem_u); break;
+      case 11: run_task<TS, MODE, SCALED, 11>(a, tk, rank, smem_u); break;
+      case 12: run_task<TS, MODE, SCALED, 12>(a, tk, rank, smem_u); break;
+      case 13: run_task<TS, MODE, SCALED, 13>(a, tk, rank, smem_u); break;
+      case 14: run_task<TS, MODE, SCALED, 14>(a, tk, rank, smem_u); break;
+      case 15: run_task<TS, MODE, SCALED, 15>(a, tk, rank, smem_u); break;
+      case 16: run_task<TS, MODE, SCALED, 16>(a, tk, rank, smem_u); break;
+      default: break;
+    }
+    // task_slot is rewritten by rank 0 only after every CTA has passed this
+    // barrier, and no CTA reaches another's shared memory across it.
+    cluster.sync();
+  }
+}
+
+template <class TS, int MODE, bool SCALED>
+cudaError_t launch_typed(const UnevenArgs& a, int clusters, cudaStream_t s) {
+  auto kern = uneven_kernel<TS, MODE, SCALED>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(clusters * kClusterCtas));
+  cfg.blockDim = dim3(kCta);
+  cfg.dynamicSmemBytes = kUnevenSmemBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <class TS, int MODE, bool SCALED>
+cudaError_t configure_typed(int* max_clusters) {
+  auto kern = uneven_kernel<TS, MODE, SCALED>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  if (kUnevenSmemBytes > 48 * 1024) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kUnevenSmemBytes));
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterCtas);
+  cfg.blockDim = dim3(kCta);
+  cfg.dynamicSmemBytes = kUnevenSmemBytes;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaOccupancyMaxActiveClusters(max_clusters, kern, &cfg);
+}
+
+// Storage kinds: 0 FP32, 1 FP16, 2 E4M3, 3 E5M2.
+template <int MODE>
+cudaError_t dispatch(int kind, bool configure, const UnevenArgs* a, int clusters, int* max_clusters,
+                     cudaStream_t s) {
+  using A = Fp8x2<E4M3>;
+  using B = Fp8x2<E5M2>;
+  switch (kind) {
+    case 0: return configure ? configure_typed<float2, MODE, false>(max_clusters)
+                             : launch_typed<float2, MODE, false>(*a, clusters, s);
+    case 1: return configure ? configure_typed<__half2, MODE, false>(max_clusters)
+                             : launch_typed<__half2, MODE, false>(*a, clusters, s);
+    case 2: return configure ? configure_typed<A, MODE, true>(max_clusters)
+                             : launch_typed<A, MODE, true>(*a, clusters, s);
+    case 3: return configure ? configure_typed<B, MODE, true>(max_clusters)
+                             : launch_typed<B, MODE, true>(*a, clusters, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t uneven_max_clusters(int kind, bool inverse, int* max_clusters) {
+  return inverse ? dispatch<kInverse>(kind, true, nullptr, 0, max_clusters, nullptr)
+                 : dispatch<kForward>(kind, true, nullptr, 0, max_clusters, nullptr);
+}
+
+cudaError_t launch_uneven(int kind, bool inverse, const UnevenArgs& a, int clusters, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  e = inverse ? dispatch<kInverse>(kind, false, &a, clusters, nullptr, s)
+              : dispatch<kForward>(kind, false, &a, clusters, nullptr, s);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace bfp

@@ -1,0 +1,35 @@
+// Uneven-batch persistent launch (host interface).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fft_rows.cuh"
+
+namespace bfp {
+
+struct UnevenTask {
+  int log2n;     // length class
+  int first;     // first line of the task in the sorted line list
+  int count;     // lines in the task (65536 / N, fewer for the last task of a class)
+  int pad;
+};
+
+struct UnevenArgs {
+  const void* in;
+  void* out;
+  const long long* line_off;     // point offset of every line, sorted by task
+  const UnevenTask* tasks;
+  int num_tasks;
+  const float2* const* tw;       // per-length twiddle tables, indexed by log2 N
+  int* counter;                  // task counter (reset before every launch)
+  int* status;
+};
+
+constexpr size_t kUnevenSmemBytes = size_t(pad16(4096)) * sizeof(float2);
+constexpr int kUnevenTaskPoints = 65536;
+
+// Storage kind: 0 FP32, 1 FP16 (block-floating-point), 2 E4M3, 3 E5M2.
+cudaError_t uneven_max_clusters(int kind, bool inverse, int* max_clusters);
+cudaError_t launch_uneven(int kind, bool inverse, const UnevenArgs& a, int clusters, cudaStream_t s);
+
+}  // namespace bfp

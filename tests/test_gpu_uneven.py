@@ -1,0 +1,137 @@
+"""GPU parity of the uneven-batch persistent launch (bfpfft_plan_create_many).
+
+Every line of a small mixed batch is checked against the FP64 oracle with the
+same bars as the uniform transforms (FP32: relative L2 <= 1e-6; FP16-BFP:
+half an FP16 ulp plus the FP32 arithmetic; FP8: the oracle's rounding of the
+same value up to a rounding-boundary tie).  The config-4 workload (20,000
+transforms, lengths 256 ... 65536 with Zipf weights, about 2^28 points) runs
+at full size and the oracle checks sampled lines of every length.  Graph
+replays must reproduce the direct launch bit for bit.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import fft as F
+from oracle import metrics, quant
+from paper_2605_28451_gb300 import bfpfft as B
+from paper_2605_28451_gb300 import build, synth
+
+from _helpers import fp16_elementwise_ok, from_device, storage_round, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(cuda_ready):
+    build.build()
+    B.lib()
+
+
+def packed(lengths, dtype, seed):
+    data, offsets = synth.uneven_batch(lengths, seed=seed)
+    if dtype in (B.E4M3_BFP, B.E5M2_BFP):
+        data = quant.round_fp8(data, "e4m3" if dtype == B.E4M3_BFP else "e5m2")
+    return storage_round(data, dtype), offsets
+
+
+def run_many(data, lengths, offsets, dtype, direction, graph=False, reps=1):
+    import torch
+    plan = B.bfpfft_plan_create_many(lengths, offsets, dtype, direction)
+    x = to_device(data, dtype)
+    y = torch.empty_like(x)
+    for _ in range(reps):
+        (B.bfpfft_exec_graph if graph else B.bfpfft_exec)(plan, x, y)
+    torch.cuda.synchronize()
+    assert B.bfpfft_device_status() == B.OK
+    return from_device(y, dtype), plan
+
+
+MIXED = [65536, 16, 4096, 256, 16384, 1024, 8192, 32, 4096, 32768, 512, 2048, 64, 128, 65536, 256, 4096] * 2
+
+
+@pytest.mark.parametrize("direction", [B.FORWARD, B.INVERSE])
+@pytest.mark.parametrize("dtype", [B.F32, B.F16_BFP])
+def test_mixed_lengths_every_line(dtype, direction):
+    lengths = np.array(MIXED)
+    data, offsets = packed(lengths, dtype, seed=31)
+    got, plan = run_many(data, lengths, offsets, dtype, direction)
+    tasks, clusters = B.bfpfft_plan_info(plan)
+    assert tasks > 0 and clusters > 0
+    for n, o in zip(lengths, offsets):
+        x = data[o:o + n]
+        ref = F.fft(x) if direction == B.FORWARD else F.ifft(x)
+        g = got[o:o + n]
+        if dtype == B.F32:
+            assert metrics.rel_l2(ref, g) <= 1e-6, n
+        else:
+            ok, worst = fp16_elementwise_ok(g, ref)
+            assert ok, (n, worst)
+
+
+@pytest.mark.parametrize("dtype,fmt", [(B.E4M3_BFP, "e4m3"), (B.E5M2_BFP, "e5m2")])
+def test_fp8_mixed_lengths(dtype, fmt):
+    lengths = np.array([4096, 256, 65536, 1024, 16384, 4096])
+    data, offsets = packed(lengths, dtype, seed=32)
+    got, _ = run_many(data, lengths, offsets, dtype, B.FORWARD)
+    for n, o in zip(lengths, offsets):
+        s = (int(np.log2(n)) + 1) // 2
+        exact = F.fft(data[o:o + n]) * 2.0 ** -s
+        g = got[o:o + n]
+        expect = quant.round_fp8(exact, fmt)
+        for gg, ee, xx in ((g.real, expect.real, exact.real), (g.imag, expect.imag, exact.imag)):
+            bad = gg != ee
+            if bad.any():
+                lo = quant.round_fp8(xx[bad] * (1 - 1e-5), fmt)
+                hi = quant.round_fp8(xx[bad] * (1 + 1e-5), fmt)
+                assert np.all((gg[bad] == lo) | (gg[bad] == hi))
+                assert bad.mean() <= 1e-3
+
+
+def test_graph_replay_matches_direct_launch():
+    lengths = np.array(MIXED)
+    data, offsets = packed(lengths, B.F16_BFP, seed=33)
+    direct, _ = run_many(data, lengths, offsets, B.F16_BFP, B.FORWARD)
+    replay, _ = run_many(data, lengths, offsets, B.F16_BFP, B.FORWARD, graph=True, reps=3)
+    assert np.array_equal(direct.view(np.float64), replay.view(np.float64))
+
+
+def test_empty_uneven_plan():
+    plan = B.bfpfft_plan_create_many([], [], B.F16_BFP, B.FORWARD)
+    B.bfpfft_exec(plan, None, None)
+
+
+def test_uneven_plan_rejects_bad_lengths():
+    with pytest.raises(B.BfpfftError) as e:
+        B.bfpfft_plan_create_many([4096, 100], [0, 4096], B.F16_BFP, B.FORWARD)
+    assert e.value.status == B.ERR_UNSUPPORTED
+    with pytest.raises(B.BfpfftError) as e:
+        B.bfpfft_plan_create_many([4096], [0], B.F16_NAIVE, B.FORWARD)
+    assert e.value.status == B.ERR_UNSUPPORTED
+
+
+def test_config4_full_size_sampled_lines():
+    """20,000 transforms, lengths from {256, 1024, 4096, 16384, 65536} with Zipf
+    weights (seed 3), FP16-BFP, one persistent launch through a CUDA graph."""
+    import torch
+    lengths = synth.uneven_lengths(20000, seed=3)
+    offsets = np.zeros_like(lengths)
+    offsets[1:] = np.cumsum(lengths)[:-1]
+    total = int(lengths.sum())
+    assert 2 ** 27 < total < 2 ** 29
+    g = torch.Generator(device="cuda:0").manual_seed(3)
+    x = torch.randn((total, 2), device="cuda:0", generator=g).to(torch.float16)
+    y = torch.empty_like(x)
+    plan = B.bfpfft_plan_create_many(lengths, offsets, B.F16_BFP, B.FORWARD)
+    B.bfpfft_exec_graph(plan, x, y)
+    torch.cuda.synchronize()
+    assert B.bfpfft_device_status() == B.OK
+    rng = np.random.default_rng(7)
+    for n in (256, 1024, 4096, 16384, 65536):
+        idx = np.flatnonzero(lengths == n)
+        for i in rng.choice(idx, 2, replace=False):
+            o = int(offsets[i])
+            xs = from_device(x[o:o + n], B.F16_BFP)
+            ys = from_device(y[o:o + n], B.F16_BFP)
+            ok, worst = fp16_elementwise_ok(ys, F.fft(xs))
+            assert ok, (n, worst)
