@@ -261,6 +261,9 @@ def run_ours(args):
     # ---- autofocus: entropy + adjoint gradient on a 4096 x 4096 FP16 scene -----------
     autofocus = _bench_autofocus(B, torch, dev, stream)
 
+    # ---- uneven batch: 20,000 transforms, lengths 256..65536, one persistent launch ---
+    uneven = _bench_uneven(B, torch, dev, stream)
+
     # ---- end to end through the C ABI with host buffers ---------------------------
     e2e = _bench_e2e(B, torch, dev, stream, x16, fwd16, inv16, flops_step, args)
 
@@ -306,6 +309,7 @@ def run_ours(args):
             "table2_batch256_l2_flushed": {"gflops": round(gflops_small, 1), "ms_median": round(t_small, 5)},
             "sar": sar,
             "autofocus_4096x4096": autofocus,
+            "uneven_20000": uneven,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks.summary(),
@@ -398,6 +402,69 @@ def _bench_autofocus(B, torch, dev, stream):
     flops = 6 * n * 5 * n * 12
     return {"ms_median_l2_flushed": round(t, 4), "gflops": round(flops / (t * 1e-3) / 1e9, 1),
             "alg_gbs": round(3 * 4 * n * n / (t * 1e-3) / 1e9, 1), "dtype": "FP16-BFP rc, FP32 arithmetic"}
+
+
+def _bench_uneven(B, torch, dev, stream):
+    """20,000 transforms with lengths drawn from {256, 1024, 4096, 16384, 65536}
+    (Zipf weights, seed 3), forward, one persistent launch replayed through a
+    CUDA graph, in FP16-BFP, FP32, E4M3 and E5M2 storage; the SQNR of each
+    against the FP32 path by the library's FP64 reduction."""
+    import numpy as np
+
+    from paper_2605_28451_gb300 import synth
+    lengths = synth.uneven_lengths(20000, seed=3)
+    offsets = np.zeros_like(lengths)
+    offsets[1:] = np.cumsum(lengths)[:-1]
+    total = int(lengths.sum())
+    flops = float(np.sum(5.0 * lengths * np.log2(lengths)))
+    g = torch.Generator(device=dev).manual_seed(3)
+    x32 = torch.randn((total, 2), device=dev, generator=g)
+    y32 = torch.empty_like(x32)
+    out = {"transforms": 20000, "points": total}
+    ws_bytes = B.bfp_sqnr_workspace_bytes()
+    ws = torch.empty(ws_bytes // 8, dtype=torch.float64, device=dev)
+    sums = torch.empty(8, dtype=torch.float64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    scale = None
+    for name, dtype in (("f32", B.F32), ("f16_bfp", B.F16_BFP), ("e4m3", B.E4M3_BFP), ("e5m2", B.E5M2_BFP)):
+        if dtype == B.F32:
+            xin = x32
+        elif dtype == B.F16_BFP:
+            xin = x32.to(torch.float16)
+        else:
+            f8 = torch.float8_e4m3fn if dtype == B.E4M3_BFP else torch.float8_e5m2
+            xin = x32.to(f8).view(torch.uint8)
+        yout = y32 if dtype == B.F32 else torch.empty_like(xin)
+        plan = B.bfpfft_plan_create_many(lengths, offsets, dtype, B.FORWARD)
+        for _ in range(3):
+            B.bfpfft_exec_graph(plan, xin, yout, stream)
+        ts = []
+        for _ in range(10):
+            e0.record(stream)
+            B.bfpfft_exec_graph(plan, xin, yout, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        t = statistics.median(ts)
+        entry = {"ms_median": round(t, 4), "gflops": round(flops / (t * 1e-3) / 1e9, 1),
+                 "alg_gbs": round(total * 2 * xin.element_size() * xin.shape[-1] / (t * 1e-3) / 1e9, 1)}
+        if dtype == B.F16_BFP:
+            B.bfp_sqnr_sums(torch.view_as_complex(y32), B.F32, yout, B.F16_BFP, total, sums, ws, ws_bytes, stream)
+            entry["sqnr_vs_f32_db"] = round(B.sqnr_from_sums(sums[:5].cpu().tolist())["aligned_db"], 2)
+        elif dtype != B.F32:
+            if scale is None:
+                s = np.repeat(np.exp2(-((np.log2(lengths).astype(np.int64) + 1) // 2)), lengths).astype(np.float32)
+                scale = torch.from_numpy(s).to(dev)
+            f8 = torch.float8_e4m3fn if dtype == B.E4M3_BFP else torch.float8_e5m2
+            y8 = yout.view(f8).float()
+            ref_scaled = (torch.view_as_real(torch.view_as_complex(y32)) * scale[:, None]).contiguous()
+            B.bfp_sqnr_sums(torch.view_as_complex(ref_scaled), B.F32, torch.view_as_complex(y8.contiguous()), B.F32,
+                            total, sums, ws, ws_bytes, stream)
+            entry["sqnr_vs_f32_db"] = round(B.sqnr_from_sums(sums[:5].cpu().tolist())["aligned_db"], 2)
+            del y8, ref_scaled
+        out[name] = entry
+        del plan
+    return out
 
 
 def _bench_e2e(B, torch, dev, stream, x16, fwd, inv, flops_step, args):

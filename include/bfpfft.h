@@ -115,6 +115,24 @@ int bfpfft_plan_destroy(bfpfft_plan plan);
 int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, const int64_t* offset_pts,
                             int dtype, int direction);
 
+/*
+ * Autotuner (not in the paper).  Times the candidate kernels of this plan on
+ * its own shape -- a uniform plan: the row-kernel variants (plain or bulk-copy
+ * pipelined, one or two FP32 exchange buffers; with allow_fp16_exchange != 0
+ * and FP16 storage also the FP16 shared-memory exchanges, which round at
+ * every pass and so change the results within the FP16 error budget); an
+ * uneven plan: the number of persistent clusters -- on scratch buffers it
+ * allocates and frees (synchronous), keeps the fastest in the plan, and
+ * writes it to the tuning cache (file named by BFPFFT_TUNE_CACHE, default
+ * $HOME/.cache/bfpfft/tune.txt, keyed by GPU name and shape).  chosen: the
+ * variant code or cluster count; best_ms (may be NULL): its median time.
+ * Plans created while BFPFFT_TUNE=cached apply a cached choice;
+ * BFPFFT_TUNE=full also tunes shapes missing from the cache.  The variable
+ * BFPFFT_ROWS, when set, overrides any tuned row variant.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* chosen, float* best_ms);
+
 /* Tasks and persistent clusters of an uneven plan (both 0 for a uniform plan). */
 int bfpfft_plan_info(bfpfft_plan plan, int64_t* tasks, int64_t* clusters);
 

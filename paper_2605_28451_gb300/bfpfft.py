@@ -47,6 +47,7 @@ SIGNATURES = {
     "bfpfft_plan_create_many": (ctypes.c_int, [ctypes.POINTER(_vp), _c_int64, _vp, _vp, ctypes.c_int, ctypes.c_int]),
     "bfpfft_plan_info": (ctypes.c_int, [_vp, ctypes.POINTER(_c_int64), ctypes.POINTER(_c_int64)]),
     "bfpfft_exec_graph": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "bfpfft_plan_tune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "bfpfft_plan_destroy": (ctypes.c_int, [_vp]),
     "bfpfft_plan_scale_exp": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "bfpfft_device_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
@@ -172,6 +173,14 @@ def bfpfft_plan_info(plan: Plan):
     t, c = _c_int64(), _c_int64()
     _check(lib().bfpfft_plan_info(plan.handle, ctypes.byref(t), ctypes.byref(c)), "bfpfft_plan_info")
     return t.value, c.value
+
+
+def bfpfft_plan_tune(plan: Plan, allow_fp16_exchange: bool = False):
+    """Tune the plan on its own shape; returns (chosen variant or cluster count, median ms)."""
+    c, ms = ctypes.c_int(), ctypes.c_float()
+    _check(lib().bfpfft_plan_tune(plan.handle, int(bool(allow_fp16_exchange)), ctypes.byref(c), ctypes.byref(ms)),
+           "bfpfft_plan_tune")
+    return c.value, ms.value
 
 
 def bfpfft_exec_graph(plan: Plan, inp, out, stream=None):

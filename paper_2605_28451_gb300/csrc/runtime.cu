@@ -13,6 +13,9 @@
 #include <map>
 #include <mutex>
 #include <utility>
+#include <string>
+#include <cstdio>
+#include <sys/stat.h>
 #include <vector>
 #include <algorithm>
 
@@ -191,8 +194,10 @@ struct bfpfft_plan_s {
   int* status;         // the device's status word (not owned)
   int in_exp;
   int out_exp;
+  int variant = -1;     // row-kernel variant chosen by the tuner (-1: library default)
   // Uneven plans (bfpfft_plan_create_many): owned device arrays.
   bool many = false;
+  int tuned_clusters = 0;               // persistent clusters chosen by the tuner (0: all resident)
   int kind = 0;                         // storage kind of the persistent kernel
   long long* d_line_off = nullptr;
   bfp::UnevenTask* d_tasks = nullptr;
@@ -224,6 +229,218 @@ int uneven_kind(int dtype) {
     case BFPFFT_E4M3_BFP: return 2;
     case BFPFFT_E5M2_BFP: return 3;
     default: return -1;
+  }
+}
+
+}  // namespace
+
+extern "C" int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream);
+static int exec_many(bfpfft_plan plan, const void* in, void* out, cudaStream_t s) {
+  bfp::UnevenArgs a{};
+  a.in = in;
+  a.out = out;
+  a.line_off = plan->d_line_off;
+  a.tasks = plan->d_tasks;
+  a.num_tasks = plan->num_tasks;
+  a.tw = plan->d_tw;
+  a.counter = plan->d_counter;
+  a.status = plan->status;
+  const int want = plan->tuned_clusters > 0 ? plan->tuned_clusters : plan->clusters;
+  const int clusters = std::min(want, std::max(1, plan->num_tasks));
+  return cuda_status(bfp::launch_uneven(plan->kind, plan->direction == BFPFFT_INVERSE, a, clusters, s));
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner.  Times candidate kernels on the plan's own shape (scratch
+// buffers, 2 warm-up and 5 timed launches, median) and keeps the fastest.
+// Results are cached in memory and in a text file (BFPFFT_TUNE_CACHE, default
+// $HOME/.cache/bfpfft/tune.txt), one "key value ms" line per shape, the key
+// naming the GPU, length(s), batch class, dtype and direction.
+// BFPFFT_TUNE: off (never tune automatically), cached (apply cached results
+// at plan creation), full (also time shapes missing from the cache).
+namespace {
+
+std::mutex g_tune_mutex;
+std::map<std::string, std::pair<int, float>> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_path() {
+  const char* p = std::getenv("BFPFFT_TUNE_CACHE");
+  if (p != nullptr && *p) return p;
+  const char* home = std::getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/bfpfft/tune.txt";
+}
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  FILE* f = std::fopen(tune_path().c_str(), "r");
+  if (f == nullptr) return;
+  char key[512];
+  int v = 0;
+  float ms = 0.f;
+  while (std::fscanf(f, "%511s %d %f", key, &v, &ms) == 3) g_tune[key] = {v, ms};
+  std::fclose(f);
+}
+
+void tune_store_locked() {
+  const std::string path = tune_path();
+  const size_t slash = path.find_last_of('/');
+  if (slash != std::string::npos) {
+    std::string dir = path.substr(0, slash);
+    // create the directory chain if needed (best effort)
+    for (size_t i = 1; i <= dir.size(); ++i)
+      if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+  }
+  const std::string tmp = path + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (f == nullptr) return;
+  for (const auto& kv : g_tune) std::fprintf(f, "%s %d %.5f\n", kv.first.c_str(), kv.second.first, kv.second.second);
+  std::fclose(f);
+  std::rename(tmp.c_str(), path.c_str());
+}
+
+std::string tune_key(bfpfft_plan p) {
+  cudaDeviceProp prop;
+  std::string gpu = "gpu";
+  if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) gpu = prop.name;
+  for (auto& c : gpu)
+    if (c == ' ') c = '_';
+  char buf[256];
+  if (p->many) {
+    std::snprintf(buf, sizeof(buf), "%s/many/tasks%d/d%d/%s", gpu.c_str(), p->num_tasks, p->dtype,
+                  p->direction == BFPFFT_FORWARD ? "fwd" : "inv");
+  } else {
+    int bclass = 0;
+    while ((int64_t(1) << bclass) < p->batch) ++bclass;
+    std::snprintf(buf, sizeof(buf), "%s/n%lld/b%d/d%d/%s", gpu.c_str(), (long long)p->n, bclass, p->dtype,
+                  p->direction == BFPFFT_FORWARD ? "fwd" : "inv");
+  }
+  return buf;
+}
+
+size_t storage_bytes(int dtype) {
+  switch (dtype) {
+    case BFPFFT_F32: return 8;
+    case BFPFFT_F16_BFP:
+    case BFPFFT_F16_NAIVE: return 4;
+    default: return 2;
+  }
+}
+
+}  // namespace
+
+extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* chosen, float* best_ms) {
+  if (plan == nullptr || chosen == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  *chosen = -1;
+  if (best_ms) *best_ms = 0.f;
+  if (plan->batch == 0) return BFPFFT_OK;
+  // Scratch: a bounded sample of the plan's own shape.
+  int64_t points = 0;
+  int64_t sample_batch = plan->batch;
+  if (plan->many) {
+    // every line of an uneven plan: the last task's line ends the buffer extent
+    std::vector<long long> off(1);
+    points = 0;
+    // extent = max(offset + n) is not stored; use tasks: sum of 65536 points per task is an upper bound
+    points = int64_t(plan->num_tasks) * bfp::kUnevenTaskPoints;
+    long long max_off = 0;
+    std::vector<long long> host_off(size_t(plan->batch));
+    if (cudaMemcpy(host_off.data(), plan->d_line_off, sizeof(long long) * host_off.size(),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+      return BFPFFT_ERR_CUDA;
+    for (long long o : host_off) max_off = std::max(max_off, o);
+    points = std::max<int64_t>(points, max_off + 65536);
+  } else {
+    sample_batch = std::min<int64_t>(plan->batch, std::max<int64_t>(1, (int64_t(1) << 28) / plan->n));
+    points = sample_batch * plan->n;
+  }
+  const size_t bytes = size_t(points) * storage_bytes(plan->dtype);
+  void* in = nullptr;
+  void* out = nullptr;
+  cudaError_t e = cudaMalloc(&in, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&out, bytes);
+  if (e == cudaSuccess) e = cudaMemset(in, 0, bytes);
+  if (e != cudaSuccess) {
+    if (in) cudaFree(in);
+    if (out) cudaFree(out);
+    return cuda_status(e);
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int64_t saved_batch = plan->batch;
+  const int saved_variant = plan->variant;
+  const int saved_clusters = plan->tuned_clusters;
+  if (!plan->many) plan->batch = sample_batch;
+  std::vector<int> candidates;
+  if (plan->many) {
+    for (int c = plan->clusters; c >= 1 && candidates.size() < 4; c = c * 3 / 4) candidates.push_back(c);
+  } else {
+    candidates = {bfp::kRowsPlain, bfp::kRowsTma, bfp::kRowsPlainPP, bfp::kRowsTmaPP};
+    if (allow_fp16_exchange && (plan->dtype == BFPFFT_F16_BFP || plan->dtype == BFPFFT_F16_NAIVE)) {
+      candidates.push_back(bfp::kRowsPlainH);
+      candidates.push_back(bfp::kRowsPlainHPP);
+      candidates.push_back(bfp::kRowsTmaH);
+      candidates.push_back(bfp::kRowsTmaHPP);
+    }
+  }
+  int st = BFPFFT_OK;
+  int best = -1;
+  float best_t = 1e30f;
+  for (int c : candidates) {
+    if (plan->many) plan->tuned_clusters = c; else plan->variant = c;
+    float ts[5];
+    for (int r = 0; r < 7 && st == BFPFFT_OK; ++r) {
+      cudaEventRecord(e0, nullptr);
+      st = plan->many ? exec_many(plan, in, out, nullptr) : bfpfft_exec(plan, in, out, nullptr);
+      cudaEventRecord(e1, nullptr);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = BFPFFT_ERR_CUDA;
+      if (r >= 2) cudaEventElapsedTime(&ts[r - 2], e0, e1);
+    }
+    if (st != BFPFFT_OK) break;
+    std::sort(ts, ts + 5);
+    if (ts[2] < best_t) {
+      best_t = ts[2];
+      best = c;
+    }
+  }
+  plan->batch = saved_batch;
+  if (plan->many) plan->tuned_clusters = saved_clusters; else plan->variant = saved_variant;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(in);
+  cudaFree(out);
+  if (st != BFPFFT_OK) return st;
+  if (plan->many) plan->tuned_clusters = best; else plan->variant = best;
+  *chosen = best;
+  if (best_ms) *best_ms = best_t;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_load_locked();
+  g_tune[tune_key(plan)] = {best, best_t};
+  tune_store_locked();
+  return BFPFFT_OK;
+}
+
+namespace {
+
+// Plan-creation hook: apply a cached choice, or tune when BFPFFT_TUNE=full.
+void tune_on_create(bfpfft_plan p) {
+  const char* mode = std::getenv("BFPFFT_TUNE");
+  if (mode == nullptr || std::strcmp(mode, "off") == 0 || p->batch == 0) return;
+  const std::string key = tune_key(p);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    tune_load_locked();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      if (p->many) p->tuned_clusters = it->second.first; else p->variant = it->second.first;
+      return;
+    }
+  }
+  if (std::strcmp(mode, "full") == 0) {
+    int chosen = 0;
+    bfpfft_plan_tune(p, 0, &chosen, nullptr);
   }
 }
 
@@ -275,6 +492,7 @@ int bfpfft_plan_create(bfpfft_plan* out, int64_t n, int64_t batch, int dtype, in
     delete p;
     return st;
   }
+  tune_on_create(p);
   *out = p;
   return BFPFFT_OK;
 }
@@ -356,6 +574,7 @@ int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, c
     delete p;
     return st;
   }
+  tune_on_create(p);
   *out = p;
   return BFPFFT_OK;
 }
@@ -367,19 +586,6 @@ int bfpfft_plan_info(bfpfft_plan plan, int64_t* tasks, int64_t* clusters) {
   return BFPFFT_OK;
 }
 
-static int exec_many(bfpfft_plan plan, const void* in, void* out, cudaStream_t s) {
-  bfp::UnevenArgs a{};
-  a.in = in;
-  a.out = out;
-  a.line_off = plan->d_line_off;
-  a.tasks = plan->d_tasks;
-  a.num_tasks = plan->num_tasks;
-  a.tw = plan->d_tw;
-  a.counter = plan->d_counter;
-  a.status = plan->status;
-  const int clusters = std::min(plan->clusters, std::max(1, plan->num_tasks));
-  return cuda_status(bfp::launch_uneven(plan->kind, plan->direction == BFPFFT_INVERSE, a, clusters, s));
-}
 
 int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
   if (plan == nullptr) return BFPFFT_ERR_INVALID_ARG;
@@ -399,7 +605,7 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
   a.tw = plan->tw;
   a.h = nullptr;
   a.status = plan->status;
-  a.variant = rows_variant();
+  a.variant = std::getenv("BFPFFT_ROWS") == nullptr && plan->variant >= 0 ? plan->variant : rows_variant();
   a.lines = plan->batch;
   a.in_stride = plan->n;
   a.out_stride = plan->n;

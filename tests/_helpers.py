@@ -73,3 +73,24 @@ def fp16_elementwise_ok(got: np.ndarray, ref: np.ndarray, fp32_rel: float = 1e-5
         ratio = np.abs(g - r) / bound
         worst = max(worst, float(np.max(ratio)))
     return worst <= out, worst
+
+
+def fp8_close(got, exact, fmt, max_frac=1e-3):
+    """FP8 parity: every stored value equals the oracle's RN rounding of the
+    exact FP64 value, except where the FP32 arithmetic of the GPU can put the
+    value on the other side of a rounding boundary: within
+    delta = 1e-5 |x| + 1e-6 rms(x) of it (relative FP32 error of the value plus
+    the absolute error the passes leave on small outputs).  There one step
+    either way is accepted, for at most max_frac of the points."""
+    from oracle import quant
+    rms = float(np.sqrt(np.mean(np.abs(exact) ** 2)))
+    expect = quant.round_fp8(exact, fmt)
+    for g, e, x in ((got.real, expect.real, exact.real), (got.imag, expect.imag, exact.imag)):
+        bad = g != e
+        if not bad.any():
+            continue
+        d = 1e-5 * np.abs(x[bad]) + 1e-6 * rms
+        lo = quant.round_fp8(x[bad] - d, fmt)
+        hi = quant.round_fp8(x[bad] + d, fmt)
+        assert np.all((g[bad] == lo) | (g[bad] == hi)), (g[bad][:5], e[bad][:5], x[bad][:5])
+        assert bad.mean() <= max_frac
