@@ -25,13 +25,14 @@ def main():
     ap.add_argument("case")
     ap.add_argument("--batch", type=int, default=16384)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--n", type=int, default=4096, help="transform length of the fft* cases")
     ap.add_argument("--time", action="store_true", help="print the median ms per rep (CUDA events)")
     args = ap.parse_args()
     times = []
     build.build()
     dev = torch.device("cuda:0")
     stream = torch.cuda.current_stream()
-    n = 4096
+    n = args.n if args.case.startswith("fft") else 4096
     g = torch.Generator(device=dev).manual_seed(0)
     if args.case in ("fft16_fwd", "fft16_inv", "fft32_fwd"):
         dtype = B.F32 if args.case == "fft32_fwd" else B.F16_BFP
