@@ -67,6 +67,8 @@ struct RowArgs {
   float out_scale;         // applied before the final rounding (FP8 block exponent)
   int* status;             // device status word (bounded waits record timeouts here)
   int variant;             // RowVariant
+  const float2* tw_line;   // N >= 8192: pass-major table of the 4096-point row transforms
+  const float2* tw_4step;  // N >= 8192: four-step twiddles T[k1][n2] = W_N^{n2 k1}
 };
 
 // Row-kernel variants for dense rows of length <= 4096 (chosen by
@@ -527,6 +529,116 @@ cudaError_t launch_rows_tma_n(const RowArgs& a, cudaStream_t stream) {
 }
 
 
+
+// Four-step line of N = N1 * 4096 points over a group of N1 CTAs (N1 = 2, 4,
+// 8, 16) of one thread-block cluster, 256 threads each.  With n = n2 + 4096 n1
+// and k = k1 + N1 k2:
+//   X[k1 + N1 k2] = sum_n2 W_4096^{n2 k2} W_N^{n2 k1} sum_n1 x[n2 + 4096 n1] W_N1^{n1 k1}.
+// Step 1: CTA c loads the n2-slab [c S, (c + 1) S) (S = 4096 / N1) of every
+//   block n1 -- N1 contiguous, coalesced segments -- runs the N1-point DFTs in
+//   registers, multiplies by W_N^{n2 k1} and writes row k1 into CTA k1's
+//   shared memory (the one exchange through distributed shared memory).
+// Step 2: CTA k1 transforms its row (4096 points, local Stockham passes) and
+//   stores X[k1 + N1 k2] (stride N1; the CTAs of the group fill each sector).
+// The caller brackets each line with cluster barriers.
+template <int N1, class TS, int MODE, bool SCALED>
+__device__ __forceinline__ void fourstep_line(const RowArgs& a, const TS* in, TS* out, float2* smem, int c,
+                                              int base_rank, bool active) {
+  constexpr int N = N1 * 4096, S = 4096 / N1, NB = 16 / N1, P = kPointsPerThread;
+  const int t = threadIdx.x;
+  const float inv_n = 1.0f / float(N);
+  auto cluster = cooperative_groups::this_cluster();
+  float2 v[P];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int n2 = c * S + t + 256 * b;
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1)
+      v[b * N1 + n1] = active ? Storage<TS>::load(in + n2 + 4096 * n1) : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int m = 0; m < P; ++m) {
+    if (SCALED) v[m] = cscale(v[m], a.in_scale);
+    if (MODE == kInverse) v[m] = cscale(cconj(v[m]), inv_n);
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int n2 = c * S + t + 256 * b;
+    float2 u[N1];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) u[i] = v[b * N1 + i];
+    Dft<N1>::run(u);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const float2 z = k1 == 0 ? u[0] : cmul(u[k1], __ldg(a.tw_4step + k1 * 4096 + n2));
+      *cluster.map_shared_rank(smem + pad16(n2), base_rank + k1) = z;
+    }
+  }
+  cluster.sync();
+#pragma unroll
+  for (int m = 0; m < P; ++m) v[m] = smem[pad16(t + 256 * m)];
+  __syncthreads();
+  line_dft<4096>(v, a.tw_line, smem, t);
+#pragma unroll
+  for (int m = 0; m < P; ++m) {
+    if (MODE == kInverse) v[m] = cconj(v[m]);
+    if (SCALED) v[m] = cscale(v[m], a.out_scale);
+  }
+  if (active) {
+#pragma unroll
+    for (int m = 0; m < P; ++m) Storage<TS>::store(out + c + N1 * (t + 256 * m), v[m]);
+  }
+}
+
+// Uniform plans with N >= 8192: one line per group of N / 4096 CTAs, a
+// cluster per line.
+template <int N, class TS, int MODE, bool SCALED>
+__global__ void __launch_bounds__(256, BFP_MIN_BLOCKS) fft_fourstep_kernel(const RowArgs a) {
+  constexpr int N1 = N / 4096;
+  extern __shared__ float2 smem_fs[];
+  auto cluster = cooperative_groups::this_cluster();
+  const int c = int(cluster.block_rank());
+  const long long line = blockIdx.x / N1;
+  const TS* in = static_cast<const TS*>(a.in) + line * a.in_stride;
+  TS* out = static_cast<TS*>(a.out) + line * a.out_stride;
+  cluster.sync();                  // every CTA running before its shared memory is written
+  fourstep_line<N1, TS, MODE, SCALED>(a, in, out, smem_fs, c, 0, true);
+  cluster.sync();                  // no CTA leaves while a peer may still write to it
+}
+
+template <int N, class TS, int MODE, bool SCALED>
+cudaError_t launch_fourstep_n(const RowArgs& a, cudaStream_t stream) {
+  constexpr int N1 = N / 4096;
+  constexpr size_t kBytes = size_t(pad16(4096)) * sizeof(float2);
+  auto kern = fft_fourstep_kernel<N, TS, MODE, SCALED>;
+  static bool configured = false;
+  if (!configured) {
+    if (N1 > 8) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    configured = true;
+  }
+  if (a.lines <= 0) return cudaSuccess;
+  const long long grid = a.lines * N1;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = kBytes;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = N1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 // Lines longer than one CTA's share (N >= 8192): a line spans a thread-block
 // cluster of C CTAs of CTA_T threads, each CTA holding a slab of N / C points
 // of every exchange in its shared memory; the passes read and write the other
@@ -625,6 +737,10 @@ template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, bool 
           bool TSTORE = false>
 cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
   if constexpr (!TLOAD && !TSTORE && N >= 8192) {
+    if constexpr (MODE != kCompress && !NAIVE && std::is_same<TIn, TOut>::value) {
+      if (a.tw_4step != nullptr && a.in_stride == N && a.out_stride == N)
+        return launch_fourstep_n<N, TIn, MODE, SCALED>(a, stream);
+    }
     return launch_cluster_n<N, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
   } else {
   using S = RowShape<N, TLOAD || TSTORE>;
@@ -709,10 +825,10 @@ cudaError_t launch_rows(int log2n, const RowArgs& a, cudaStream_t stream) {
     case 13: return launch_rows_n<8192, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
     case 14: return launch_rows_n<16384, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>(a, stream);
     case 15:
-      if constexpr (!TLOAD && !TSTORE) return launch_cluster_n<32768, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
+      if constexpr (!TLOAD && !TSTORE) return launch_rows_n<32768, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
       else return cudaErrorInvalidValue;
     case 16:
-      if constexpr (!TLOAD && !TSTORE) return launch_cluster_n<65536, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
+      if constexpr (!TLOAD && !TSTORE) return launch_rows_n<65536, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
       else return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }

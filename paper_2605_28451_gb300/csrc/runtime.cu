@@ -72,8 +72,21 @@ __global__ void twiddle_kernel(float2* tw, int n) {
   tw[i] = make_float2(float(c), float(s));
 }
 
+// Four-step twiddles of a length n = N1 * 4096 line: T[k1][n2] = W_n^{n2 k1}
+// for k1 < N1, n2 < 4096 (n entries, k1-major so that lanes with consecutive
+// n2 read consecutive entries).  FP64 sincospi, rounded once to FP32.
+__global__ void fourstep_twiddle_kernel(float2* tw, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k1 = i / 4096, n2 = i % 4096;
+  double s, c;
+  sincospi(-2.0 * double((long long)n2 * k1) / double(n), &s, &c);
+  tw[i] = make_float2(float(c), float(s));
+}
+
 // Per-device, per-length twiddle tables, created on first use and kept for
-// the life of the process (a few hundred KB per device at most).
+// the life of the process (a few hundred KB per device at most).  Keys
+// 0..16: pass-major Stockham tables; 100 + log2 n: four-step tables.
 std::mutex g_tw_mutex;
 std::map<std::pair<int, int>, float2*> g_tw;
 
@@ -89,11 +102,16 @@ int get_twiddles(int log2n, float2** out) {
     return BFPFFT_OK;
   }
   if (fault("alloc")) return BFPFFT_ERR_OOM;
-  const int n = 1 << log2n;
+  const bool four = log2n >= 100;
+  const int n = 1 << (four ? log2n - 100 : log2n);
   float2* tw = nullptr;
   e = cudaMalloc(&tw, sizeof(float2) * n);
   if (e != cudaSuccess) return cuda_status(e);
-  twiddle_kernel<<<(n + 255) / 256, 256>>>(tw, n);
+  if (four) {
+    fourstep_twiddle_kernel<<<(n + 255) / 256, 256>>>(tw, n);
+  } else {
+    twiddle_kernel<<<(n + 255) / 256, 256>>>(tw, n);
+  }
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -145,6 +163,22 @@ int rows_variant() {
   return bfp::kRowsTma;
 }
 
+// Lines of 8192 points and more use the four-step kernel: the 4096-point
+// row table and the four-step table of their length.
+int fourstep_tables(int log2n, bfp::RowArgs* a) {
+  a->tw_line = nullptr;
+  a->tw_4step = nullptr;
+  if (log2n < 13) return BFPFFT_OK;
+  float2* t = nullptr;
+  int st = get_twiddles(12, &t);
+  if (st != BFPFFT_OK) return st;
+  a->tw_line = t;
+  st = get_twiddles(100 + log2n, &t);
+  if (st != BFPFFT_OK) return st;
+  a->tw_4step = t;
+  return BFPFFT_OK;
+}
+
 // Common RowArgs set-up: twiddles, status word, unit scales.
 int row_args(int log2n, bfp::RowArgs* a) {
   std::memset(a, 0, sizeof(*a));
@@ -155,7 +189,7 @@ int row_args(int log2n, bfp::RowArgs* a) {
   a->in_scale = 1.f;
   a->out_scale = 1.f;
   a->variant = rows_variant();
-  return BFPFFT_OK;
+  return fourstep_tables(log2n, a);
 }
 
 bool valid_dtype(int d) { return d >= BFPFFT_F32 && d <= BFPFFT_E5M2_BFP; }
@@ -202,6 +236,7 @@ struct bfpfft_plan_s {
   long long* d_line_off = nullptr;
   bfp::UnevenTask* d_tasks = nullptr;
   const float2** d_tw = nullptr;
+  const float2** d_tw4 = nullptr;
   int* d_counter = nullptr;
   int num_tasks = 0;
   int clusters = 0;
@@ -219,6 +254,7 @@ void free_plan_resources(bfpfft_plan p) {
   if (p->d_line_off) cudaFree(p->d_line_off);
   if (p->d_tasks) cudaFree(p->d_tasks);
   if (p->d_tw) cudaFree(p->d_tw);
+  if (p->d_tw4) cudaFree(p->d_tw4);
   if (p->d_counter) cudaFree(p->d_counter);
 }
 
@@ -243,6 +279,7 @@ static int exec_many(bfpfft_plan plan, const void* in, void* out, cudaStream_t s
   a.tasks = plan->d_tasks;
   a.num_tasks = plan->num_tasks;
   a.tw = plan->d_tw;
+  a.tw4 = plan->d_tw4;
   a.counter = plan->d_counter;
   a.status = plan->status;
   const int want = plan->tuned_clusters > 0 ? plan->tuned_clusters : plan->clusters;
@@ -548,23 +585,32 @@ int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, c
   if (e != cudaSuccess) st = cuda_status(e);
   if (st == BFPFFT_OK) st = get_status_word(&p->status);
   const float2* tw_host[kMaxLog2 + 1] = {};
+  const float2* tw4_host[kMaxLog2 + 1] = {};
   for (int l = kMinLog2; l <= kMaxLog2 && st == BFPFFT_OK; ++l) {
     if (by_class[l].empty()) continue;
     float2* t = nullptr;
     st = get_twiddles(l, &t);
     tw_host[l] = t;
+    if (st == BFPFFT_OK && l >= 13) {
+      bfp::RowArgs tmp{};
+      st = fourstep_tables(l, &tmp);
+      tw_host[12] = tmp.tw_line;
+      tw4_host[l] = tmp.tw_4step;
+    }
   }
   if (st == BFPFFT_OK && fault("alloc")) st = BFPFFT_ERR_OOM;
   if (st == BFPFFT_OK && count > 0) {
     e = cudaMalloc(&p->d_line_off, sizeof(long long) * line_off.size());
     if (e == cudaSuccess) e = cudaMalloc(&p->d_tasks, sizeof(bfp::UnevenTask) * tasks.size());
     if (e == cudaSuccess) e = cudaMalloc(&p->d_tw, sizeof(tw_host));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_tw4, sizeof(tw4_host));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_counter, sizeof(int));
     if (e == cudaSuccess)
       e = cudaMemcpy(p->d_line_off, line_off.data(), sizeof(long long) * line_off.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
       e = cudaMemcpy(p->d_tasks, tasks.data(), sizeof(bfp::UnevenTask) * tasks.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_tw, tw_host, sizeof(tw_host), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_tw4, tw4_host, sizeof(tw4_host), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = bfp::uneven_max_clusters(kind, direction == BFPFFT_INVERSE, &p->clusters);
     if (e != cudaSuccess) st = cuda_status(e);
     if (st == BFPFFT_OK && p->clusters <= 0) st = BFPFFT_ERR_UNSUPPORTED;
@@ -606,6 +652,10 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
   a.h = nullptr;
   a.status = plan->status;
   a.variant = std::getenv("BFPFFT_ROWS") == nullptr && plan->variant >= 0 ? plan->variant : rows_variant();
+  {
+    const int st4 = fourstep_tables(plan->log2n, &a);
+    if (st4 != BFPFFT_OK) return st4;
+  }
   a.lines = plan->batch;
   a.in_stride = plan->n;
   a.out_stride = plan->n;

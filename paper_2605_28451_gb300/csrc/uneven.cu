@@ -9,8 +9,9 @@
 // distributed shared memory; no CTA ever waits for another cluster.  Within a
 // task:
 //   N <= 4096   every CTA transforms 4096 / N lines in its own shared memory;
-//   N >= 8192   a line spans N / 4096 CTAs of the cluster and its passes
-//               exchange through distributed shared memory (cluster barriers).
+//   N >= 8192   a line spans N / 4096 CTAs of the cluster: the four-step line
+//               of fft_rows.cuh (one exchange through distributed shared
+//               memory, then local 4096-point transforms).
 // Tasks are ordered largest length first so the short tasks fill the tail.
 // Storage: FP16 (BFP shift before the inverse), FP32, or FP8 with the static
 // block exponents of the uniform plans; arithmetic FP32.
@@ -28,20 +29,6 @@ namespace {
 constexpr int kCta = 256;
 constexpr int kClusterCtas = 16;
 constexpr int kSlab = 4096;     // points of one line per CTA (N >= 4096)
-
-// Cluster exchange for a line that starts at cluster rank `base`.
-template <int SLAB>
-struct ClusterXchAt {
-  float2* local;
-  int base;
-  __device__ __forceinline__ float2* at(int i) const {
-    return cooperative_groups::this_cluster().map_shared_rank(local + pad16(i % SLAB), base + i / SLAB);
-  }
-  template <int Q> __device__ __forceinline__ float2 load(int i) const { return *at(i); }
-  template <int Q> __device__ __forceinline__ void store(int i, float2 v) const { *at(i) = v; }
-  __device__ __forceinline__ void sync() const { cooperative_groups::this_cluster().sync(); }
-  __device__ __forceinline__ void sync_war() const { cooperative_groups::this_cluster().sync(); }
-};
 
 template <class TS, int MODE, bool SCALED, int LOG2N>
 __device__ __noinline__ void run_task(const UnevenArgs& a, const UnevenTask& tk, int rank, float2* smem) {
@@ -79,23 +66,12 @@ __device__ __noinline__ void run_task(const UnevenArgs& a, const UnevenTask& tk,
     constexpr int C = N / kSlab;                         // CTAs per line
     const int idx = rank / C;                            // line within the task
     const int base = idx * C;
-    const int t = (rank - base) * kCta + threadIdx.x;
     const bool active = idx < tk.count;
     const long long off = active ? a.line_off[tk.first + idx] : 0;
-    if (active) {
-      const TS* in = static_cast<const TS*>(a.in) + off + t;
-#pragma unroll
-      for (int m = 0; m < P; ++m) v[m] = Storage<TS>::load(in + T * m);
-    } else {
-#pragma unroll
-      for (int m = 0; m < P; ++m) v[m] = make_float2(0.f, 0.f);
-    }
-    row_compute_x<N, MODE, false, SCALED>(v, ra, ClusterXchAt<kSlab>{smem, base}, t);
-    if (active) {
-      TS* out = static_cast<TS*>(a.out) + off + t;
-#pragma unroll
-      for (int m = 0; m < P; ++m) Storage<TS>::store(out + T * m, v[m]);
-    }
+    ra.tw_line = a.tw[12];
+    ra.tw_4step = a.tw4[LOG2N];
+    fourstep_line<C, TS, MODE, SCALED>(ra, static_cast<const TS*>(a.in) + off, static_cast<TS*>(a.out) + off,
+                                       smem, rank - base, base, active);
   }
 }
 

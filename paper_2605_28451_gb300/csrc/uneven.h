@@ -21,6 +21,7 @@ struct UnevenArgs {
   const UnevenTask* tasks;
   int num_tasks;
   const float2* const* tw;       // per-length twiddle tables, indexed by log2 N
+  const float2* const* tw4;      // per-length four-step tables (N >= 8192), indexed by log2 N
   int* counter;                  // task counter (reset before every launch)
   int* status;
 };
