@@ -69,6 +69,7 @@ struct RowArgs {
   int variant;             // RowVariant
   const float2* tw_line;   // N >= 8192: pass-major table of the 4096-point row transforms
   const float2* tw_4step;  // N >= 8192: four-step twiddles T[k1][n2] = W_N^{n2 k1}
+  const void* tc_b;        // tensor-core variant: 16-point DFT matrix, real form, FP16 [32][32]
 };
 
 // Row-kernel variants for dense rows of length <= 4096 (chosen by
@@ -78,7 +79,7 @@ struct RowArgs {
 // anything not applicable falls back to kRowsTma.
 enum RowVariant : int {
   kRowsTma = 0, kRowsPlain = 1, kRowsPlainPP = 2, kRowsPlainH = 3, kRowsPlainHPP = 4,
-  kRowsTmaPP = 5, kRowsTmaH = 6, kRowsTmaHPP = 7
+  kRowsTmaPP = 5, kRowsTmaH = 6, kRowsTmaHPP = 7, kRowsTc = 8
 };
 
 constexpr int kPointsPerThread = 16;
@@ -712,6 +713,10 @@ cudaError_t launch_cluster_n(const RowArgs& a, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+// Tensor-core radix-16 variant (tc_fft.cuh), N = 4096, FP16 storage.
+template <class TS, int MODE>
+cudaError_t launch_tc_n(const RowArgs& a, cudaStream_t stream);
+
 // Plain (one group per CTA, no prefetch) row kernel with an exchange variant.
 template <int N, class TIn, class TOut, int MODE, bool NAIVE, int XV>
 cudaError_t launch_rows_plain_x(const RowArgs& a, cudaStream_t stream) {
@@ -764,6 +769,11 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
           break;
         case kRowsTmaHPP:
           if constexpr (kHalf) return launch_rows_tma_n<N, TIn, TOut, MODE, NAIVE, SCALED, kXchF16PP>(a, stream);
+          break;
+        case kRowsTc:
+          if constexpr (kHalf && N == 4096 && !NAIVE) {
+            if (a.tc_b != nullptr) return launch_tc_n<TIn, MODE>(a, stream);
+          }
           break;
         default: break;
       }

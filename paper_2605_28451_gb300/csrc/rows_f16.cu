@@ -1,6 +1,7 @@
 // FP16-storage row transforms: the block-floating-point path (Eq. 1) and the
 // naive unshifted path of Section III-B.
 #include "launch.h"
+#include "tc_fft.cuh"
 
 namespace bfp {
 

@@ -4,6 +4,7 @@
 // (FP64 sincospi on the GPU, rounded once to FP32) and the small filter
 // normalisation kernel; every transform runs in the row kernels of
 // fft_rows.cuh, launched through launch.h.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -157,10 +158,49 @@ int rows_variant() {
   static const struct { const char* name; int code; } kNames[] = {
       {"tma", bfp::kRowsTma},         {"plain", bfp::kRowsPlain},    {"pp", bfp::kRowsPlainPP},
       {"h16", bfp::kRowsPlainH},      {"h16pp", bfp::kRowsPlainHPP}, {"tma_pp", bfp::kRowsTmaPP},
-      {"tma_h16", bfp::kRowsTmaH},    {"tma_h16pp", bfp::kRowsTmaHPP}};
+      {"tma_h16", bfp::kRowsTmaH},    {"tma_h16pp", bfp::kRowsTmaHPP}, {"tc", bfp::kRowsTc}};
   for (const auto& k : kNames)
     if (std::strcmp(v, k.name) == 0) return k.code;
   return bfp::kRowsTma;
+}
+
+// The 16-point DFT matrix of the tensor-core variant in real form, FP16,
+// [n][k]: B[2q][2r] = Re W, B[2q][2r+1] = -Im W, B[2q+1][2r] = Im W,
+// B[2q+1][2r+1] = Re W with W = exp(-2 pi i q r / 16); one copy per device.
+std::map<int, void*> g_tc_b;
+
+int get_tc_matrix(void** out) {
+  *out = nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  std::lock_guard<std::mutex> lock(g_tw_mutex);
+  auto it = g_tc_b.find(dev);
+  if (it != g_tc_b.end()) {
+    *out = it->second;
+    return BFPFFT_OK;
+  }
+  __half host[32 * 32];
+  const double pi = 3.14159265358979323846;
+  for (int q = 0; q < 16; ++q)
+    for (int r = 0; r < 16; ++r) {
+      const double ang = -2.0 * pi * double((q * r) % 16) / 16.0;
+      const double wr = std::cos(ang), wi = std::sin(ang);
+      host[(2 * q) * 32 + 2 * r] = __double2half(wr);
+      host[(2 * q) * 32 + 2 * r + 1] = __double2half(-wi);
+      host[(2 * q + 1) * 32 + 2 * r] = __double2half(wi);
+      host[(2 * q + 1) * 32 + 2 * r + 1] = __double2half(wr);
+    }
+  void* d = nullptr;
+  e = cudaMalloc(&d, sizeof(host));
+  if (e == cudaSuccess) e = cudaMemcpy(d, host, sizeof(host), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (d) cudaFree(d);
+    return cuda_status(e);
+  }
+  g_tc_b[dev] = d;
+  *out = d;
+  return BFPFFT_OK;
 }
 
 // Lines of 8192 points and more use the four-step kernel: the 4096-point
@@ -652,6 +692,10 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
   a.h = nullptr;
   a.status = plan->status;
   a.variant = std::getenv("BFPFFT_ROWS") == nullptr && plan->variant >= 0 ? plan->variant : rows_variant();
+  if (a.variant == bfp::kRowsTc && plan->log2n == 12 && plan->dtype == BFPFFT_F16_BFP) {
+    const int stc = get_tc_matrix(const_cast<void**>(&a.tc_b));
+    if (stc != BFPFFT_OK) return stc;
+  }
   {
     const int st4 = fourstep_tables(plan->log2n, &a);
     if (st4 != BFPFFT_OK) return st4;

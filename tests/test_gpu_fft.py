@@ -56,7 +56,7 @@ def test_f32_forward_and_inverse(n, batch, rows_variant):
     assert metrics.rel_l2(ref_i, got_i) <= 1e-6
 
 
-ROW_VARIANTS = ["tma", "plain", "pp", "h16", "h16pp", "tma_pp", "tma_h16", "tma_h16pp"]
+ROW_VARIANTS = ["tma", "plain", "pp", "h16", "h16pp", "tma_pp", "tma_h16", "tma_h16pp", "tc"]
 
 
 @pytest.fixture(params=ROW_VARIANTS)
@@ -76,9 +76,14 @@ def f16_check(got, ref, variant, n):
     remaining passes like noise of rms about 2^-11 rms(y), so every element
     must lie within 2^-11 |y| + 6 * 2^-11 rms(y) (a 6-sigma bound) and the
     SQNR must reach 55 dB (the benchmark spec's FP16-BFP bar)."""
-    if "h16" in variant and n > 16:
+    fp16_inside = ("h16" in variant and n > 16) or (variant == "tc" and n == 4096)
+    if fp16_inside:
+        # The tensor-core variant (tc, N = 4096) also rounds the DFT-16
+        # coefficients to FP16: two error sources of rms 2^-11/sqrt(3) per pass,
+        # about 1.1 * 2^-11 rms per component in all; 8 * 2^-11 rms is > 7 sigma.
         rms = np.sqrt(np.mean(np.abs(ref) ** 2))
-        bound = 2.0 ** -11 * (np.abs(ref) + 6.0 * rms)
+        k = 8.0 if variant == "tc" else 6.0
+        bound = 2.0 ** -11 * (np.abs(ref) + k * rms)
         assert np.all(np.abs(got.real - ref.real) <= bound) and np.all(np.abs(got.imag - ref.imag) <= bound)
         assert metrics.sqnr_db(ref, got) >= 55.0
     else:
