@@ -603,8 +603,10 @@ __global__ void __launch_bounds__(256, BFP_MIN_BLOCKS) fft_fourstep_kernel(const
   const TS* in = static_cast<const TS*>(a.in) + line * a.in_stride;
   TS* out = static_cast<TS*>(a.out) + line * a.out_stride;
   cluster.sync();                  // every CTA running before its shared memory is written
+  // All writes into a CTA's shared memory happen before the barrier inside
+  // the line, so no closing barrier is needed (one would also wait for the
+  // line's global stores to drain).
   fourstep_line<N1, TS, MODE, SCALED>(a, in, out, smem_fs, c, 0, true);
-  cluster.sync();                  // no CTA leaves while a peer may still write to it
 }
 
 template <int N, class TS, int MODE, bool SCALED>

@@ -22,9 +22,8 @@
 // paper's half2 kernel.
 //
 // Rows: butterfly j of pass p sits in A/D row rho_p(j); thread tau (TMEM lane
-// tau % 128 of tile tau / 128) handles the butterfly in row tau.  rho_p are
-// bit permutations chosen to keep the producer's shared-memory stores free of
-// bank conflicts (tables below).
+// tau % 128 of tile tau / 128) handles the butterfly in row tau.  rho_p keep
+// every shared-memory store of the producer free of bank conflicts (below).
 //
 // Waits are bounded; on expiry the CTA records a timeout, waits (bounded) for
 // its last commit, frees its tensor memory and returns.
@@ -53,26 +52,39 @@ __host__ __device__ constexpr int kmaj(int row, int k) {
   return (row / 8) * kSbo + (k / 8) * kLbo + (row % 8) * 16 + (k % 8) * 2;
 }
 
-// Row of butterfly j in pass P (0, 1, 2) and its inverse.  Each map is a
-// permutation of the 8 bits of j: bit b of the row is bit row_bit(P, b) of j.
-__host__ __device__ constexpr int row_bit(int p, int b) {
-  constexpr int kBits[3][8] = {{0, 1, 2, 3, 4, 5, 6, 7}, {0, 1, 2, 3, 4, 5, 6, 7}, {0, 1, 2, 3, 4, 5, 6, 7}};
-  return kBits[p][b];
-}
+// Row of butterfly j in pass P (0, 1, 2) and its inverse.  The bank of a
+// 4-byte store into the A tile is (row % 8) * 4 + (k-pair % 4), so the maps
+// are chosen (GF(2)-linear in the 8 bits of j) such that the 32 lanes of a
+// warp always hit 32 different banks:
+//   P = 0: row bits = j bits (0, 1, 2, 4, 5, 3, 6, 7)
+//   P = 1: row bits = (j4, j5, j6 ^ j0, j1, j2, j3, j6, j7)
+//   P = 2: identity (the last pass stores X[j + 256 q] coalesced)
+// and the pass-0 loads visit the k-pairs in a lane-rotated order.
+__device__ __forceinline__ int bit(int x, int b) { return (x >> b) & 1; }
 
 template <int P>
 __device__ __forceinline__ int row_of(int j) {
-  int r = 0;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) r |= ((j >> row_bit(P, b)) & 1) << b;
-  return r;
+  if constexpr (P == 0) {
+    return bit(j, 0) | bit(j, 1) << 1 | bit(j, 2) << 2 | bit(j, 4) << 3 | bit(j, 5) << 4 | bit(j, 3) << 5 |
+           bit(j, 6) << 6 | bit(j, 7) << 7;
+  } else if constexpr (P == 1) {
+    return bit(j, 4) | bit(j, 5) << 1 | (bit(j, 6) ^ bit(j, 0)) << 2 | bit(j, 1) << 3 | bit(j, 2) << 4 |
+           bit(j, 3) << 5 | bit(j, 6) << 6 | bit(j, 7) << 7;
+  } else {
+    return j;
+  }
 }
 template <int P>
-__device__ __forceinline__ int butterfly_of(int row) {
-  int j = 0;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) j |= ((row >> b) & 1) << row_bit(P, b);
-  return j;
+__device__ __forceinline__ int butterfly_of(int r) {
+  if constexpr (P == 0) {
+    return bit(r, 0) | bit(r, 1) << 1 | bit(r, 2) << 2 | bit(r, 5) << 3 | bit(r, 3) << 4 | bit(r, 4) << 5 |
+           bit(r, 6) << 6 | bit(r, 7) << 7;
+  } else if constexpr (P == 1) {
+    return (bit(r, 2) ^ bit(r, 6)) | bit(r, 3) << 1 | bit(r, 4) << 2 | bit(r, 5) << 3 | bit(r, 0) << 4 |
+           bit(r, 1) << 5 | bit(r, 6) << 6 | bit(r, 7) << 7;
+  } else {
+    return r;
+  }
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
@@ -211,8 +223,10 @@ __global__ void __launch_bounds__(256, 3) fft_tc_kernel(const RowArgs a) {
     // Pass-0 inputs: butterfly j = tid takes x[j + 256 r]; coalesced loads.
     const TS* in = static_cast<const TS*>(a.in) + line * a.in_stride + tid;
     const int row = tc::row_of<0>(tid);
+    const int rot = (tid >> 3) & 3;                     // lane-rotated k-pair order
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int m = 0; m < 16; ++m) {
+      const int r = (m + rot) & 15;
       float2 x = Storage<TS>::load(in + 256 * r);
       if (MODE == kInverse) x = cscale(cconj(x), inv_n);
       tc::store_pair(sA, row, r, x);
@@ -236,14 +250,16 @@ cudaError_t launch_tc_n(const RowArgs& a, cudaStream_t stream) {
   auto kern = fft_tc_kernel<TS, MODE>;
   static int grid_cap = 0;
   if (grid_cap == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
+    // Three CTAs per SM: the register limit of __launch_bounds__(256, 3);
+    // tensor memory would allow eight (64 of 512 columns each), so the
+    // persistent CTAs never wait on each other's allocation.
+    int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, tc::kSmemBytes);
     if (e != cudaSuccess) return e;
-    if (per_sm > 8) per_sm = 8;                        // tensor memory: 8 x 64 columns per SM
-    grid_cap = (per_sm > 0 ? per_sm : 1) * sms;
+    grid_cap = 3 * sms;
   }
+  (void)kern;
   if (a.lines <= 0) return cudaSuccess;
   const int grid = int(a.lines < grid_cap ? a.lines : grid_cap);
   kern<<<grid, 256, tc::kSmemBytes, stream>>>(a);

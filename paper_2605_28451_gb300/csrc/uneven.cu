@@ -4,10 +4,9 @@
 // Work is cut into tasks of 65,536 points of one length: a task is one line
 // of 65536, four of 16384, ..., sixteen of 4096, ..., 4096 of 16.  The grid is
 // made of thread-block clusters of 16 CTAs x 256 threads (16 points per
-// thread, the register layout of fft_rows.cuh).  Rank 0 of each cluster takes
-// the next task from a global counter and hands it to its 15 peers through
-// distributed shared memory; no CTA ever waits for another cluster.  Within a
-// task:
+// thread, the register layout of fft_rows.cuh).  Cluster k takes tasks k,
+// k + clusters, ... (all tasks are the same size); no CTA ever waits for
+// another cluster.  Within a task:
 //   N <= 4096   every CTA transforms 4096 / N lines in its own shared memory;
 //   N >= 8192   a line spans N / 4096 CTAs of the cluster: the four-step line
 //               of fft_rows.cuh (one exchange through distributed shared
@@ -75,21 +74,24 @@ __device__ __noinline__ void run_task(const UnevenArgs& a, const UnevenTask& tk,
   }
 }
 
+// Cluster barrier without memory ordering: it only tells every CTA that its
+// peers are done with their shared memory (a release barrier would also wait
+// for the previous task's global stores to drain).
+__device__ __forceinline__ void cluster_barrier_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+}
+
 template <class TS, int MODE, bool SCALED>
 __global__ void __launch_bounds__(kCta, 3) uneven_kernel(const UnevenArgs a) {
   extern __shared__ float2 smem_u[];
-  __shared__ int task_slot;
   auto cluster = cooperative_groups::this_cluster();
   const int rank = int(cluster.block_rank());
+  const int cluster_id = int(blockIdx.x) / kClusterCtas;
+  const int clusters = int(gridDim.x) / kClusterCtas;
   cluster.sync();                                        // all peers running before any DSMEM write
-  for (;;) {
-    if (rank == 0 && threadIdx.x == 0) {
-      const int task = atomicAdd(a.counter, 1);
-      for (int r = 0; r < kClusterCtas; ++r) *cluster.map_shared_rank(&task_slot, r) = task;
-    }
-    cluster.sync();
-    const int task = task_slot;
-    if (task >= a.num_tasks) break;
+  // Tasks hold 65,536 points each, so a static round-robin over the clusters
+  // balances the work; no counter or broadcast is needed.
+  for (int task = cluster_id; task < a.num_tasks; task += clusters) {
     const UnevenTask tk = a.tasks[task];
     switch (tk.log2n) {
       case 4: run_task<TS, MODE, SCALED, 4>(a, tk, rank, smem_u); break;
@@ -107,9 +109,9 @@ __global__ void __launch_bounds__(kCta, 3) uneven_kernel(const UnevenArgs a) {
       case 16: run_task<TS, MODE, SCALED, 16>(a, tk, rank, smem_u); break;
       default: break;
     }
-    // task_slot is rewritten by rank 0 only after every CTA has passed this
-    // barrier, and no CTA reaches another's shared memory across it.
-    cluster.sync();
+    // A peer may write into this CTA's shared memory in the next task only
+    // after this CTA is done with it.
+    cluster_barrier_relaxed();
   }
 }
 
