@@ -358,6 +358,8 @@ def _bench_sar(B, torch, dev, stream):
         out[name] = {"ms_median_l2_flushed": round(t, 4), "gflops": round(flops / (t * 1e-3) / 1e9, 1),
                      "alg_gbs": round(bytes_ / (t * 1e-3) / 1e9, 1), "dtype": "complex64 in, FP16-BFP out",
                      "naive_has_nonfinite": None}
+        if full:
+            out[name].update(_image_quality(B, torch, dev, stream, raw, hr, ha, img, sc.targets, n_az, n_rg))
         if not full:
             naive = torch.empty((n_az, n_rg, 2), dtype=torch.float16, device=dev)
             B.sar_range_compress(raw, B.F32, naive, B.F16_NAIVE, hr, n_az, n_rg, False, stream)
@@ -365,6 +367,40 @@ def _bench_sar(B, torch, dev, stream):
             out[name]["naive_has_nonfinite"] = bool((~torch.isfinite(naive)).any().item())
         del raw, rc, img, flush
     return out
+
+
+def _image_quality(B, torch, dev, stream, raw, hr, ha, img16, targets, n_az, n_rg):
+    """FP16-BFP image vs the FP32 image of the same scene, both on the GPU:
+    end-to-end SQNR (FP64 reduction) and the point-target metrics (FP64 kernel)."""
+    rc32 = torch.empty((n_rg, n_az), dtype=torch.complex64, device=dev)
+    img32 = torch.empty((n_az, n_rg), dtype=torch.complex64, device=dev)
+    B.sar_range_compress(raw, B.F32, rc32, B.F32, hr, n_az, n_rg, True, stream)
+    B.sar_azimuth_compress(rc32, B.F32, 1, img32, B.F32, ha, n_az, n_rg, stream)
+    ws_bytes = B.bfp_sqnr_workspace_bytes()
+    ws = torch.empty(ws_bytes // 8, dtype=torch.float64, device=dev)
+    sums = torch.empty(8, dtype=torch.float64, device=dev)
+    B.bfp_sqnr_sums(img32, B.F32, img16, B.F16_BFP, n_az * n_rg, sums, ws, ws_bytes, stream)
+    sq = B.sqnr_from_sums(sums[:5].cpu().tolist())
+    t = torch.tensor([[e, r] for e, r, _ in targets], dtype=torch.int32, device=dev)
+    pw = B.sar_point_target_workspace_bytes(n_az, n_rg)
+    pws = torch.empty(pw, dtype=torch.uint8, device=dev)
+    m16 = torch.empty((len(targets), 12), dtype=torch.float64, device=dev)
+    m32 = torch.empty_like(m16)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    B.sar_point_target_metrics(img16, B.F16_BFP, n_az, n_rg, t, len(targets), 96, m16, pws, pw, stream)
+    e1.record(stream)
+    B.sar_point_target_metrics(img32, B.F32, n_az, n_rg, t, len(targets), 96, m32, pws, pw, stream)
+    torch.cuda.synchronize()
+    a, b = m16.cpu().numpy(), m32.cpu().numpy()
+    d = abs(a - b)
+    return {"sqnr_fp16_vs_fp32_db": round(sq["aligned_db"], 2), "nonfinite": sq["nonfinite"],
+            "max_abs_delta_db": {"pslr": float(d[:, 0:2].max()), "islr": float(d[:, 2:4].max()),
+                                 "snr": float(d[:, 7].max())},
+            "max_abs_delta_width_cells": float(d[:, 4:6].max()),
+            "pslr_db_fp16": [round(float(x), 2) for x in a[:, 0:2].max(axis=1)],
+            "snr_db_fp16": [round(float(x), 2) for x in a[:, 7]],
+            "metrics_kernel_ms": round(e0.elapsed_time(e1), 3)}
 
 
 def _bench_autofocus(B, torch, dev, stream):

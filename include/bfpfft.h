@@ -257,6 +257,30 @@ int sar_autofocus_grad(const void* rc, int rc_dtype, const float* phi, const voi
  * FP64 metric reductions on the GPU (Section IV-B, Section VI).
  * ------------------------------------------------------------------------- */
 
+/*
+ * Point-target metrics of a SAR image, FP64 on the GPU (Section VI, Table
+ * III).  The paper names PSLR, ISLR, target SNR and 3 dB resolution without
+ * defining windows; per target (eta, r) this computes:
+ *   peak cell = argmax |I| within +-4 cells of (eta, r); a 64 x 64 window
+ *   around it interpolated x16 by zero-padding its 2-D DFT; the interpolated
+ *   maximum within +-1 cell; the range and azimuth cuts through it (1024 fine
+ *   samples); per cut the mainlobe (peak to the first minimum on each side),
+ *   PSLR = 20 log10(max sidelobe / peak), ISLR = 10 log10(sidelobe / mainlobe
+ *   energy), 3 dB width in cells (linear interpolation of the half-power
+ *   crossings); SNR = 10 log10(peak^2 / mean |I|^2 over every cell at least
+ *   `guard` cells from every target in both axes).
+ *   img       [n_az][n_rg], dtype BFPFFT_F32 or BFPFFT_F16_*, n_az, n_rg >= 64
+ *   targets   device int32 [k][2] = (eta, r)
+ *   out       device double [k][12] = PSLR range, PSLR azimuth, ISLR range,
+ *             ISLR azimuth, width range, width azimuth (cells), peak |I|, SNR
+ *             (dB), noise power, peak cell eta, peak cell r, (reserved)
+ *   workspace caller-owned device scratch of sar_point_target_workspace_bytes().
+ * Errors: INVALID_ARG, UNSUPPORTED (dtype), MISALIGNED, CUDA.
+ */
+size_t sar_point_target_workspace_bytes(int64_t n_az, int64_t n_rg);
+int sar_point_target_metrics(const void* img, int img_dtype, int64_t n_az, int64_t n_rg, const int32_t* targets,
+                             int64_t k, int guard, void* out, void* workspace, size_t ws_bytes, void* stream);
+
 /* Device workspace bytes bfp_sqnr_sums() needs, for any count. */
 size_t bfp_sqnr_workspace_bytes(void);
 

@@ -61,6 +61,9 @@ SIGNATURES = {
                                              ctypes.c_size_t, _vp]),
     "sar_autofocus_grad": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_int64, _c_int64, _vp, _vp, _vp,
                                           ctypes.c_size_t, _vp]),
+    "sar_point_target_workspace_bytes": (ctypes.c_size_t, [_c_int64, _c_int64]),
+    "sar_point_target_metrics": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64, _c_int64, _vp, _c_int64, ctypes.c_int,
+                                                _vp, _vp, ctypes.c_size_t, _vp]),
     "bfp_sqnr_workspace_bytes": (ctypes.c_size_t, []),
     "bfp_sqnr_sums_noalloc_max_count": (ctypes.c_longlong, []),
     "bfp_sqnr_sums_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _c_int64, _vp, _vp]),
@@ -272,3 +275,18 @@ def bfp_sqnr_sums_noalloc(ref, ref_dtype: int, test, test_dtype: int, count: int
     """bfp_sqnr_sums with the library's built-in scratch: no workspace, no allocation."""
     _check(lib().bfp_sqnr_sums_noalloc(_ptr(ref), int(ref_dtype), _ptr(test), int(test_dtype), int(count),
                                        _ptr(sums_out), _stream(stream)), "bfp_sqnr_sums_noalloc")
+
+
+PT_FIELDS = ("pslr_range_db", "pslr_azimuth_db", "islr_range_db", "islr_azimuth_db", "width_range_cells",
+             "width_azimuth_cells", "peak", "snr_db", "noise_power", "peak_eta", "peak_r", "reserved")
+
+
+def sar_point_target_workspace_bytes(n_az: int, n_rg: int) -> int:
+    return int(lib().sar_point_target_workspace_bytes(int(n_az), int(n_rg)))
+
+
+def sar_point_target_metrics(img, img_dtype: int, n_az: int, n_rg: int, targets, k: int, guard: int, out, workspace,
+                             ws_bytes: int, stream=None):
+    _check(lib().sar_point_target_metrics(_ptr(img), int(img_dtype), int(n_az), int(n_rg), _ptr(targets), int(k),
+                                          int(guard), _ptr(out), _ptr(workspace), int(ws_bytes), _stream(stream)),
+           "sar_point_target_metrics")

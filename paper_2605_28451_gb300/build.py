@@ -33,6 +33,7 @@ SOURCES = [
     "autofocus.cu",
     "metrics_noalloc.cu",
     "uneven.cu",
+    "pt_metrics.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

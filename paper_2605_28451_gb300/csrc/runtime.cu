@@ -25,6 +25,7 @@
 #include "metrics.h"
 #include "autofocus.h"
 #include "uneven.h"
+#include "pt_metrics.h"
 
 namespace {
 
@@ -897,6 +898,27 @@ int sar_autofocus_grad(const void* rc, int rc_dtype, const float* phi, const voi
                        void* stream) {
   if (grad_out == nullptr) return BFPFFT_ERR_INVALID_ARG;
   return autofocus_common(rc, rc_dtype, phi, ha, n_az, n_rg, grad_out, stats_out, workspace, ws_bytes, stream);
+}
+
+size_t sar_point_target_workspace_bytes(int64_t n_az, int64_t n_rg) {
+  if (n_az < 0 || n_rg < 0) return 0;
+  return bfp::pt_workspace_bytes(n_az, n_rg);
+}
+
+int sar_point_target_metrics(const void* img, int img_dtype, int64_t n_az, int64_t n_rg, const int32_t* targets,
+                             int64_t k, int guard, void* out, void* workspace, size_t ws_bytes, void* stream) {
+  if (n_az < 64 || n_rg < 64 || k < 0 || k > 65535 || guard < 1) return BFPFFT_ERR_INVALID_ARG;
+  if (img_dtype != BFPFFT_F32 && img_dtype != BFPFFT_F16_BFP && img_dtype != BFPFFT_F16_NAIVE)
+    return BFPFFT_ERR_UNSUPPORTED;
+  if (k == 0) return BFPFFT_OK;
+  if (img == nullptr || targets == nullptr || out == nullptr || workspace == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (!aligned16(img) || !aligned16(out) || !aligned16(workspace)) return BFPFFT_ERR_MISALIGNED;
+  if (ws_bytes < bfp::pt_workspace_bytes(n_az, n_rg)) return BFPFFT_ERR_INVALID_ARG;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
+  cudaError_t e = bfp::launch_point_target_metrics(img, img_dtype != BFPFFT_F32, n_az, n_rg, targets, int(k), guard,
+                                                   static_cast<double*>(out), workspace,
+                                                   static_cast<cudaStream_t>(stream));
+  return cuda_status(e);
 }
 
 size_t bfp_sqnr_workspace_bytes(void) { return bfp::kMetricWorkspaceBytes; }
