@@ -60,10 +60,15 @@ def _peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+# Sources of the headline row kernel: its DRAM traffic in profiles/ is valid
+# only while these are unchanged.
+KERNEL_SOURCES = ("fft_rows.cuh", "complex_ops.cuh", "storage.cuh", "async_copy.cuh", "rows_f16.cu", "tc_fft.cuh")
+
+
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2605_28451_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -298,7 +303,8 @@ def run_ours(args):
             "roofline": {
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "fft_rows_kernel<4096, half2, half2, forward>",
+                "kernel": "fft_rows_kernel<4096, half2, half2, forward> (plain, FP32 exchange)",
+                "kernel_source_hash": _kernel_source_hash(),
                 "bytes_per_launch": alg_bytes, "launch_ms": round(fwd_avg, 5), "peak_source": peak_kind,
                 "frac_of_8tbs_nominal": round(achieved / 8000.0, 4),
             },
