@@ -62,4 +62,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+
+// Asynchronous store of one complex FP32 value into another CTA's shared
+// memory; its arrival is counted (8 bytes) on that CTA's mbarrier.
+__device__ __forceinline__ void st_async_f2(uint32_t remote_addr, float2 v, uint32_t remote_bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(remote_addr),
+               "f"(v.x), "f"(v.y), "r"(remote_bar)
+               : "memory");
+}
+
+// Cluster barrier without memory ordering (only "everyone got here").
+__device__ __forceinline__ void cluster_barrier_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+}
+
 }  // namespace bfp

@@ -79,7 +79,7 @@ struct RowArgs {
 // anything not applicable falls back to kRowsTma.
 enum RowVariant : int {
   kRowsTma = 0, kRowsPlain = 1, kRowsPlainPP = 2, kRowsPlainH = 3, kRowsPlainHPP = 4,
-  kRowsTmaPP = 5, kRowsTmaH = 6, kRowsTmaHPP = 7, kRowsTc = 8
+  kRowsTmaPP = 5, kRowsTmaH = 6, kRowsTmaHPP = 7, kRowsTc = 8, kRowsPlain4 = 9
 };
 
 constexpr int kPointsPerThread = 16;
@@ -336,9 +336,10 @@ __device__ __forceinline__ void cluster_barrier() {
   }
 }
 
-template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, bool TLOAD, bool TSTORE, int XV = kXchF32>
+template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, bool TLOAD, bool TSTORE, int XV = kXchF32,
+          int MINB = 0>
 __global__ void __launch_bounds__(RowShape<N, TLOAD || TSTORE>::kThreads,
-                                  RowShape<N, TLOAD || TSTORE>::kMinBlocks)
+                                  MINB > 0 ? MINB : RowShape<N, TLOAD || TSTORE>::kMinBlocks)
 fft_rows_kernel(const RowArgs a) {
   static_assert(XV == kXchF32 || (!TLOAD && !TSTORE), "corner turns stage lines in FP32");
   using S = RowShape<N, TLOAD || TSTORE>;
@@ -537,18 +538,24 @@ cudaError_t launch_rows_tma_n(const RowArgs& a, cudaStream_t stream) {
 //   X[k1 + N1 k2] = sum_n2 W_4096^{n2 k2} W_N^{n2 k1} sum_n1 x[n2 + 4096 n1] W_N1^{n1 k1}.
 // Step 1: CTA c loads the n2-slab [c S, (c + 1) S) (S = 4096 / N1) of every
 //   block n1 -- N1 contiguous, coalesced segments -- runs the N1-point DFTs in
-//   registers, multiplies by W_N^{n2 k1} and writes row k1 into CTA k1's
-//   shared memory (the one exchange through distributed shared memory).
+//   registers, multiplies by W_N^{n2 k1} and sends row k1 to CTA k1's shared
+//   memory with asynchronous remote stores (st.async) that count their bytes
+//   on CTA k1's mbarrier: the one exchange through distributed shared memory,
+//   with no cluster barrier (whose release would wait for global stores).
 // Step 2: CTA k1 transforms its row (4096 points, local Stockham passes) and
 //   stores X[k1 + N1 k2] (stride N1; the CTAs of the group fill each sector).
-// The caller brackets each line with cluster barriers.
+// The caller initialises `bar` (one arrival) and makes it visible to the
+// cluster before the first line, and separates consecutive lines on the same
+// CTAs by a (relaxed) cluster barrier so no row is overwritten while in use.
 template <int N1, class TS, int MODE, bool SCALED>
-__device__ __forceinline__ void fourstep_line(const RowArgs& a, const TS* in, TS* out, float2* smem, int c,
-                                              int base_rank, bool active) {
+__device__ __forceinline__ void fourstep_line(const RowArgs& a, const TS* in, TS* out, float2* smem, uint64_t* bar,
+                                              uint32_t& phase, int c, int base_rank, bool active) {
   constexpr int N = N1 * 4096, S = 4096 / N1, NB = 16 / N1, P = kPointsPerThread;
   const int t = threadIdx.x;
   const float inv_n = 1.0f / float(N);
-  auto cluster = cooperative_groups::this_cluster();
+  // This CTA receives its row: 4096 points of 8 bytes, from all N1 CTAs.
+  if (t == 0) mbar_arrive_expect_tx(bar, 4096 * sizeof(float2));
+  const uint32_t smem_base = smem_addr(smem), bar_local = smem_addr(bar);
   float2 v[P];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
@@ -569,13 +576,16 @@ __device__ __forceinline__ void fourstep_line(const RowArgs& a, const TS* in, TS
 #pragma unroll
     for (int i = 0; i < N1; ++i) u[i] = v[b * N1 + i];
     Dft<N1>::run(u);
+    const uint32_t slot = smem_base + uint32_t(pad16(n2)) * sizeof(float2);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) {
       const float2 z = k1 == 0 ? u[0] : cmul(u[k1], __ldg(a.tw_4step + k1 * 4096 + n2));
-      *cluster.map_shared_rank(smem + pad16(n2), base_rank + k1) = z;
+      st_async_f2(mapa(slot, base_rank + k1), z, mapa(bar_local, base_rank + k1));
     }
   }
-  cluster.sync();
+  // The row is complete when all 32 KB have landed (bounded wait).
+  mbar_wait_bounded(bar, phase, a.status);
+  phase ^= 1;
 #pragma unroll
   for (int m = 0; m < P; ++m) v[m] = smem[pad16(t + 256 * m)];
   __syncthreads();
@@ -597,16 +607,21 @@ template <int N, class TS, int MODE, bool SCALED>
 __global__ void __launch_bounds__(256, BFP_MIN_BLOCKS) fft_fourstep_kernel(const RowArgs a) {
   constexpr int N1 = N / 4096;
   extern __shared__ float2 smem_fs[];
+  __shared__ __align__(8) uint64_t bar;
   auto cluster = cooperative_groups::this_cluster();
   const int c = int(cluster.block_rank());
   const long long line = blockIdx.x / N1;
   const TS* in = static_cast<const TS*>(a.in) + line * a.in_stride;
   TS* out = static_cast<TS*>(a.out) + line * a.out_stride;
-  cluster.sync();                  // every CTA running before its shared memory is written
-  // All writes into a CTA's shared memory happen before the barrier inside
-  // the line, so no closing barrier is needed (one would also wait for the
-  // line's global stores to drain).
-  fourstep_line<N1, TS, MODE, SCALED>(a, in, out, smem_fs, c, 0, true);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cluster.sync();                  // every CTA running, every barrier initialised
+  uint32_t phase = 0;
+  fourstep_line<N1, TS, MODE, SCALED>(a, in, out, smem_fs, &bar, phase, c, 0, true);
+  // No CTA leaves while a peer's asynchronous stores may still be in flight.
+  cluster_barrier_relaxed();
 }
 
 template <int N, class TS, int MODE, bool SCALED>
@@ -720,11 +735,11 @@ template <class TS, int MODE>
 cudaError_t launch_tc_n(const RowArgs& a, cudaStream_t stream);
 
 // Plain (one group per CTA, no prefetch) row kernel with an exchange variant.
-template <int N, class TIn, class TOut, int MODE, bool NAIVE, int XV>
+template <int N, class TIn, class TOut, int MODE, bool NAIVE, int XV, int MINB = 0>
 cudaError_t launch_rows_plain_x(const RowArgs& a, cudaStream_t stream) {
   using S = RowShape<N>;
   constexpr size_t kBytes = size_t(S::G) * XchSel<N, XV>::kLineBytes;
-  auto kern = fft_rows_kernel<N, TIn, TOut, MODE, NAIVE, false, false, false, XV>;
+  auto kern = fft_rows_kernel<N, TIn, TOut, MODE, NAIVE, false, false, false, XV, MINB>;
   static bool configured = false;
   if (!configured) {
     if (kBytes > 48 * 1024) {
@@ -759,6 +774,7 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
       constexpr bool kHalf = std::is_same<TIn, __half2>::value;
       switch (a.variant) {
         case kRowsPlainPP: return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF32PP>(a, stream);
+        case kRowsPlain4: return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF32, 4>(a, stream);
         case kRowsTmaPP: return launch_rows_tma_n<N, TIn, TOut, MODE, NAIVE, SCALED, kXchF32PP>(a, stream);
         case kRowsPlainH:
           if constexpr (kHalf) return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF16>(a, stream);

@@ -159,7 +159,8 @@ int rows_variant() {
   static const struct { const char* name; int code; } kNames[] = {
       {"tma", bfp::kRowsTma},         {"plain", bfp::kRowsPlain},    {"pp", bfp::kRowsPlainPP},
       {"h16", bfp::kRowsPlainH},      {"h16pp", bfp::kRowsPlainHPP}, {"tma_pp", bfp::kRowsTmaPP},
-      {"tma_h16", bfp::kRowsTmaH},    {"tma_h16pp", bfp::kRowsTmaHPP}, {"tc", bfp::kRowsTc}};
+      {"tma_h16", bfp::kRowsTmaH},    {"tma_h16pp", bfp::kRowsTmaHPP}, {"tc", bfp::kRowsTc},
+      {"plain4", bfp::kRowsPlain4}};
   for (const auto& k : kNames)
     if (std::strcmp(v, k.name) == 0) return k.code;
   return bfp::kRowsTma;
@@ -455,12 +456,13 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
   if (plan->many) {
     for (int c = plan->clusters; c >= 1 && candidates.size() < 4; c = c * 3 / 4) candidates.push_back(c);
   } else {
-    candidates = {bfp::kRowsPlain, bfp::kRowsTma, bfp::kRowsPlainPP, bfp::kRowsTmaPP};
+    candidates = {bfp::kRowsPlain, bfp::kRowsPlain4, bfp::kRowsTma, bfp::kRowsPlainPP, bfp::kRowsTmaPP};
     if (allow_fp16_exchange && (plan->dtype == BFPFFT_F16_BFP || plan->dtype == BFPFFT_F16_NAIVE)) {
       candidates.push_back(bfp::kRowsPlainH);
       candidates.push_back(bfp::kRowsPlainHPP);
       candidates.push_back(bfp::kRowsTmaH);
       candidates.push_back(bfp::kRowsTmaHPP);
+      if (plan->log2n == 12) candidates.push_back(bfp::kRowsTc);
     }
   }
   int st = BFPFFT_OK;

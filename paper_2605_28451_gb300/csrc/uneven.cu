@@ -30,7 +30,8 @@ constexpr int kClusterCtas = 16;
 constexpr int kSlab = 4096;     // points of one line per CTA (N >= 4096)
 
 template <class TS, int MODE, bool SCALED, int LOG2N>
-__device__ __noinline__ void run_task(const UnevenArgs& a, const UnevenTask& tk, int rank, float2* smem) {
+__device__ __noinline__ void run_task(const UnevenArgs& a, const UnevenTask& tk, int rank, float2* smem,
+                                      uint64_t* bar, uint32_t& phase) {
   constexpr int N = 1 << LOG2N;
   constexpr int P = kPointsPerThread, T = N / P;
   RowArgs ra{};
@@ -70,43 +71,42 @@ __device__ __noinline__ void run_task(const UnevenArgs& a, const UnevenTask& tk,
     ra.tw_line = a.tw[12];
     ra.tw_4step = a.tw4[LOG2N];
     fourstep_line<C, TS, MODE, SCALED>(ra, static_cast<const TS*>(a.in) + off, static_cast<TS*>(a.out) + off,
-                                       smem, rank - base, base, active);
+                                       smem, bar, phase, rank - base, base, active);
   }
-}
-
-// Cluster barrier without memory ordering: it only tells every CTA that its
-// peers are done with their shared memory (a release barrier would also wait
-// for the previous task's global stores to drain).
-__device__ __forceinline__ void cluster_barrier_relaxed() {
-  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
 }
 
 template <class TS, int MODE, bool SCALED>
 __global__ void __launch_bounds__(kCta, 3) uneven_kernel(const UnevenArgs a) {
   extern __shared__ float2 smem_u[];
+  __shared__ __align__(8) uint64_t bar;
   auto cluster = cooperative_groups::this_cluster();
   const int rank = int(cluster.block_rank());
   const int cluster_id = int(blockIdx.x) / kClusterCtas;
   const int clusters = int(gridDim.x) / kClusterCtas;
-  cluster.sync();                                        // all peers running before any DSMEM write
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cluster.sync();                                        // peers running, barriers initialised
+  uint32_t phase = 0;
   // Tasks hold 65,536 points each, so a static round-robin over the clusters
   // balances the work; no counter or broadcast is needed.
   for (int task = cluster_id; task < a.num_tasks; task += clusters) {
     const UnevenTask tk = a.tasks[task];
     switch (tk.log2n) {
-      case 4: run_task<TS, MODE, SCALED, 4>(a, tk, rank, smem_u); break;
-      case 5: run_task<TS, MODE, SCALED, 5>(a, tk, rank, smem_u); break;
-      case 6: run_task<TS, MODE, SCALED, 6>(a, tk, rank, smem_u); break;
-      case 7: run_task<TS, MODE, SCALED, 7>(a, tk, rank, smem_u); break;
-      case 8: run_task<TS, MODE, SCALED, 8>(a, tk, rank, smem_u); break;
-      case 9: run_task<TS, MODE, SCALED, 9>(a, tk, rank, smem_u); break;
-      case 10: run_task<TS, MODE, SCALED, 10>(a, tk, rank, smem_u); break;
-      case 11: run_task<TS, MODE, SCALED, 11>(a, tk, rank, smem_u); break;
-      case 12: run_task<TS, MODE, SCALED, 12>(a, tk, rank, smem_u); break;
-      case 13: run_task<TS, MODE, SCALED, 13>(a, tk, rank, smem_u); break;
-      case 14: run_task<TS, MODE, SCALED, 14>(a, tk, rank, smem_u); break;
-      case 15: run_task<TS, MODE, SCALED, 15>(a, tk, rank, smem_u); break;
-      case 16: run_task<TS, MODE, SCALED, 16>(a, tk, rank, smem_u); break;
+      case 4: run_task<TS, MODE, SCALED, 4>(a, tk, rank, smem_u, &bar, phase); break;
+      case 5: run_task<TS, MODE, SCALED, 5>(a, tk, rank, smem_u, &bar, phase); break;
+      case 6: run_task<TS, MODE, SCALED, 6>(a, tk, rank, smem_u, &bar, phase); break;
+      case 7: run_task<TS, MODE, SCALED, 7>(a, tk, rank, smem_u, &bar, phase); break;
+      case 8: run_task<TS, MODE, SCALED, 8>(a, tk, rank, smem_u, &bar, phase); break;
+      case 9: run_task<TS, MODE, SCALED, 9>(a, tk, rank, smem_u, &bar, phase); break;
+      case 10: run_task<TS, MODE, SCALED, 10>(a, tk, rank, smem_u, &bar, phase); break;
+      case 11: run_task<TS, MODE, SCALED, 11>(a, tk, rank, smem_u, &bar, phase); break;
+      case 12: run_task<TS, MODE, SCALED, 12>(a, tk, rank, smem_u, &bar, phase); break;
+      case 13: run_task<TS, MODE, SCALED, 13>(a, tk, rank, smem_u, &bar, phase); break;
+      case 14: run_task<TS, MODE, SCALED, 14>(a, tk, rank, smem_u, &bar, phase); break;
+      case 15: run_task<TS, MODE, SCALED, 15>(a, tk, rank, smem_u, &bar, phase); break;
+      case 16: run_task<TS, MODE, SCALED, 16>(a, tk, rank, smem_u, &bar, phase); break;
       default: break;
     }
     // A peer may write into this CTA's shared memory in the next task only

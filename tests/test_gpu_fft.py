@@ -56,7 +56,7 @@ def test_f32_forward_and_inverse(n, batch, rows_variant):
     assert metrics.rel_l2(ref_i, got_i) <= 1e-6
 
 
-ROW_VARIANTS = ["tma", "plain", "pp", "h16", "h16pp", "tma_pp", "tma_h16", "tma_h16pp", "tc"]
+ROW_VARIANTS = ["tma", "plain", "pp", "h16", "h16pp", "tma_pp", "tma_h16", "tma_h16pp", "tc", "plain4"]
 
 
 @pytest.fixture(params=ROW_VARIANTS)
