@@ -403,8 +403,14 @@ fft_rows_kernel(const RowArgs a) {
       if (ln < a.lines) Storage<TOut>::store(out + (long long)k * a.out_stride + ln,
                                              *cluster_slot<S>(smem_rows, l, pad16(k)));
     }
-    // Keep this CTA's shared memory alive until every peer has read it.
-    cluster_barrier<S>();
+    // Keep this CTA's shared memory alive until every peer has read it.  The
+    // peers' remote loads have completed once they arrive, so a relaxed
+    // barrier suffices (a release barrier would wait for the global stores).
+    if constexpr (S::C > 1) {
+      cluster_barrier_relaxed();
+    } else {
+      __syncthreads();
+    }
   } else if (active) {
     TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;
 #pragma unroll
