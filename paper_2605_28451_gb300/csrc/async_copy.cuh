@@ -77,6 +77,12 @@ __device__ __forceinline__ void st_async_f2(uint32_t remote_addr, float2 v, uint
                : "memory");
 }
 
+__device__ __forceinline__ void st_async_b32(uint32_t remote_addr, uint32_t v, uint32_t remote_bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(remote_addr), "r"(v),
+               "r"(remote_bar)
+               : "memory");
+}
+
 // Cluster barrier without memory ordering (only "everyone got here").
 __device__ __forceinline__ void cluster_barrier_relaxed() {
   asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");

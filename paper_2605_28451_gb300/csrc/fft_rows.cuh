@@ -33,6 +33,8 @@
 // then move 8 lines at a time: each CTA reads (or writes) a slab of k for all
 // 8 lines as 32-byte segments and exchanges the points with the owning CTA
 // through distributed shared memory, so a transpose costs no extra HBM pass.
+// On the store side every CTA pushes its points to the slab owners with
+// asynchronous remote stores (st.async) counted on the owner's mbarrier.
 //
 // Twiddles come from a per-length FP32 table generated on the GPU in FP64
 // (sincospi) and rounded once -- never by recurrence, which the paper
@@ -54,6 +56,12 @@
 namespace bfp {
 
 enum RowMode : int { kForward = 0, kInverse = 1, kCompress = 2 };
+
+__device__ __forceinline__ void Pushed<float2>::push(uint32_t addr, float2 v, uint32_t bar) { st_async_f2(addr, v, bar); }
+__device__ __forceinline__ void Pushed<__half2>::push(uint32_t addr, float2 v, uint32_t bar) {
+  const __half2 h = __float22half2_rn(v);
+  st_async_b32(addr, *reinterpret_cast<const uint32_t*>(&h), bar);
+}
 
 struct RowArgs {
   const void* in;
@@ -102,6 +110,9 @@ struct RowShape {
   // Cluster size of a corner-turn kernel: enough CTAs for 8 lines.
   static constexpr int C = TURN ? (G >= 8 ? 1 : 8 / G) : 1;
   static constexpr int kLinesPerCluster = C * G;
+  // Receive buffer of a corner-turned store: this CTA's slab of N / C points
+  // of every cluster line, 8 bytes per point (enough for any storage type).
+  static constexpr size_t kRecvBytes = TURN ? size_t(N / C) * kLinesPerCluster * sizeof(float2) : 0;
   // Resident CTAs per SM requested from the register allocator.
   static constexpr int kMinBlocks = kThreads >= 1024 ? 1 : (kThreads >= 512 ? 1 : BFP_MIN_BLOCKS);
 };
@@ -356,6 +367,16 @@ fft_rows_kernel(const RowArgs a) {
   constexpr int kSlab = N / S::C;                        // points per CTA in a corner turn
 
   float2 v[P];
+  __shared__ __align__(8) uint64_t recv_bar;
+  if constexpr (TSTORE) {
+    // The corner-turned store receives this CTA's slab of every cluster line
+    // by asynchronous stores counted on recv_bar.
+    if (threadIdx.x == 0) {
+      mbar_init(&recv_bar, 1);
+      mbar_arrive_expect_tx(&recv_bar, uint32_t(kSlab * S::kLinesPerCluster * sizeof(TOut)));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
   if constexpr (TLOAD) {
     // Gather: this CTA reads points [rank * kSlab, (rank + 1) * kSlab) of all
     // cluster lines, 8 consecutive lines (one 32 B segment in FP16) per point.
@@ -375,10 +396,12 @@ fft_rows_kernel(const RowArgs a) {
     for (int m = 0; m < P; ++m) v[m] = sm[pad16(t + T * m)];
     __syncthreads();
   } else if (active) {
+    if constexpr (TSTORE) cluster_barrier<S>();         // peers running, receive barriers set
     const TIn* in = static_cast<const TIn*>(a.in) + line * a.in_stride + t;
 #pragma unroll
     for (int m = 0; m < P; ++m) v[m] = Storage<TIn>::load(in + T * m);
   } else {
+    if constexpr (TSTORE) cluster_barrier<S>();
 #pragma unroll
     for (int m = 0; m < P; ++m) v[m] = make_float2(0.f, 0.f);
   }
@@ -390,26 +413,35 @@ fft_rows_kernel(const RowArgs a) {
   }
 
   if constexpr (TSTORE) {
-    // Stage the line, then scatter slabs of all cluster lines as segments.
-    // The last pass read shared memory before a barrier, so the slots are free.
+    // Push every point k of this line to the CTA owning slab k / kSlab, into
+    // its receive buffer at [k % kSlab][l]; then write this CTA's slab of all
+    // cluster lines as contiguous segments (8 lines per point).
+    unsigned char* recv = reinterpret_cast<unsigned char*>(smem_rows) + S::kSmemBytes;
+    const int l = int(line - line0);
+    const uint32_t recv_local = smem_addr(recv), bar_local = smem_addr(&recv_bar);
 #pragma unroll
-    for (int m = 0; m < P; ++m) sm[pad16(t + T * m)] = v[m];
-    cluster_barrier<S>();
-    TOut* out = static_cast<TOut*>(a.out);
-    for (int idx = threadIdx.x; idx < kSlab * S::kLinesPerCluster; idx += S::kThreads) {
-      const int l = idx % S::kLinesPerCluster;
-      const int k = rank * kSlab + idx / S::kLinesPerCluster;
-      const long long ln = line0 + l;
-      if (ln < a.lines) Storage<TOut>::store(out + (long long)k * a.out_stride + ln,
-                                             *cluster_slot<S>(smem_rows, l, pad16(k)));
+    for (int m = 0; m < P; ++m) {
+      const int k = t + T * m;
+      const int owner = k / kSlab;
+      const uint32_t slot = recv_local + uint32_t(((k % kSlab) * S::kLinesPerCluster + l) * sizeof(TOut));
+      if constexpr (S::C > 1) {
+        Pushed<TOut>::push(mapa(slot, uint32_t(owner)), v[m], mapa(bar_local, uint32_t(owner)));
+      } else {
+        Pushed<TOut>::push(slot, v[m], bar_local);
+      }
     }
-    // Keep this CTA's shared memory alive until every peer has read it.  The
-    // peers' remote loads have completed once they arrive, so a relaxed
-    // barrier suffices (a release barrier would wait for the global stores).
+    mbar_wait_bounded(&recv_bar, 0, a.status);
+    TOut* out = static_cast<TOut*>(a.out);
+    const TOut* staged = reinterpret_cast<const TOut*>(recv);
+    for (int idx = threadIdx.x; idx < kSlab * S::kLinesPerCluster; idx += S::kThreads) {
+      const int l2 = idx % S::kLinesPerCluster;
+      const int k = rank * kSlab + idx / S::kLinesPerCluster;
+      const long long ln = line0 + l2;
+      if (ln < a.lines) Pushed<TOut>::copy_out(out + (long long)k * a.out_stride + ln, staged + idx);
+    }
+    // No CTA leaves while its own asynchronous stores may still be in flight.
     if constexpr (S::C > 1) {
       cluster_barrier_relaxed();
-    } else {
-      __syncthreads();
     }
   } else if (active) {
     TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;
@@ -808,11 +840,11 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
       return launch_rows_tma_n<N, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
   }
   auto kern = fft_rows_kernel<N, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>;
-  if (S::kSmemBytes > 48 * 1024) {
+  constexpr size_t kBytes = S::kSmemBytes + (TSTORE ? S::kRecvBytes : 0);
+  if (kBytes > 48 * 1024) {
     static bool configured = false;   // attribute is per function; set once
     if (!configured) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           int(S::kSmemBytes));
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBytes));
       if (e != cudaSuccess) return e;
       configured = true;
     }
@@ -825,7 +857,7 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(grid));
     cfg.blockDim = dim3(S::kThreads);
-    cfg.dynamicSmemBytes = S::kSmemBytes;
+    cfg.dynamicSmemBytes = kBytes;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -837,7 +869,7 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
     if (e != cudaSuccess) return e;
   } else {
-    kern<<<dim3(unsigned(grid)), dim3(S::kThreads), S::kSmemBytes, stream>>>(a);
+    kern<<<dim3(unsigned(grid)), dim3(S::kThreads), kBytes, stream>>>(a);
   }
   return cudaGetLastError();
   }

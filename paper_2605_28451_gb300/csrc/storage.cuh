@@ -66,6 +66,21 @@ template <> struct Storage<Fp8x2<E5M2>> {
   __device__ __forceinline__ static float2 load_smem(const Fp8x2<E5M2>* p) { return load(p); }
 };
 
+// Push one output point (converted to its storage type) into another CTA's
+// shared memory with an asynchronous store counted on that CTA's mbarrier,
+// and copy such a staged point to HBM unchanged.
+template <class T> struct Pushed;
+template <> struct Pushed<float2> {
+  __device__ __forceinline__ static void push(uint32_t addr, float2 v, uint32_t bar);
+  __device__ __forceinline__ static void copy_out(float2* dst, const float2* src) { __stcs(dst, *src); }
+};
+template <> struct Pushed<__half2> {
+  __device__ __forceinline__ static void push(uint32_t addr, float2 v, uint32_t bar);
+  __device__ __forceinline__ static void copy_out(__half2* dst, const __half2* src) {
+    __stcs(reinterpret_cast<unsigned int*>(dst), *reinterpret_cast<const unsigned int*>(src));
+  }
+};
+
 // Naive FP16 output of an unshifted inverse (Section III-B): the unnormalised
 // result is stored to half first (overflowing to +-Inf beyond 65504) and only
 // then multiplied by 1/N, in half.
