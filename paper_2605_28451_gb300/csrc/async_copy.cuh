@@ -11,7 +11,14 @@
 namespace bfp {
 
 constexpr uint32_t kMaxPolls = 1u << 22;
+constexpr unsigned long long kMaxWaitNs = 1000000000ull;   // 1 s of wall time per wait
 constexpr int kStatusTimeout = 5;   // BFPFFT_ERR_TIMEOUT
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -54,9 +61,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for phase `parity` of `bar`; false (and status set) on expiry.
+// A try_wait may suspend the thread for a while, so the bound is wall time
+// (kMaxWaitNs) as well as a poll count.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
   for (uint32_t i = 0; i < kMaxPolls; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && global_ns() - t0 > kMaxWaitNs) break;
   }
   if (status != nullptr) atomicExch(status, kStatusTimeout);
   return false;
@@ -83,9 +95,30 @@ __device__ __forceinline__ void st_async_b32(uint32_t remote_addr, uint32_t v, u
                : "memory");
 }
 
+// Plain (synchronous) stores into a peer CTA's shared memory; ordered for the
+// peer by a following release / acquire cluster barrier.
+__device__ __forceinline__ void st_cluster_f2(uint32_t remote_addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(remote_addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_b32(uint32_t remote_addr, uint32_t v) {
+  asm volatile("st.shared::cluster.b32 [%0], %1;" ::"r"(remote_addr), "r"(v) : "memory");
+}
+
+// Split cluster barrier (non-aligned forms: safe after divergent code).
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
 // Cluster barrier without memory ordering (only "everyone got here").
 __device__ __forceinline__ void cluster_barrier_relaxed() {
-  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.arrive.relaxed;\n\tbarrier.cluster.wait;" ::: "memory");
 }
 
 }  // namespace bfp

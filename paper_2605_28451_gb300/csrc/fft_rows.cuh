@@ -57,10 +57,10 @@ namespace bfp {
 
 enum RowMode : int { kForward = 0, kInverse = 1, kCompress = 2 };
 
-__device__ __forceinline__ void Pushed<float2>::push(uint32_t addr, float2 v, uint32_t bar) { st_async_f2(addr, v, bar); }
-__device__ __forceinline__ void Pushed<__half2>::push(uint32_t addr, float2 v, uint32_t bar) {
+__device__ __forceinline__ void Pushed<float2>::push(uint32_t addr, float2 v) { st_cluster_f2(addr, v); }
+__device__ __forceinline__ void Pushed<__half2>::push(uint32_t addr, float2 v) {
   const __half2 h = __float22half2_rn(v);
-  st_async_b32(addr, *reinterpret_cast<const uint32_t*>(&h), bar);
+  st_cluster_b32(addr, *reinterpret_cast<const uint32_t*>(&h));
 }
 
 struct RowArgs {
@@ -112,7 +112,10 @@ struct RowShape {
   static constexpr int kLinesPerCluster = C * G;
   // Receive buffer of a corner-turned store: this CTA's slab of N / C points
   // of every cluster line, 8 bytes per point (enough for any storage type).
-  static constexpr size_t kRecvBytes = TURN ? size_t(N / C) * kLinesPerCluster * sizeof(float2) : 0;
+  // Where it does not fit beside the row buffers (N = 16384) the store stages
+  // in the row buffers and the slab owners pull instead.
+  static constexpr bool kPushTurn = TURN && (C == 1 || kSmemBytes + size_t(N / C) * kLinesPerCluster * 8 <= 200 * 1024);
+  static constexpr size_t kRecvBytes = kPushTurn ? size_t(N / C) * kLinesPerCluster * sizeof(float2) : 0;
   // Resident CTAs per SM requested from the register allocator.
   static constexpr int kMinBlocks = kThreads >= 1024 ? 1 : (kThreads >= 512 ? 1 : BFP_MIN_BLOCKS);
 };
@@ -367,16 +370,11 @@ fft_rows_kernel(const RowArgs a) {
   constexpr int kSlab = N / S::C;                        // points per CTA in a corner turn
 
   float2 v[P];
-  __shared__ __align__(8) uint64_t recv_bar;
-  if constexpr (TSTORE) {
-    // The corner-turned store receives this CTA's slab of every cluster line
-    // by asynchronous stores counted on recv_bar.
-    if (threadIdx.x == 0) {
-      mbar_init(&recv_bar, 1);
-      mbar_arrive_expect_tx(&recv_bar, uint32_t(kSlab * S::kLinesPerCluster * sizeof(TOut)));
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-  }
+  // A pushing corner-turned store writes into its peers' receive buffers
+  // after its own transform; this split barrier (arrive now, wait before the
+  // first push) makes sure every peer is running by then.
+  constexpr bool kEarlyArrive = TSTORE && !TLOAD && S::kPushTurn && S::C > 1;
+  if constexpr (kEarlyArrive) cluster_arrive_relaxed();
   if constexpr (TLOAD) {
     // Gather: this CTA reads points [rank * kSlab, (rank + 1) * kSlab) of all
     // cluster lines, 8 consecutive lines (one 32 B segment in FP16) per point.
@@ -396,12 +394,10 @@ fft_rows_kernel(const RowArgs a) {
     for (int m = 0; m < P; ++m) v[m] = sm[pad16(t + T * m)];
     __syncthreads();
   } else if (active) {
-    if constexpr (TSTORE) cluster_barrier<S>();         // peers running, receive barriers set
     const TIn* in = static_cast<const TIn*>(a.in) + line * a.in_stride + t;
 #pragma unroll
     for (int m = 0; m < P; ++m) v[m] = Storage<TIn>::load(in + T * m);
   } else {
-    if constexpr (TSTORE) cluster_barrier<S>();
 #pragma unroll
     for (int m = 0; m < P; ++m) v[m] = make_float2(0.f, 0.f);
   }
@@ -412,25 +408,58 @@ fft_rows_kernel(const RowArgs a) {
     row_compute_x<N, MODE, NAIVE, SCALED>(v, a, XchSel<N, XV>::make(base), t);
   }
 
-  if constexpr (TSTORE) {
+  if constexpr (TSTORE && !S::kPushTurn) {
+    // Stage the line, then every CTA pulls its slab of all cluster lines from
+    // the peers' row buffers and writes it as segments.  The last pass read
+    // shared memory before a barrier, so the slots are free.
+#pragma unroll
+    for (int m = 0; m < P; ++m) sm[pad16(t + T * m)] = v[m];
+    cluster_barrier<S>();
+    TOut* out = static_cast<TOut*>(a.out);
+    for (int idx = threadIdx.x; idx < kSlab * S::kLinesPerCluster; idx += S::kThreads) {
+      const int l2 = idx % S::kLinesPerCluster;
+      const int k = rank * kSlab + idx / S::kLinesPerCluster;
+      const long long ln = line0 + l2;
+      if (ln < a.lines) Storage<TOut>::store(out + (long long)k * a.out_stride + ln,
+                                             *cluster_slot<S>(smem_rows, l2, pad16(k)));
+    }
+    // Keep this CTA's shared memory alive until every peer has read it.  The
+    // peers' remote loads have completed once they arrive, so a relaxed
+    // barrier suffices (a release barrier would wait for the global stores).
+    cluster_barrier_relaxed();
+  } else if constexpr (TSTORE) {
     // Push every point k of this line to the CTA owning slab k / kSlab, into
-    // its receive buffer at [k % kSlab][l]; then write this CTA's slab of all
-    // cluster lines as contiguous segments (8 lines per point).
+    // its receive buffer at [k % kSlab][l] (plain stores, remote ones through
+    // distributed shared memory), then write this CTA's slab of all cluster
+    // lines as contiguous segments (8 lines per point).  The receive buffers
+    // lie beyond the row buffers, so pushes never disturb a peer's transform.
     unsigned char* recv = reinterpret_cast<unsigned char*>(smem_rows) + S::kSmemBytes;
     const int l = int(line - line0);
-    const uint32_t recv_local = smem_addr(recv), bar_local = smem_addr(&recv_bar);
+    const uint32_t recv_local = smem_addr(recv);
+    if constexpr (S::C > 1) {
+      // (After a corner-turned load every peer is known to be running.)
+      if constexpr (kEarlyArrive) cluster_wait_acquire();
 #pragma unroll
-    for (int m = 0; m < P; ++m) {
-      const int k = t + T * m;
-      const int owner = k / kSlab;
-      const uint32_t slot = recv_local + uint32_t(((k % kSlab) * S::kLinesPerCluster + l) * sizeof(TOut));
-      if constexpr (S::C > 1) {
-        Pushed<TOut>::push(mapa(slot, uint32_t(owner)), v[m], mapa(bar_local, uint32_t(owner)));
-      } else {
-        Pushed<TOut>::push(slot, v[m], bar_local);
+      for (int m = 0; m < P; ++m) {
+        const int k = t + T * m;
+        const uint32_t slot = recv_local + uint32_t(((k % kSlab) * S::kLinesPerCluster + l) * sizeof(TOut));
+        Pushed<TOut>::push(mapa(slot, uint32_t(k / kSlab)), v[m]);
       }
+      // Release the pushes to their owners; no global store is pending here,
+      // so the release is cheap.  After this no CTA touches a peer's memory.
+      cluster_arrive_release();
+      cluster_wait_acquire();
+    } else {
+      // One CTA holds all the cluster's lines: local shared-memory stores.
+      (void)recv_local;
+      TOut* local = reinterpret_cast<TOut*>(recv);
+#pragma unroll
+      for (int m = 0; m < P; ++m) {
+        const int k = t + T * m;
+        Storage<TOut>::store_smem(local + k * S::kLinesPerCluster + l, v[m]);
+      }
+      __syncthreads();
     }
-    mbar_wait_bounded(&recv_bar, 0, a.status);
     TOut* out = static_cast<TOut*>(a.out);
     const TOut* staged = reinterpret_cast<const TOut*>(recv);
     for (int idx = threadIdx.x; idx < kSlab * S::kLinesPerCluster; idx += S::kThreads) {
@@ -438,10 +467,6 @@ fft_rows_kernel(const RowArgs a) {
       const int k = rank * kSlab + idx / S::kLinesPerCluster;
       const long long ln = line0 + l2;
       if (ln < a.lines) Pushed<TOut>::copy_out(out + (long long)k * a.out_stride + ln, staged + idx);
-    }
-    // No CTA leaves while its own asynchronous stores may still be in flight.
-    if constexpr (S::C > 1) {
-      cluster_barrier_relaxed();
     }
   } else if (active) {
     TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;
