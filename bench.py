@@ -303,7 +303,8 @@ def run_ours(args):
             "roofline": {
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "fft_rows_kernel<4096, half2, half2, forward> (plain, FP32 exchange)",
+                "kernel": "fft_rows_kernel<4096, half2, half2, forward> (plain4_l2: FP32 exchange, 4 CTAs/SM, "
+                          "L2 prefetch one wave ahead)",
                 "kernel_source_hash": _kernel_source_hash(),
                 "bytes_per_launch": alg_bytes, "launch_ms": round(fwd_avg, 5), "peak_source": peak_kind,
                 "frac_of_8tbs_nominal": round(achieved / 8000.0, 4),

@@ -117,8 +117,9 @@ int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, c
 
 /*
  * Autotuner (not in the paper).  Times the candidate kernels of this plan on
- * its own shape -- a uniform plan: the row-kernel variants (plain or bulk-copy
- * pipelined, one or two FP32 exchange buffers; with allow_fp16_exchange != 0
+ * its own shape -- a uniform plan: the row-kernel variants (plain, with or
+ * without an L2 prefetch one wave ahead, at 3 or 4 CTAs per SM, or bulk-copy
+ * pipelined; one or two FP32 exchange buffers; with allow_fp16_exchange != 0
  * and FP16 storage also the FP16 shared-memory exchanges, which round at
  * every pass and so change the results within the FP16 error budget); an
  * uneven plan: the number of persistent clusters -- on scratch buffers it

@@ -74,6 +74,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a multiple
+// of 16); no completion to wait for.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Address of the same shared-memory location in CTA `rank` of the cluster.
 __device__ __forceinline__ uint32_t mapa(uint32_t local, uint32_t rank) {
   uint32_t r;
@@ -93,27 +99,6 @@ __device__ __forceinline__ void st_async_b32(uint32_t remote_addr, uint32_t v, u
   asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(remote_addr), "r"(v),
                "r"(remote_bar)
                : "memory");
-}
-
-// Plain (synchronous) stores into a peer CTA's shared memory; ordered for the
-// peer by a following release / acquire cluster barrier.
-__device__ __forceinline__ void st_cluster_f2(uint32_t remote_addr, float2 v) {
-  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(remote_addr), "f"(v.x), "f"(v.y) : "memory");
-}
-
-__device__ __forceinline__ void st_cluster_b32(uint32_t remote_addr, uint32_t v) {
-  asm volatile("st.shared::cluster.b32 [%0], %1;" ::"r"(remote_addr), "r"(v) : "memory");
-}
-
-// Split cluster barrier (non-aligned forms: safe after divergent code).
-__device__ __forceinline__ void cluster_arrive_relaxed() {
-  asm volatile("barrier.cluster.arrive.relaxed;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_arrive_release() {
-  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait_acquire() {
-  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
 }
 
 // Cluster barrier without memory ordering (only "everyone got here").

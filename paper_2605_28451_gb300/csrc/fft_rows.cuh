@@ -33,8 +33,6 @@
 // then move 8 lines at a time: each CTA reads (or writes) a slab of k for all
 // 8 lines as 32-byte segments and exchanges the points with the owning CTA
 // through distributed shared memory, so a transpose costs no extra HBM pass.
-// On the store side every CTA pushes its points to the slab owners with
-// asynchronous remote stores (st.async) counted on the owner's mbarrier.
 //
 // Twiddles come from a per-length FP32 table generated on the GPU in FP64
 // (sincospi) and rounded once -- never by recurrence, which the paper
@@ -57,12 +55,6 @@ namespace bfp {
 
 enum RowMode : int { kForward = 0, kInverse = 1, kCompress = 2 };
 
-__device__ __forceinline__ void Pushed<float2>::push(uint32_t addr, float2 v) { st_cluster_f2(addr, v); }
-__device__ __forceinline__ void Pushed<__half2>::push(uint32_t addr, float2 v) {
-  const __half2 h = __float22half2_rn(v);
-  st_cluster_b32(addr, *reinterpret_cast<const uint32_t*>(&h));
-}
-
 struct RowArgs {
   const void* in;
   void* out;
@@ -78,16 +70,21 @@ struct RowArgs {
   const float2* tw_line;   // N >= 8192: pass-major table of the 4096-point row transforms
   const float2* tw_4step;  // N >= 8192: four-step twiddles T[k1][n2] = W_N^{n2 k1}
   const void* tc_b;        // tensor-core variant: 16-point DFT matrix, real form, FP16 [32][32]
+  int pf_ahead;            // > 0: each CTA prefetches into L2 the lines of the CTA pf_ahead blocks later
 };
 
 // Row-kernel variants for dense rows of length <= 4096 (chosen by
 // BFPFFT_ROWS or the tuner): bulk-copy pipelined persistent kernel or plain
 // one-group-per-CTA kernel, with an FP32 or FP16 shared-memory exchange in
-// one buffer or two (ping-pong).  FP16 exchanges apply to FP16 storage only;
-// anything not applicable falls back to kRowsTma.
+// one buffer or two (ping-pong), at 3 or 4 CTAs per SM, with or without a
+// bulk L2 prefetch of the lines of the CTA one resident wave later (_l2).
+// FP16 exchanges apply to FP16 storage only.  Shapes a variant does not
+// cover run the pipelined kernel (TMA family) or the generic kernel (the
+// rest; the _l2 prefetch applies there too when rows are dense).
 enum RowVariant : int {
   kRowsTma = 0, kRowsPlain = 1, kRowsPlainPP = 2, kRowsPlainH = 3, kRowsPlainHPP = 4,
-  kRowsTmaPP = 5, kRowsTmaH = 6, kRowsTmaHPP = 7, kRowsTc = 8, kRowsPlain4 = 9
+  kRowsTmaPP = 5, kRowsTmaH = 6, kRowsTmaHPP = 7, kRowsTc = 8, kRowsPlain4 = 9,
+  kRowsPlainL2 = 10, kRowsPlain4L2 = 11
 };
 
 constexpr int kPointsPerThread = 16;
@@ -110,12 +107,6 @@ struct RowShape {
   // Cluster size of a corner-turn kernel: enough CTAs for 8 lines.
   static constexpr int C = TURN ? (G >= 8 ? 1 : 8 / G) : 1;
   static constexpr int kLinesPerCluster = C * G;
-  // Receive buffer of a corner-turned store: this CTA's slab of N / C points
-  // of every cluster line, 8 bytes per point (enough for any storage type).
-  // Where it does not fit beside the row buffers (N = 16384) the store stages
-  // in the row buffers and the slab owners pull instead.
-  static constexpr bool kPushTurn = TURN && (C == 1 || kSmemBytes + size_t(N / C) * kLinesPerCluster * 8 <= 200 * 1024);
-  static constexpr size_t kRecvBytes = kPushTurn ? size_t(N / C) * kLinesPerCluster * sizeof(float2) : 0;
   // Resident CTAs per SM requested from the register allocator.
   static constexpr int kMinBlocks = kThreads >= 1024 ? 1 : (kThreads >= 512 ? 1 : BFP_MIN_BLOCKS);
 };
@@ -370,11 +361,6 @@ fft_rows_kernel(const RowArgs a) {
   constexpr int kSlab = N / S::C;                        // points per CTA in a corner turn
 
   float2 v[P];
-  // A pushing corner-turned store writes into its peers' receive buffers
-  // after its own transform; this split barrier (arrive now, wait before the
-  // first push) makes sure every peer is running by then.
-  constexpr bool kEarlyArrive = TSTORE && !TLOAD && S::kPushTurn && S::C > 1;
-  if constexpr (kEarlyArrive) cluster_arrive_relaxed();
   if constexpr (TLOAD) {
     // Gather: this CTA reads points [rank * kSlab, (rank + 1) * kSlab) of all
     // cluster lines, 8 consecutive lines (one 32 B segment in FP16) per point.
@@ -394,6 +380,13 @@ fft_rows_kernel(const RowArgs a) {
     for (int m = 0; m < P; ++m) v[m] = sm[pad16(t + T * m)];
     __syncthreads();
   } else if (active) {
+    if (a.pf_ahead > 0 && threadIdx.x == 0) {
+      // Dense rows: one bulk L2 prefetch of the lines of the CTA that will
+      // take this one's slot about one resident wave later.
+      const long long l0 = ((long long)blockIdx.x + a.pf_ahead) * S::G;
+      const long long cnt = a.lines - l0 < S::G ? a.lines - l0 : S::G;
+      if (cnt > 0) prefetch_l2_bulk(static_cast<const TIn*>(a.in) + l0 * N, uint32_t(cnt * N * sizeof(TIn)));
+    }
     const TIn* in = static_cast<const TIn*>(a.in) + line * a.in_stride + t;
 #pragma unroll
     for (int m = 0; m < P; ++m) v[m] = Storage<TIn>::load(in + T * m);
@@ -408,65 +401,30 @@ fft_rows_kernel(const RowArgs a) {
     row_compute_x<N, MODE, NAIVE, SCALED>(v, a, XchSel<N, XV>::make(base), t);
   }
 
-  if constexpr (TSTORE && !S::kPushTurn) {
+  if constexpr (TSTORE) {
     // Stage the line, then every CTA pulls its slab of all cluster lines from
     // the peers' row buffers and writes it as segments.  The last pass read
-    // shared memory before a barrier, so the slots are free.
+    // shared memory before a barrier, so the slots are free.  (Pulling with
+    // remote loads measured faster than pushing with remote stores, whose
+    // release barrier waits for every store to land.)
 #pragma unroll
     for (int m = 0; m < P; ++m) sm[pad16(t + T * m)] = v[m];
     cluster_barrier<S>();
     TOut* out = static_cast<TOut*>(a.out);
     for (int idx = threadIdx.x; idx < kSlab * S::kLinesPerCluster; idx += S::kThreads) {
-      const int l2 = idx % S::kLinesPerCluster;
+      const int l = idx % S::kLinesPerCluster;
       const int k = rank * kSlab + idx / S::kLinesPerCluster;
-      const long long ln = line0 + l2;
+      const long long ln = line0 + l;
       if (ln < a.lines) Storage<TOut>::store(out + (long long)k * a.out_stride + ln,
-                                             *cluster_slot<S>(smem_rows, l2, pad16(k)));
+                                             *cluster_slot<S>(smem_rows, l, pad16(k)));
     }
     // Keep this CTA's shared memory alive until every peer has read it.  The
     // peers' remote loads have completed once they arrive, so a relaxed
     // barrier suffices (a release barrier would wait for the global stores).
-    cluster_barrier_relaxed();
-  } else if constexpr (TSTORE) {
-    // Push every point k of this line to the CTA owning slab k / kSlab, into
-    // its receive buffer at [k % kSlab][l] (plain stores, remote ones through
-    // distributed shared memory), then write this CTA's slab of all cluster
-    // lines as contiguous segments (8 lines per point).  The receive buffers
-    // lie beyond the row buffers, so pushes never disturb a peer's transform.
-    unsigned char* recv = reinterpret_cast<unsigned char*>(smem_rows) + S::kSmemBytes;
-    const int l = int(line - line0);
-    const uint32_t recv_local = smem_addr(recv);
     if constexpr (S::C > 1) {
-      // (After a corner-turned load every peer is known to be running.)
-      if constexpr (kEarlyArrive) cluster_wait_acquire();
-#pragma unroll
-      for (int m = 0; m < P; ++m) {
-        const int k = t + T * m;
-        const uint32_t slot = recv_local + uint32_t(((k % kSlab) * S::kLinesPerCluster + l) * sizeof(TOut));
-        Pushed<TOut>::push(mapa(slot, uint32_t(k / kSlab)), v[m]);
-      }
-      // Release the pushes to their owners; no global store is pending here,
-      // so the release is cheap.  After this no CTA touches a peer's memory.
-      cluster_arrive_release();
-      cluster_wait_acquire();
+      cluster_barrier_relaxed();
     } else {
-      // One CTA holds all the cluster's lines: local shared-memory stores.
-      (void)recv_local;
-      TOut* local = reinterpret_cast<TOut*>(recv);
-#pragma unroll
-      for (int m = 0; m < P; ++m) {
-        const int k = t + T * m;
-        Storage<TOut>::store_smem(local + k * S::kLinesPerCluster + l, v[m]);
-      }
       __syncthreads();
-    }
-    TOut* out = static_cast<TOut*>(a.out);
-    const TOut* staged = reinterpret_cast<const TOut*>(recv);
-    for (int idx = threadIdx.x; idx < kSlab * S::kLinesPerCluster; idx += S::kThreads) {
-      const int l2 = idx % S::kLinesPerCluster;
-      const int k = rank * kSlab + idx / S::kLinesPerCluster;
-      const long long ln = line0 + l2;
-      if (ln < a.lines) Pushed<TOut>::copy_out(out + (long long)k * a.out_stride + ln, staged + idx);
     }
   } else if (active) {
     TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;
@@ -797,24 +755,34 @@ cudaError_t launch_cluster_n(const RowArgs& a, cudaStream_t stream) {
 template <class TS, int MODE>
 cudaError_t launch_tc_n(const RowArgs& a, cudaStream_t stream);
 
-// Plain (one group per CTA, no prefetch) row kernel with an exchange variant.
+// Plain row kernel (one group per CTA) with an exchange variant; optionally
+// each CTA prefetches into L2 the lines of the CTA one resident wave later.
 template <int N, class TIn, class TOut, int MODE, bool NAIVE, int XV, int MINB = 0>
-cudaError_t launch_rows_plain_x(const RowArgs& a, cudaStream_t stream) {
+cudaError_t launch_rows_plain_x(const RowArgs& a, cudaStream_t stream, bool l2_prefetch = false) {
   using S = RowShape<N>;
   constexpr size_t kBytes = size_t(S::G) * XchSel<N, XV>::kLineBytes;
   auto kern = fft_rows_kernel<N, TIn, TOut, MODE, NAIVE, false, false, false, XV, MINB>;
   static bool configured = false;
+  static int resident = 0;   // CTAs of this kernel resident on the whole GPU
   if (!configured) {
     if (kBytes > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBytes));
       if (e != cudaSuccess) return e;
     }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::kThreads, kBytes);
+    if (e != cudaSuccess) return e;
+    resident = sms * per_sm;
     configured = true;
   }
   if (a.lines <= 0) return cudaSuccess;
   const long long grid = (a.lines + S::G - 1) / S::G;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  kern<<<dim3(unsigned(grid)), dim3(S::kThreads), kBytes, stream>>>(a);
+  RowArgs b = a;
+  b.pf_ahead = l2_prefetch ? resident : 0;
+  kern<<<dim3(unsigned(grid)), dim3(S::kThreads), kBytes, stream>>>(b);
   return cudaGetLastError();
 }
 
@@ -838,6 +806,8 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
       switch (a.variant) {
         case kRowsPlainPP: return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF32PP>(a, stream);
         case kRowsPlain4: return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF32, 4>(a, stream);
+        case kRowsPlainL2: return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF32>(a, stream, true);
+        case kRowsPlain4L2: return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF32, 4>(a, stream, true);
         case kRowsTmaPP: return launch_rows_tma_n<N, TIn, TOut, MODE, NAIVE, SCALED, kXchF32PP>(a, stream);
         case kRowsPlainH:
           if constexpr (kHalf) return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF16>(a, stream);
@@ -860,24 +830,39 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
       }
     }
   }
+  // Shapes the switch does not cover (scaled FP8 storage, compress mode,
+  // mixed storage, corner turns, strided rows) run the pipelined kernel for
+  // the TMA family and the generic kernel otherwise.
+  const bool tma_family =
+      a.variant == kRowsTma || a.variant == kRowsTmaPP || a.variant == kRowsTmaH || a.variant == kRowsTmaHPP;
   if constexpr (!TLOAD && !TSTORE && N >= 256 && TmaLayout<N, TIn, 2>::kBytes <= kTmaSmemBudget) {
-    if (a.variant != kRowsPlain && a.in_stride == N && a.out_stride == N)
+    if (tma_family && a.in_stride == N && a.out_stride == N)
       return launch_rows_tma_n<N, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
   }
   auto kern = fft_rows_kernel<N, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>;
-  constexpr size_t kBytes = S::kSmemBytes + (TSTORE ? S::kRecvBytes : 0);
-  if (kBytes > 48 * 1024) {
-    static bool configured = false;   // attribute is per function; set once
-    if (!configured) {
+  constexpr size_t kBytes = S::kSmemBytes;
+  static bool configured = false;   // attributes are per function; set once
+  static int resident = 0;          // CTAs of this kernel resident on the whole GPU
+  if (!configured) {
+    if (kBytes > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBytes));
       if (e != cudaSuccess) return e;
-      configured = true;
     }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::kThreads, kBytes);
+    if (e != cudaSuccess) return e;
+    resident = sms * (per_sm > 0 ? per_sm : 1);
+    configured = true;
   }
   if (a.lines <= 0) return cudaSuccess;
   const long long clusters = (a.lines + S::kLinesPerCluster - 1) / S::kLinesPerCluster;
   const long long grid = clusters * S::C;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  RowArgs b = a;
+  const bool l2 = a.variant == kRowsPlainL2 || a.variant == kRowsPlain4L2;
+  b.pf_ahead = (l2 && !TLOAD && a.in_stride == N) ? resident : 0;
   if constexpr (S::C > 1) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(grid));
@@ -891,10 +876,10 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, b);
     if (e != cudaSuccess) return e;
   } else {
-    kern<<<dim3(unsigned(grid)), dim3(S::kThreads), kBytes, stream>>>(a);
+    kern<<<dim3(unsigned(grid)), dim3(S::kThreads), kBytes, stream>>>(b);
   }
   return cudaGetLastError();
   }

@@ -150,17 +150,19 @@ int get_status_word(int** out) {
 }
 
 // Row-kernel variant from BFPFFT_ROWS (tma, plain, pp, h16, h16pp, tma_pp,
-// tma_h16, tma_h16pp).  Unset: the plain kernel with an FP32 exchange, the
-// fastest exact-numerics variant measured on GB300 (FP32 storage at 98.7% of
-// the measured copy bandwidth); unknown names: the pipelined kernel.
+// tma_h16, tma_h16pp, tc, plain4, plain_l2, plain4_l2).  Unset: plain4_l2,
+// the plain kernel with an FP32 exchange at 4 CTAs per SM whose CTAs prefetch
+// into L2 the lines of the CTA one resident wave later -- the fastest
+// exact-numerics variant measured on GB300; unknown names: the pipelined
+// kernel.
 int rows_variant() {
   const char* v = std::getenv("BFPFFT_ROWS");
-  if (v == nullptr) return bfp::kRowsPlain;
+  if (v == nullptr) return bfp::kRowsPlain4L2;
   static const struct { const char* name; int code; } kNames[] = {
       {"tma", bfp::kRowsTma},         {"plain", bfp::kRowsPlain},    {"pp", bfp::kRowsPlainPP},
       {"h16", bfp::kRowsPlainH},      {"h16pp", bfp::kRowsPlainHPP}, {"tma_pp", bfp::kRowsTmaPP},
       {"tma_h16", bfp::kRowsTmaH},    {"tma_h16pp", bfp::kRowsTmaHPP}, {"tc", bfp::kRowsTc},
-      {"plain4", bfp::kRowsPlain4}};
+      {"plain4", bfp::kRowsPlain4},   {"plain_l2", bfp::kRowsPlainL2}, {"plain4_l2", bfp::kRowsPlain4L2}};
   for (const auto& k : kNames)
     if (std::strcmp(v, k.name) == 0) return k.code;
   return bfp::kRowsTma;
@@ -456,7 +458,8 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
   if (plan->many) {
     for (int c = plan->clusters; c >= 1 && candidates.size() < 4; c = c * 3 / 4) candidates.push_back(c);
   } else {
-    candidates = {bfp::kRowsPlain, bfp::kRowsPlain4, bfp::kRowsTma, bfp::kRowsPlainPP, bfp::kRowsTmaPP};
+    candidates = {bfp::kRowsPlain4L2, bfp::kRowsPlainL2, bfp::kRowsPlain, bfp::kRowsPlain4,
+                  bfp::kRowsTma,        bfp::kRowsPlainPP, bfp::kRowsTmaPP};
     if (allow_fp16_exchange && (plan->dtype == BFPFFT_F16_BFP || plan->dtype == BFPFFT_F16_NAIVE)) {
       candidates.push_back(bfp::kRowsPlainH);
       candidates.push_back(bfp::kRowsPlainHPP);

@@ -27,7 +27,6 @@ template <> struct Storage<float2> {
   __device__ __forceinline__ static float2 load(const float2* p) { return __ldcs(p); }
   __device__ __forceinline__ static void store(float2* p, float2 v) { __stcs(p, v); }
   __device__ __forceinline__ static float2 load_smem(const float2* p) { return *p; }
-  __device__ __forceinline__ static void store_smem(float2* p, float2 v) { *p = v; }
 };
 
 template <> struct Storage<__half2> {
@@ -41,7 +40,6 @@ template <> struct Storage<__half2> {
     __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
   }
   __device__ __forceinline__ static float2 load_smem(const __half2* p) { return __half22float2(*p); }
-  __device__ __forceinline__ static void store_smem(__half2* p, float2 v) { *p = __float22half2_rn(v); }
 };
 
 template <> struct Storage<Fp8x2<E4M3>> {
@@ -66,21 +64,6 @@ template <> struct Storage<Fp8x2<E5M2>> {
     p->bits = __nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E5M2);
   }
   __device__ __forceinline__ static float2 load_smem(const Fp8x2<E5M2>* p) { return load(p); }
-};
-
-// Push one output point (converted to its storage type) into a CTA's shared
-// memory (a shared::cluster address), and copy such a staged point to HBM
-// unchanged.
-template <class T> struct Pushed;
-template <> struct Pushed<float2> {
-  __device__ __forceinline__ static void push(uint32_t addr, float2 v);
-  __device__ __forceinline__ static void copy_out(float2* dst, const float2* src) { __stcs(dst, *src); }
-};
-template <> struct Pushed<__half2> {
-  __device__ __forceinline__ static void push(uint32_t addr, float2 v);
-  __device__ __forceinline__ static void copy_out(__half2* dst, const __half2* src) {
-    __stcs(reinterpret_cast<unsigned int*>(dst), *reinterpret_cast<const unsigned int*>(src));
-  }
 };
 
 // Naive FP16 output of an unshifted inverse (Section III-B): the unnormalised

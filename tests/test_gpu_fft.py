@@ -56,7 +56,8 @@ def test_f32_forward_and_inverse(n, batch, rows_variant):
     assert metrics.rel_l2(ref_i, got_i) <= 1e-6
 
 
-ROW_VARIANTS = ["tma", "plain", "pp", "h16", "h16pp", "tma_pp", "tma_h16", "tma_h16pp", "tc", "plain4"]
+ROW_VARIANTS = ["tma", "plain", "pp", "h16", "h16pp", "tma_pp", "tma_h16", "tma_h16pp", "tc", "plain4", "plain_l2",
+                "plain4_l2"]
 
 
 @pytest.fixture(params=ROW_VARIANTS)
@@ -198,3 +199,28 @@ def test_fp8_storage_matches_oracle_rounding(dtype, fmt, n, rows_variant):
     got_i = run_fft(got, dtype, B.INVERSE)
     exact_i = F.ifft(got * 2.0 ** out_exp)
     fp8_close(got_i, exact_i, fmt)
+
+
+@pytest.mark.parametrize("variant", ["plain_l2", "plain4_l2"])
+@pytest.mark.parametrize("n,batch", [(4096, 1999), (256, 16 * 977 + 5)])
+def test_prefetching_variants_over_many_waves(variant, n, batch, monkeypatch):
+    """Variants whose CTAs prefetch into L2 the lines of the CTA one resident
+    wave later: batches several waves deep with a ragged tail (the last
+    prefetches are clipped to the array), sampled lines (all of them at
+    N = 256) against the oracle, forward and inverse."""
+    import torch
+    monkeypatch.setenv("BFPFFT_ROWS", variant)
+    x = storage_round(synth.complex_gaussian(batch, n, seed=batch), B.F16_BFP)
+    rows = np.arange(batch) if n <= 256 else np.unique(
+        np.r_[0, 1, 455, 456, 457, 607, 608, batch // 2, batch - 2, batch - 1,
+              np.random.default_rng(5).integers(0, batch, 8)])
+    for direction, ref_fn in ((B.FORWARD, F.fft), (B.INVERSE, F.ifft)):
+        plan = B.bfpfft_plan_create(n, batch, B.F16_BFP, direction)
+        xin = to_device(x, B.F16_BFP)
+        out = torch.empty_like(xin)
+        B.bfpfft_exec(plan, xin, out)
+        torch.cuda.synchronize()
+        assert B.bfpfft_device_status() == B.OK
+        got = from_device(out[torch.as_tensor(rows, device=out.device)], B.F16_BFP)
+        ok, worst = fp16_elementwise_ok(got, ref_fn(x[rows]))
+        assert ok, (variant, n, direction, worst)

@@ -138,7 +138,7 @@ def test_tuner_uniform_and_uneven(tmp_path, monkeypatch):
     monkeypatch.delenv("BFPFFT_ROWS", raising=False)
     plan = B.bfpfft_plan_create(4096, 512, B.F16_BFP, B.FORWARD)
     chosen, ms = B.bfpfft_plan_tune(plan, allow_fp16_exchange=False)
-    assert chosen in (0, 1, 2, 5, 9) and ms > 0
+    assert chosen in (0, 1, 2, 5, 9, 10, 11) and ms > 0
     text = (tmp_path / "tune.txt").read_text()
     assert "/n4096/" in text and f" {chosen} " in text
     x = storage_round(synth.complex_gaussian(512, 4096, seed=9), B.F16_BFP)
