@@ -101,6 +101,16 @@ __device__ __forceinline__ void st_async_b32(uint32_t remote_addr, uint32_t v, u
                : "memory");
 }
 
+// 32-bit loads and stores of shared::cluster addresses (from mapa).
+__device__ __forceinline__ uint32_t ld_cluster_b32(uint32_t addr) {
+  uint32_t r;
+  asm volatile("ld.shared::cluster.b32 %0, [%1];" : "=r"(r) : "r"(addr) : "memory");
+  return r;
+}
+__device__ __forceinline__ void st_cluster_b32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared::cluster.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
 // Cluster barrier without memory ordering (only "everyone got here").
 __device__ __forceinline__ void cluster_barrier_relaxed() {
   asm volatile("barrier.cluster.arrive.relaxed;\n\tbarrier.cluster.wait;" ::: "memory");

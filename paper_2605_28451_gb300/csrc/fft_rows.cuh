@@ -332,6 +332,32 @@ __device__ __forceinline__ float2* cluster_slot(float2* local_base, int l, int i
   }
 }
 
+// Load of slot `idx` of line `l` of the cluster: ld.shared::cluster through
+// mapa for a peer's row buffer, a plain shared load when C == 1.
+template <class S>
+__device__ __forceinline__ float2 cluster_load(float2* local_base, int l, int idx) {
+  float2* p = local_base + (l % S::G) * S::kSmemPerLine + idx;
+  if constexpr (S::C > 1) {
+    const uint32_t addr = mapa(smem_addr(p), uint32_t(l / S::G));
+    float2 r;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(addr) : "memory");
+    return r;
+  } else {
+    return *p;
+  }
+}
+
+template <class S>
+__device__ __forceinline__ void cluster_store(float2* local_base, int l, int idx, float2 v) {
+  float2* p = local_base + (l % S::G) * S::kSmemPerLine + idx;
+  if constexpr (S::C > 1) {
+    const uint32_t addr = mapa(smem_addr(p), uint32_t(l / S::G));
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+  } else {
+    *p = v;
+  }
+}
+
 template <class S>
 __device__ __forceinline__ void cluster_barrier() {
   if constexpr (S::C > 1) {
@@ -363,21 +389,96 @@ fft_rows_kernel(const RowArgs a) {
   float2 v[P];
   if constexpr (TLOAD) {
     // Gather: this CTA reads points [rank * kSlab, (rank + 1) * kSlab) of all
-    // cluster lines, 8 consecutive lines (one 32 B segment in FP16) per point.
+    // cluster lines and writes each line's values into the row buffer of the
+    // CTA that transforms it.  With 8 lines per cluster a thread owns two
+    // points and reads each point's 8 lines as one contiguous segment (32 B in
+    // FP16), so a warp's remote stores go to one CTA, 32 consecutive points.
+    static_assert(kSlab * S::kLinesPerCluster == P * S::kThreads, "one slot per thread and point");
     const TIn* in = static_cast<const TIn*>(a.in);
-    // Every CTA of the cluster must be running before its shared memory is written.
-    cluster_barrier<S>();
-    for (int idx = threadIdx.x; idx < kSlab * S::kLinesPerCluster; idx += S::kThreads) {
-      const int l = idx % S::kLinesPerCluster;
-      const int k = rank * kSlab + idx / S::kLinesPerCluster;
-      const long long ln = line0 + l;
-      const float2 x = ln < a.lines ? Storage<TIn>::load(in + (long long)k * a.in_stride + ln)
-                                    : make_float2(0.f, 0.f);
-      *cluster_slot<S>(smem_rows, l, pad16(k)) = x;
+    if constexpr (S::kLinesPerCluster == 8 && std::is_same<TIn, __half2>::value) {
+      // FP16 input moves as raw half2 words (exact): half the bytes.
+      constexpr int Q = kSlab / S::kThreads;
+      const bool seg = line0 + 8 <= a.lines && a.in_stride % 4 == 0;
+      uint32_t x[Q][8];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int k = rank * kSlab + int(threadIdx.x) + S::kThreads * q;
+        const __half2* src = in + (long long)k * a.in_stride + line0;
+        if (seg) {
+          seg8_load_raw(src, x[q]);
+        } else {
+#pragma unroll
+          for (int l = 0; l < 8; ++l)
+            x[q][l] = line0 + l < a.lines ? __ldcs(reinterpret_cast<const unsigned int*>(src + l)) : 0u;
+        }
+      }
+      cluster_barrier<S>();
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int k = rank * kSlab + int(threadIdx.x) + S::kThreads * q;
+#pragma unroll
+        for (int l = 0; l < 8; ++l) {
+          // Line l's row buffer, read as 32-bit words (the first half of it).
+          uint32_t* slot = reinterpret_cast<uint32_t*>(smem_rows + (l % S::G) * S::kSmemPerLine) + pad16(k);
+          if constexpr (S::C > 1) {
+            st_cluster_b32(mapa(smem_addr(slot), uint32_t(l / S::G)), x[q][l]);
+          } else {
+            *slot = x[q][l];
+          }
+        }
+      }
+    } else if constexpr (S::kLinesPerCluster == 8) {
+      constexpr int Q = kSlab / S::kThreads;   // points per thread (2)
+      const bool seg = line0 + 8 <= a.lines && a.in_stride % (16 / sizeof(TIn)) == 0;
+      float2 x[Q][8];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int k = rank * kSlab + int(threadIdx.x) + S::kThreads * q;
+        const TIn* src = in + (long long)k * a.in_stride + line0;
+        if (seg) {
+          Seg8<TIn>::load(src, x[q]);
+        } else {
+#pragma unroll
+          for (int l = 0; l < 8; ++l)
+            x[q][l] = line0 + l < a.lines ? Storage<TIn>::load(src + l) : make_float2(0.f, 0.f);
+        }
+      }
+      // Every CTA of the cluster must be running before its shared memory is written.
+      cluster_barrier<S>();
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int k = rank * kSlab + int(threadIdx.x) + S::kThreads * q;
+#pragma unroll
+        for (int l = 0; l < 8; ++l) cluster_store<S>(smem_rows, l, pad16(k), x[q][l]);
+      }
+    } else {
+      float2 x[P];
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        const int idx = threadIdx.x + i * S::kThreads;
+        const int l = idx % S::kLinesPerCluster;
+        const int k = rank * kSlab + idx / S::kLinesPerCluster;
+        const long long ln = line0 + l;
+        x[i] = ln < a.lines ? Storage<TIn>::load(in + (long long)k * a.in_stride + ln) : make_float2(0.f, 0.f);
+      }
+      cluster_barrier<S>();
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        const int idx = threadIdx.x + i * S::kThreads;
+        const int l = idx % S::kLinesPerCluster;
+        const int k = rank * kSlab + idx / S::kLinesPerCluster;
+        cluster_store<S>(smem_rows, l, pad16(k), x[i]);
+      }
     }
     cluster_barrier<S>();
+    if constexpr (S::kLinesPerCluster == 8 && std::is_same<TIn, __half2>::value) {
+      const uint32_t* sh = reinterpret_cast<const uint32_t*>(sm);
 #pragma unroll
-    for (int m = 0; m < P; ++m) v[m] = sm[pad16(t + T * m)];
+      for (int m = 0; m < P; ++m) v[m] = bits_half2(sh[pad16(t + T * m)]);
+    } else {
+#pragma unroll
+      for (int m = 0; m < P; ++m) v[m] = sm[pad16(t + T * m)];
+    }
     __syncthreads();
   } else if (active) {
     if (a.pf_ahead > 0 && threadIdx.x == 0) {
@@ -401,7 +502,48 @@ fft_rows_kernel(const RowArgs a) {
     row_compute_x<N, MODE, NAIVE, SCALED>(v, a, XchSel<N, XV>::make(base), t);
   }
 
-  if constexpr (TSTORE) {
+  if constexpr (TSTORE && S::kLinesPerCluster == 8 && std::is_same<TOut, __half2>::value) {
+    // FP16 output: the line is staged already rounded to half2 (the one
+    // rounding it gets anyway), so the pull moves half the bytes.
+    uint32_t* sh = reinterpret_cast<uint32_t*>(sm);
+#pragma unroll
+    for (int m = 0; m < P; ++m) sh[pad16(t + T * m)] = half2_bits(v[m]);
+    cluster_barrier<S>();
+    constexpr int Q = kSlab / S::kThreads;   // points per thread (2)
+    const bool seg = line0 + 8 <= a.lines && a.out_stride % 4 == 0;
+    __half2* out = static_cast<__half2*>(a.out);
+    uint32_t w[Q][8];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int k = rank * kSlab + int(threadIdx.x) + S::kThreads * q;
+#pragma unroll
+      for (int l = 0; l < 8; ++l) {
+        const uint32_t* slot = reinterpret_cast<const uint32_t*>(smem_rows + (l % S::G) * S::kSmemPerLine) + pad16(k);
+        if constexpr (S::C > 1) {
+          w[q][l] = ld_cluster_b32(mapa(smem_addr(slot), uint32_t(l / S::G)));
+        } else {
+          w[q][l] = *slot;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int k = rank * kSlab + int(threadIdx.x) + S::kThreads * q;
+      __half2* dst = out + (long long)k * a.out_stride + line0;
+      if (seg) {
+        seg8_store_raw(dst, w[q]);
+      } else {
+#pragma unroll
+        for (int l = 0; l < 8; ++l)
+          if (line0 + l < a.lines) __stcs(reinterpret_cast<unsigned int*>(dst + l), w[q][l]);
+      }
+    }
+    if constexpr (S::C > 1) {
+      cluster_barrier_relaxed();
+    } else {
+      __syncthreads();
+    }
+  } else if constexpr (TSTORE) {
     // Stage the line, then every CTA pulls its slab of all cluster lines from
     // the peers' row buffers and writes it as segments.  The last pass read
     // shared memory before a barrier, so the slots are free.  (Pulling with
@@ -410,13 +552,52 @@ fft_rows_kernel(const RowArgs a) {
 #pragma unroll
     for (int m = 0; m < P; ++m) sm[pad16(t + T * m)] = v[m];
     cluster_barrier<S>();
+    // With 8 lines per cluster a thread owns two points of this CTA's slab:
+    // it loads each point's value from the 8 lines (a warp's loads go to one
+    // CTA, 32 consecutive points) and writes them as one contiguous 8-line
+    // segment of output row k (32 B in FP16).  All loads are in flight before
+    // the first store.
+    static_assert(kSlab * S::kLinesPerCluster == P * S::kThreads, "one slot per thread and point");
     TOut* out = static_cast<TOut*>(a.out);
-    for (int idx = threadIdx.x; idx < kSlab * S::kLinesPerCluster; idx += S::kThreads) {
-      const int l = idx % S::kLinesPerCluster;
-      const int k = rank * kSlab + idx / S::kLinesPerCluster;
-      const long long ln = line0 + l;
-      if (ln < a.lines) Storage<TOut>::store(out + (long long)k * a.out_stride + ln,
-                                             *cluster_slot<S>(smem_rows, l, pad16(k)));
+    if constexpr (S::kLinesPerCluster == 8) {
+      constexpr int Q = kSlab / S::kThreads;   // points per thread (2)
+      const bool seg = line0 + 8 <= a.lines && a.out_stride % (16 / sizeof(TOut)) == 0;
+      float2 w[Q][8];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int k = rank * kSlab + int(threadIdx.x) + S::kThreads * q;
+#pragma unroll
+        for (int l = 0; l < 8; ++l) w[q][l] = cluster_load<S>(smem_rows, l, pad16(k));
+      }
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int k = rank * kSlab + int(threadIdx.x) + S::kThreads * q;
+        TOut* dst = out + (long long)k * a.out_stride + line0;
+        if (seg) {
+          Seg8<TOut>::store(dst, w[q]);
+        } else {
+#pragma unroll
+          for (int l = 0; l < 8; ++l)
+            if (line0 + l < a.lines) Storage<TOut>::store(dst + l, w[q][l]);
+        }
+      }
+    } else {
+      float2 w[P];
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        const int idx = threadIdx.x + i * S::kThreads;
+        const int l = idx % S::kLinesPerCluster;
+        const int k = rank * kSlab + idx / S::kLinesPerCluster;
+        w[i] = cluster_load<S>(smem_rows, l, pad16(k));
+      }
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        const int idx = threadIdx.x + i * S::kThreads;
+        const int l = idx % S::kLinesPerCluster;
+        const int k = rank * kSlab + idx / S::kLinesPerCluster;
+        const long long ln = line0 + l;
+        if (ln < a.lines) Storage<TOut>::store(out + (long long)k * a.out_stride + ln, w[i]);
+      }
     }
     // Keep this CTA's shared memory alive until every peer has read it.  The
     // peers' remote loads have completed once they arrive, so a relaxed

@@ -66,6 +66,71 @@ template <> struct Storage<Fp8x2<E5M2>> {
   __device__ __forceinline__ static float2 load_smem(const Fp8x2<E5M2>* p) { return load(p); }
 };
 
+// Eight consecutive complex values (one 8-line segment of a corner-turned
+// row) moved as 16-byte vectors: two for FP16, four for FP32.  The address
+// must be 16-byte aligned.
+template <class T> struct Seg8;
+template <> struct Seg8<float2> {
+  __device__ __forceinline__ static void load(const float2* p, float2 (&v)[8]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 q = __ldcs(reinterpret_cast<const float4*>(p) + i);
+      v[2 * i] = make_float2(q.x, q.y);
+      v[2 * i + 1] = make_float2(q.z, q.w);
+    }
+  }
+  __device__ __forceinline__ static void store(float2* p, const float2 (&v)[8]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      __stcs(reinterpret_cast<float4*>(p) + i, make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y));
+  }
+};
+// Raw FP16 segments: eight half2 words as two 16-byte vectors.
+__device__ __forceinline__ void seg8_load_raw(const __half2* p, uint32_t (&w)[8]) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const uint4 q = __ldcs(reinterpret_cast<const uint4*>(p) + i);
+    w[4 * i] = q.x;
+    w[4 * i + 1] = q.y;
+    w[4 * i + 2] = q.z;
+    w[4 * i + 3] = q.w;
+  }
+}
+__device__ __forceinline__ void seg8_store_raw(__half2* p, const uint32_t (&w)[8]) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+    __stcs(reinterpret_cast<uint4*>(p) + i, make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]));
+}
+__device__ __forceinline__ uint32_t half2_bits(float2 v) {
+  const __half2 h = __float22half2_rn(v);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ float2 bits_half2(uint32_t u) { return __half22float2(*reinterpret_cast<const __half2*>(&u)); }
+
+template <> struct Seg8<__half2> {
+  __device__ __forceinline__ static void load(const __half2* p, float2 (&v)[8]) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const uint4 q = __ldcs(reinterpret_cast<const uint4*>(p) + i);
+      const unsigned int w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[4 * i + j] = __half22float2(*reinterpret_cast<const __half2*>(&w[j]));
+    }
+  }
+  __device__ __forceinline__ static void store(__half2* p, const float2 (&v)[8]) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      unsigned int w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const __half2 h = __float22half2_rn(v[4 * i + j]);
+        w[j] = *reinterpret_cast<const unsigned int*>(&h);
+      }
+      __stcs(reinterpret_cast<uint4*>(p) + i, make_uint4(w[0], w[1], w[2], w[3]));
+    }
+  }
+};
+
 // Naive FP16 output of an unshifted inverse (Section III-B): the unnormalised
 // result is stored to half first (overflowing to +-Inf beyond 65504) and only
 // then multiplied by 1/N, in half.

@@ -64,7 +64,7 @@ def test_make_filter(n, norm):
 
 
 @pytest.mark.parametrize("n_az", [8, 45])
-@pytest.mark.parametrize("n_rg", [256, 2048, 4096])
+@pytest.mark.parametrize("n_rg", [256, 512, 1024, 2048, 4096, 8192, 16384])
 @pytest.mark.parametrize("transpose", [False, True])
 @pytest.mark.parametrize("raw_dtype,out_dtype", [(B.F32, B.F32), (B.F32, B.F16_BFP), (B.F16_BFP, B.F16_BFP),
                                                  (B.F16_BFP, B.F32)])
@@ -85,7 +85,7 @@ def test_range_compress(n_az, n_rg, transpose, raw_dtype, out_dtype):
         assert ok, worst
 
 
-@pytest.mark.parametrize("n_az", [256, 4096])
+@pytest.mark.parametrize("n_az", [256, 1024, 4096, 16384])
 @pytest.mark.parametrize("n_rg", [8, 45])
 @pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("rc_dtype,img_dtype", [(B.F32, B.F32), (B.F16_BFP, B.F16_BFP), (B.F16_BFP, B.F32)])
