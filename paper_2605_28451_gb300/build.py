@@ -34,6 +34,7 @@ SOURCES = [
     "metrics_noalloc.cu",
     "uneven.cu",
     "pt_metrics.cu",
+    "transpose.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -27,5 +27,10 @@ cudaError_t launch_sar_nn(int log2n, bool in16, bool out16, bool naive, const Ro
 cudaError_t launch_sar_nt(int log2n, bool in16, bool out16, bool naive, const RowArgs& a, cudaStream_t s);
 cudaError_t launch_sar_tt(int log2n, bool in16, bool out16, bool naive, const RowArgs& a, cudaStream_t s);
 
+// out[c][r] = in[r][c] for a row-major [rows][cols] array of 4- or 8-byte
+// elements (half2 / float2).
+cudaError_t launch_transpose(const void* in, void* out, long long rows, long long cols, int elem_bytes,
+                             cudaStream_t s);
+
 
 }  // namespace bfp

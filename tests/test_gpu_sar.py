@@ -25,6 +25,15 @@ def _lib(cuda_ready):
     B.lib()
 
 
+@pytest.fixture(params=["split", "fused"])
+def sar_turn(request, monkeypatch):
+    """Both corner-turn forms: dense rows plus a tiled transpose through
+    scratch, or the on-chip turn through cluster shared memory."""
+    monkeypatch.setenv("BFPFFT_SAR_TURN", request.param)
+    yield request.param
+    assert B.bfpfft_device_status() == B.OK
+
+
 def gpu_filter(ref: np.ndarray, peak_normalise: bool):
     import torch
     n = ref.shape[0]
@@ -68,7 +77,7 @@ def test_make_filter(n, norm):
 @pytest.mark.parametrize("transpose", [False, True])
 @pytest.mark.parametrize("raw_dtype,out_dtype", [(B.F32, B.F32), (B.F32, B.F16_BFP), (B.F16_BFP, B.F16_BFP),
                                                  (B.F16_BFP, B.F32)])
-def test_range_compress(n_az, n_rg, transpose, raw_dtype, out_dtype):
+def test_range_compress(n_az, n_rg, transpose, raw_dtype, out_dtype, sar_turn):
     sc = synth.point_target_scene(n_az, n_rg, aperture=16, targets=[(n_az // 2, n_rg // 2, 1.0)],
                                   noise_seed=n_az + n_rg)
     ref_r = synth.centred_reference(synth.range_chirp()[: min(480, n_rg // 2)], n_rg)
@@ -89,7 +98,7 @@ def test_range_compress(n_az, n_rg, transpose, raw_dtype, out_dtype):
 @pytest.mark.parametrize("n_rg", [8, 45])
 @pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("rc_dtype,img_dtype", [(B.F32, B.F32), (B.F16_BFP, B.F16_BFP), (B.F16_BFP, B.F32)])
-def test_azimuth_compress(n_az, n_rg, layout, rc_dtype, img_dtype):
+def test_azimuth_compress(n_az, n_rg, layout, rc_dtype, img_dtype, sar_turn):
     rng = np.random.default_rng(n_az + n_rg)
     rc = rng.standard_normal((n_az, n_rg)) + 1j * rng.standard_normal((n_az, n_rg))
     rc = storage_round(rc, rc_dtype)
