@@ -744,20 +744,59 @@ cudaError_t launch_rows_tma_n(const RowArgs& a, cudaStream_t stream) {
 //   memory with asynchronous remote stores (st.async) that count their bytes
 //   on CTA k1's mbarrier: the one exchange through distributed shared memory,
 //   with no cluster barrier (whose release would wait for global stores).
-// Step 2: CTA k1 transforms its row (4096 points, local Stockham passes) and
-//   stores X[k1 + N1 k2] (stride N1; the CTAs of the group fill each sector).
-// The caller initialises `bar` (one arrival) and makes it visible to the
-// cluster before the first line, and separates consecutive lines on the same
-// CTAs by a (relaxed) cluster barrier so no row is overwritten while in use.
+// Step 2: CTA k1 transforms its row (4096 points, local Stockham passes).
+// Step 3 (N1 >= 8): natural-order output, 4096 contiguous points per CTA: CTA
+//   k1 sends X[k1 + N1 k2] to the output buffer of CTA k2 / S with st.async
+//   counted on that CTA's second mbarrier (a warp's 32 values go to one CTA,
+//   contiguous; FP16 storage sends the rounded half2 words, the one rounding
+//   the store makes anyway), waits for its own 4096 points and writes them
+//   with coalesced stores.  For N1 = 16 storing X[k1 + N1 k2] straight from
+//   step 2 scatters every warp store over 32 sectors (35-40 % slower); for
+//   N1 <= 4 the direct strided store is faster than the exchange, which makes
+//   each CTA wait for its whole group.
+// Both exchanges only wait on data, never on a cluster barrier.  A CTA's row
+// buffer is free again once it has sent its step-3 values, and its output
+// buffer once it has stored them; no peer can send into either for the next
+// line before receiving this CTA's contributions to that line, so lines on
+// the same CTAs need no barrier in between.
+// The caller provides `smem` with a row buffer of pad16(4096) points followed
+// by the output buffer (fourstep_smem_bytes in all), initialises `bar` and
+// `bar_out` (one arrival each) and makes them visible to the cluster before
+// the first line.
+template <class TS> struct FsSend {           // step-3 send type: float2, or half2 words for FP16 storage
+  using Word = float2;
+};
+template <> struct FsSend<__half2> {
+  using Word = uint32_t;
+};
+// Shared memory of a four-step line: the row buffer, and for N1 >= 8 the
+// output buffer of N1 padded segments of S = 4096 / N1 words.
+template <class TS, int N1>
+__host__ __device__ constexpr size_t fourstep_smem_bytes() {
+  using Word = typename FsSend<TS>::Word;
+  constexpr int kPad = sizeof(Word) == 4 ? 2 : 1;
+  return size_t(pad16(4096)) * sizeof(float2) + (N1 >= 8 ? size_t(N1) * (4096 / N1 + kPad) * sizeof(Word) : 0);
+}
+
 template <int N1, class TS, int MODE, bool SCALED>
 __device__ __forceinline__ void fourstep_line(const RowArgs& a, const TS* in, TS* out, float2* smem, uint64_t* bar,
-                                              uint32_t& phase, int c, int base_rank, bool active) {
+                                              uint64_t* bar_out, uint32_t& phase, int c, int base_rank,
+                                              bool active) {
   constexpr int N = N1 * 4096, S = 4096 / N1, NB = 16 / N1, P = kPointsPerThread;
   const int t = threadIdx.x;
   const float inv_n = 1.0f / float(N);
-  // This CTA receives its row: 4096 points of 8 bytes, from all N1 CTAs.
-  if (t == 0) mbar_arrive_expect_tx(bar, 4096 * sizeof(float2));
+  // This CTA receives its row and its output range: 4096 points of 8 bytes
+  // each, from all N1 CTAs.
+  constexpr bool kOutXch = N1 >= 8;
+  using Word = typename FsSend<TS>::Word;
+  constexpr int kPadOut = sizeof(Word) == 4 ? 2 : 1;    // conflict-free gather
+  if (t == 0) {
+    mbar_arrive_expect_tx(bar, 4096 * sizeof(float2));
+    if constexpr (kOutXch) mbar_arrive_expect_tx(bar_out, 4096 * sizeof(Word));
+  }
+  float2* smem_out = smem + pad16(4096);
   const uint32_t smem_base = smem_addr(smem), bar_local = smem_addr(bar);
+  const uint32_t out_base = smem_addr(smem_out), bar_out_local = smem_addr(bar_out);
   float2 v[P];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
@@ -787,7 +826,6 @@ __device__ __forceinline__ void fourstep_line(const RowArgs& a, const TS* in, TS
   }
   // The row is complete when all 32 KB have landed (bounded wait).
   mbar_wait_bounded(bar, phase, a.status);
-  phase ^= 1;
 #pragma unroll
   for (int m = 0; m < P; ++m) v[m] = smem[pad16(t + 256 * m)];
   __syncthreads();
@@ -797,9 +835,43 @@ __device__ __forceinline__ void fourstep_line(const RowArgs& a, const TS* in, TS
     if (MODE == kInverse) v[m] = cconj(v[m]);
     if (SCALED) v[m] = cscale(v[m], a.out_scale);
   }
-  if (active) {
+  if constexpr (!kOutXch) {
+    phase ^= 1;
+    if (active) {
 #pragma unroll
-    for (int m = 0; m < P; ++m) Storage<TS>::store(out + c + N1 * (t + 256 * m), v[m]);
+      for (int m = 0; m < P; ++m) Storage<TS>::store(out + c + N1 * (t + 256 * m), v[m]);
+    }
+  } else {
+    // The owner's buffer holds the values as [k1][k2 mod S] with kPadOut
+    // padding slots per segment, so a warp's 32 sends are contiguous; the
+    // owner gathers output position j = (k2 mod S) N1 + k1 from slot
+    // k1 (S + kPadOut) + j / N1.
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      const int k2 = t + 256 * m;
+      const uint32_t slot = out_base + uint32_t(c * (S + kPadOut) + k2 % S) * uint32_t(sizeof(Word));
+      const uint32_t dst = uint32_t(base_rank + k2 / S);
+      if constexpr (sizeof(Word) == 4) {
+        st_async_b32(mapa(slot, dst), half2_bits(v[m]), mapa(bar_out_local, dst));
+      } else {
+        st_async_f2(mapa(slot, dst), v[m], mapa(bar_out_local, dst));
+      }
+    }
+    mbar_wait_bounded(bar_out, phase, a.status);
+    phase ^= 1;
+    if (active) {
+      const Word* ob = reinterpret_cast<const Word*>(smem_out);
+#pragma unroll
+      for (int m = 0; m < P; ++m) {
+        const int j = t + 256 * m;
+        const Word w = ob[(j % N1) * (S + kPadOut) + j / N1];
+        if constexpr (sizeof(Word) == 4) {
+          __stcs(reinterpret_cast<unsigned int*>(out + c * 4096 + j), w);
+        } else {
+          Storage<TS>::store(out + c * 4096 + j, w);
+        }
+      }
+    }
   }
 }
 
@@ -809,7 +881,7 @@ template <int N, class TS, int MODE, bool SCALED>
 __global__ void __launch_bounds__(256, BFP_MIN_BLOCKS) fft_fourstep_kernel(const RowArgs a) {
   constexpr int N1 = N / 4096;
   extern __shared__ float2 smem_fs[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar, bar_out;
   auto cluster = cooperative_groups::this_cluster();
   const int c = int(cluster.block_rank());
   const long long line = blockIdx.x / N1;
@@ -817,11 +889,12 @@ __global__ void __launch_bounds__(256, BFP_MIN_BLOCKS) fft_fourstep_kernel(const
   TS* out = static_cast<TS*>(a.out) + line * a.out_stride;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
+    mbar_init(&bar_out, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   cluster.sync();                  // every CTA running, every barrier initialised
   uint32_t phase = 0;
-  fourstep_line<N1, TS, MODE, SCALED>(a, in, out, smem_fs, &bar, phase, c, 0, true);
+  fourstep_line<N1, TS, MODE, SCALED>(a, in, out, smem_fs, &bar, &bar_out, phase, c, 0, true);
   // No CTA leaves while a peer's asynchronous stores may still be in flight.
   cluster_barrier_relaxed();
 }
@@ -829,7 +902,7 @@ __global__ void __launch_bounds__(256, BFP_MIN_BLOCKS) fft_fourstep_kernel(const
 template <int N, class TS, int MODE, bool SCALED>
 cudaError_t launch_fourstep_n(const RowArgs& a, cudaStream_t stream) {
   constexpr int N1 = N / 4096;
-  constexpr size_t kBytes = size_t(pad16(4096)) * sizeof(float2);
+  constexpr size_t kBytes = fourstep_smem_bytes<TS, N / 4096>();
   auto kern = fft_fourstep_kernel<N, TS, MODE, SCALED>;
   static bool configured = false;
   if (!configured) {
@@ -837,6 +910,8 @@ cudaError_t launch_fourstep_n(const RowArgs& a, cudaStream_t stream) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
     }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBytes));
+    if (e != cudaSuccess) return e;
     configured = true;
   }
   if (a.lines <= 0) return cudaSuccess;

@@ -71,20 +71,21 @@ __device__ __noinline__ void run_task(const UnevenArgs& a, const UnevenTask& tk,
     ra.tw_line = a.tw[12];
     ra.tw_4step = a.tw4[LOG2N];
     fourstep_line<C, TS, MODE, SCALED>(ra, static_cast<const TS*>(a.in) + off, static_cast<TS*>(a.out) + off,
-                                       smem, bar, phase, rank - base, base, active);
+                                       smem, bar, bar + 1, phase, rank - base, base, active);
   }
 }
 
 template <class TS, int MODE, bool SCALED>
 __global__ void __launch_bounds__(kCta, 3) uneven_kernel(const UnevenArgs a) {
   extern __shared__ float2 smem_u[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar[2];   // row and output exchanges of four-step lines
   auto cluster = cooperative_groups::this_cluster();
   const int rank = int(cluster.block_rank());
   const int cluster_id = int(blockIdx.x) / kClusterCtas;
   const int clusters = int(gridDim.x) / kClusterCtas;
   if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   cluster.sync();                                        // peers running, barriers initialised
@@ -94,19 +95,19 @@ __global__ void __launch_bounds__(kCta, 3) uneven_kernel(const UnevenArgs a) {
   for (int task = cluster_id; task < a.num_tasks; task += clusters) {
     const UnevenTask tk = a.tasks[task];
     switch (tk.log2n) {
-      case 4: run_task<TS, MODE, SCALED, 4>(a, tk, rank, smem_u, &bar, phase); break;
-      case 5: run_task<TS, MODE, SCALED, 5>(a, tk, rank, smem_u, &bar, phase); break;
-      case 6: run_task<TS, MODE, SCALED, 6>(a, tk, rank, smem_u, &bar, phase); break;
-      case 7: run_task<TS, MODE, SCALED, 7>(a, tk, rank, smem_u, &bar, phase); break;
-      case 8: run_task<TS, MODE, SCALED, 8>(a, tk, rank, smem_u, &bar, phase); break;
-      case 9: run_task<TS, MODE, SCALED, 9>(a, tk, rank, smem_u, &bar, phase); break;
-      case 10: run_task<TS, MODE, SCALED, 10>(a, tk, rank, smem_u, &bar, phase); break;
-      case 11: run_task<TS, MODE, SCALED, 11>(a, tk, rank, smem_u, &bar, phase); break;
-      case 12: run_task<TS, MODE, SCALED, 12>(a, tk, rank, smem_u, &bar, phase); break;
-      case 13: run_task<TS, MODE, SCALED, 13>(a, tk, rank, smem_u, &bar, phase); break;
-      case 14: run_task<TS, MODE, SCALED, 14>(a, tk, rank, smem_u, &bar, phase); break;
-      case 15: run_task<TS, MODE, SCALED, 15>(a, tk, rank, smem_u, &bar, phase); break;
-      case 16: run_task<TS, MODE, SCALED, 16>(a, tk, rank, smem_u, &bar, phase); break;
+      case 4: run_task<TS, MODE, SCALED, 4>(a, tk, rank, smem_u, bar, phase); break;
+      case 5: run_task<TS, MODE, SCALED, 5>(a, tk, rank, smem_u, bar, phase); break;
+      case 6: run_task<TS, MODE, SCALED, 6>(a, tk, rank, smem_u, bar, phase); break;
+      case 7: run_task<TS, MODE, SCALED, 7>(a, tk, rank, smem_u, bar, phase); break;
+      case 8: run_task<TS, MODE, SCALED, 8>(a, tk, rank, smem_u, bar, phase); break;
+      case 9: run_task<TS, MODE, SCALED, 9>(a, tk, rank, smem_u, bar, phase); break;
+      case 10: run_task<TS, MODE, SCALED, 10>(a, tk, rank, smem_u, bar, phase); break;
+      case 11: run_task<TS, MODE, SCALED, 11>(a, tk, rank, smem_u, bar, phase); break;
+      case 12: run_task<TS, MODE, SCALED, 12>(a, tk, rank, smem_u, bar, phase); break;
+      case 13: run_task<TS, MODE, SCALED, 13>(a, tk, rank, smem_u, bar, phase); break;
+      case 14: run_task<TS, MODE, SCALED, 14>(a, tk, rank, smem_u, bar, phase); break;
+      case 15: run_task<TS, MODE, SCALED, 15>(a, tk, rank, smem_u, bar, phase); break;
+      case 16: run_task<TS, MODE, SCALED, 16>(a, tk, rank, smem_u, bar, phase); break;
       default: break;
     }
     // A peer may write into this CTA's shared memory in the next task only
@@ -121,7 +122,7 @@ cudaError_t launch_typed(const UnevenArgs& a, int clusters, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(clusters * kClusterCtas));
   cfg.blockDim = dim3(kCta);
-  cfg.dynamicSmemBytes = kUnevenSmemBytes;
+  cfg.dynamicSmemBytes = uneven_smem_bytes<TS>();
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -138,14 +139,14 @@ cudaError_t configure_typed(int* max_clusters) {
   auto kern = uneven_kernel<TS, MODE, SCALED>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
-  if (kUnevenSmemBytes > 48 * 1024) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kUnevenSmemBytes));
+  if (uneven_smem_bytes<TS>() > 48 * 1024) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(uneven_smem_bytes<TS>()));
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kClusterCtas);
   cfg.blockDim = dim3(kCta);
-  cfg.dynamicSmemBytes = kUnevenSmemBytes;
+  cfg.dynamicSmemBytes = uneven_smem_bytes<TS>();
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = kClusterCtas;

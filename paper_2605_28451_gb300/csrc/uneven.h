@@ -26,7 +26,10 @@ struct UnevenArgs {
   int* status;
 };
 
-constexpr size_t kUnevenSmemBytes = size_t(pad16(4096)) * sizeof(float2);
+// Row and output buffers of the longest four-step line (N1 = 16), for the
+// storage type TS.
+template <class TS>
+constexpr size_t uneven_smem_bytes() { return fourstep_smem_bytes<TS, 16>(); }
 constexpr int kUnevenTaskPoints = 65536;
 
 // Storage kind: 0 FP32, 1 FP16 (block-floating-point), 2 E4M3, 3 E5M2.
