@@ -891,6 +891,11 @@ __global__ void __launch_bounds__(256, BFP_MIN_BLOCKS) fft_fourstep_kernel(const
     mbar_init(&bar, 1);
     mbar_init(&bar_out, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // Dense lines: prefetch this CTA's share of the line one resident wave
+    // of clusters later into L2.
+    if (a.pf_ahead > 0 && line + a.pf_ahead < a.lines)
+      prefetch_l2_bulk(static_cast<const TS*>(a.in) + (line + a.pf_ahead) * N + c * 4096,
+                       uint32_t(4096 * sizeof(TS)));
   }
   cluster.sync();                  // every CTA running, every barrier initialised
   uint32_t phase = 0;
@@ -905,20 +910,8 @@ cudaError_t launch_fourstep_n(const RowArgs& a, cudaStream_t stream) {
   constexpr size_t kBytes = fourstep_smem_bytes<TS, N / 4096>();
   auto kern = fft_fourstep_kernel<N, TS, MODE, SCALED>;
   static bool configured = false;
-  if (!configured) {
-    if (N1 > 8) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      if (e != cudaSuccess) return e;
-    }
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBytes));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  if (a.lines <= 0) return cudaSuccess;
-  const long long grid = a.lines * N1;
-  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  static int resident_clusters = 0;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(grid));
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = kBytes;
   cfg.stream = stream;
@@ -929,7 +922,25 @@ cudaError_t launch_fourstep_n(const RowArgs& a, cudaStream_t stream) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
+  if (!configured) {
+    if (N1 > 8) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBytes));
+    if (e != cudaSuccess) return e;
+    cfg.gridDim = dim3(N1);
+    e = cudaOccupancyMaxActiveClusters(&resident_clusters, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (a.lines <= 0) return cudaSuccess;
+  const long long grid = a.lines * N1;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  cfg.gridDim = dim3(unsigned(grid));
+  RowArgs b = a;
+  b.pf_ahead = (a.variant == kRowsPlainL2 || a.variant == kRowsPlain4L2) ? resident_clusters : 0;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, b);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -326,6 +326,8 @@ static int exec_many(bfpfft_plan plan, const void* in, void* out, cudaStream_t s
   a.tw4 = plan->d_tw4;
   a.counter = plan->d_counter;
   a.status = plan->status;
+  const int variant = rows_variant();   // the _l2 row variants also prefetch the next task into L2
+  a.prefetch = variant == bfp::kRowsPlainL2 || variant == bfp::kRowsPlain4L2;
   const int want = plan->tuned_clusters > 0 ? plan->tuned_clusters : plan->clusters;
   const int clusters = std::min(want, std::max(1, plan->num_tasks));
   return cuda_status(bfp::launch_uneven(plan->kind, plan->direction == BFPFFT_INVERSE, a, clusters, s));

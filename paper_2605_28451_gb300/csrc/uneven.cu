@@ -75,6 +75,30 @@ __device__ __noinline__ void run_task(const UnevenArgs& a, const UnevenTask& tk,
   }
 }
 
+// Prefetch into L2 the lines this CTA transforms in `task` (the cluster's next
+// task, about one resident wave ahead): for N <= 4096 the first thread of each
+// line group prefetches its line, for longer lines thread 0 its 4096-point
+// share.  Line offsets and lengths are multiples of 16 points, so every
+// prefetch is 16-byte aligned and sized.
+template <class TS>
+__device__ __forceinline__ void prefetch_task(const UnevenArgs& a, int task, int rank) {
+  if (task >= a.num_tasks) return;
+  const UnevenTask tk = a.tasks[task];
+  const int n = 1 << tk.log2n;
+  const TS* in = static_cast<const TS*>(a.in);
+  if (n <= kSlab) {
+    const int T = n / kPointsPerThread, G = kCta / T;
+    const int g = threadIdx.x / T, t = threadIdx.x - g * T;
+    const int idx = rank * G + g;
+    if (t == 0 && idx < tk.count) prefetch_l2_bulk(in + a.line_off[tk.first + idx], uint32_t(n * sizeof(TS)));
+  } else {
+    const int C = n / kSlab;
+    const int idx = rank / C, c = rank - idx * C;
+    if (threadIdx.x == 0 && idx < tk.count)
+      prefetch_l2_bulk(in + a.line_off[tk.first + idx] + c * kSlab, uint32_t(kSlab * sizeof(TS)));
+  }
+}
+
 template <class TS, int MODE, bool SCALED>
 __global__ void __launch_bounds__(kCta, 3) uneven_kernel(const UnevenArgs a) {
   extern __shared__ float2 smem_u[];
@@ -92,7 +116,9 @@ __global__ void __launch_bounds__(kCta, 3) uneven_kernel(const UnevenArgs a) {
   uint32_t phase = 0;
   // Tasks hold 65,536 points each, so a static round-robin over the clusters
   // balances the work; no counter or broadcast is needed.
+  if (a.prefetch) prefetch_task<TS>(a, cluster_id, rank);
   for (int task = cluster_id; task < a.num_tasks; task += clusters) {
+    if (a.prefetch) prefetch_task<TS>(a, task + clusters, rank);
     const UnevenTask tk = a.tasks[task];
     switch (tk.log2n) {
       case 4: run_task<TS, MODE, SCALED, 4>(a, tk, rank, smem_u, bar, phase); break;

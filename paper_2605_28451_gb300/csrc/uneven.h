@@ -24,6 +24,7 @@ struct UnevenArgs {
   const float2* const* tw4;      // per-length four-step tables (N >= 8192), indexed by log2 N
   int* counter;                  // task counter (reset before every launch)
   int* status;
+  int prefetch;                  // nonzero: prefetch each CTA's lines of the next task into L2
 };
 
 // Row and output buffers of the longest four-step line (N1 = 16), for the
