@@ -63,11 +63,19 @@ __device__ __forceinline__ void af_compress(float2 (&v)[kPointsPerThread], const
   int t1;
   asm volatile("mov.b32 %0, %1;" : "=r"(t1) : "r"(t));
   line_dft<N>(v, tw, sm, t1);
+  // Filter loads in groups of four, so the compiler does not hoist all
+  // sixteen next to the line (register pressure at 3 CTAs / SM).
 #pragma unroll
-  for (int m = 0; m < P; ++m) {
-    float2 hv = __ldg(h + t + T * m);
-    if (CONJ_H) hv = cconj(hv);
-    v[m] = cscale(cconj(cmul(v[m], hv)), inv_n);
+  for (int m0 = 0; m0 < P; m0 += 4) {
+    float2 hv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) hv[i] = __ldg(h + t + T * (m0 + i));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = CONJ_H ? cconj(hv[i]) : hv[i];
+      v[m0 + i] = cscale(cconj(cmul(v[m0 + i], f)), inv_n);
+    }
+    asm volatile("" ::: "memory");
   }
   int t2;
   asm volatile("mov.b32 %0, %1;" : "=r"(t2) : "r"(t));
@@ -89,11 +97,27 @@ __device__ __forceinline__ void af_load(float2 (&v)[kPointsPerThread], const AfA
                                         bool active) {
   constexpr int P = kPointsPerThread, T = N / P;
   const TIn* in = static_cast<const TIn*>(a.rc) + row * N + t;
+  // The line first, then its phases four at a time.
 #pragma unroll
-  for (int m = 0; m < P; ++m) {
-    const float2 x = active ? load_cached(in + T * m) : make_float2(0.f, 0.f);
-    v[m] = cmul(x, __ldg(a.ph + t + T * m));
+  for (int m = 0; m < P; ++m) v[m] = active ? load_cached(in + T * m) : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int m0 = 0; m0 < P; m0 += 4) {
+    float2 p[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) p[i] = __ldg(a.ph + t + T * (m0 + i));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[m0 + i] = cmul(v[m0 + i], p[i]);
+    asm volatile("" ::: "memory");
   }
+}
+
+// Shared memory of af_kernel: the row buffers, and for the gradient pass one
+// FP32 partial gradient per pulse for each line group of the CTA (a thread
+// owns the pulses t + T m of its group's slice, so no atomics are needed).
+template <int N, bool BACKWARD>
+constexpr size_t af_smem_bytes() {
+  using S = RowShape<N>;
+  return S::kSmemBytes + (BACKWARD ? size_t(S::G) * N * sizeof(float) : 0);
 }
 
 template <int N, class TIn, bool BACKWARD>
@@ -105,21 +129,27 @@ af_kernel(const AfArgs a) {
   const int g = threadIdx.x / T;
   const int t = threadIdx.x - g * T;
   float2* sm = smem_af + g * S::kSmemPerLine;
+  float* gsm = reinterpret_cast<float*>(smem_af + G * S::kSmemPerLine) + g * N;   // this group's gradients
   const long long groups = (a.rows + G - 1) / G;
 
   float s_acc = 0.f, q_acc = 0.f;
-  float gacc[P];
-#pragma unroll
-  for (int m = 0; m < P; ++m) gacc[m] = 0.f;
-  double sum_s = 0.0, ln_s = 0.0, ent = 0.0;
   if (BACKWARD) {
-    sum_s = a.stats[0];
-    ent = a.stats[2];
-    ln_s = a.stats[3];
+#pragma unroll
+    for (int m = 0; m < P; ++m) gsm[t + T * m] = 0.f;
   }
-  const float inv_s = BACKWARD ? float(1.0 / sum_s) : 0.f;
+  float ln_s_minus_e = 0.f, inv_s = 0.f;
+  if (BACKWARD) {
+    ln_s_minus_e = float(a.stats[3] - a.stats[2]);   // ln S - E
+    inv_s = float(1.0 / a.stats[0]);
+  }
 
   for (long long grp = blockIdx.x; grp < groups; grp += gridDim.x) {
+    if (threadIdx.x == 0 && grp + gridDim.x < groups) {
+      // The rows of this CTA's next group, into L2.
+      const long long r0 = (grp + gridDim.x) * G;
+      const long long cnt = a.rows - r0 < G ? a.rows - r0 : G;
+      prefetch_l2_bulk(static_cast<const TIn*>(a.rc) + r0 * N, uint32_t(cnt * N * sizeof(TIn)));
+    }
     const long long row = grp * G + g;
     const bool active = row < a.rows;
     int ti;
@@ -141,7 +171,7 @@ af_kernel(const AfArgs a) {
 #pragma unroll
       for (int m = 0; m < P; ++m) {
         const float q = v[m].x * v[m].x + v[m].y * v[m].y;
-        const float w = q > 0.f ? -(logf(q) - float(ln_s) + float(ent)) * inv_s : 0.f;
+        const float w = q > 0.f ? (ln_s_minus_e - logf(q)) * inv_s : 0.f;
         v[m] = cscale(v[m], w);
       }
       af_compress<N, true>(v, a.ha, a.tw, sm, ti);         // v = (A^H G)[row]
@@ -156,7 +186,7 @@ af_kernel(const AfArgs a) {
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const float2 b = v[m0 + i];
-            gacc[m0 + i] += 2.f * (b.x * x[i].y - b.y * x[i].x);      // 2 Im(conj(b) x)
+            gsm[ti + T * (m0 + i)] += 2.f * (b.x * x[i].y - b.y * x[i].x);      // 2 Im(conj(b) x)
           }
           asm volatile("" ::: "memory");
         }
@@ -187,23 +217,16 @@ af_kernel(const AfArgs a) {
       a.sq_part[2 * blockIdx.x + 1] = qq;
     }
   } else {
-    // Groups of one CTA cover the same pulses: add them in shared memory.
+    // Groups of one CTA cover the same pulses: add their slices.
     __syncthreads();
-    float* gs = reinterpret_cast<float*>(smem_af);
-    if (g == 0) {
-#pragma unroll
-      for (int m = 0; m < P; ++m) gs[t + T * m] = gacc[m];
-    }
-    for (int gg = 1; gg < G; ++gg) {
-      __syncthreads();
-      if (g == gg) {
-#pragma unroll
-        for (int m = 0; m < P; ++m) gs[t + T * m] += gacc[m];
-      }
-    }
-    __syncthreads();
+    const float* g0 = reinterpret_cast<const float*>(smem_af + G * S::kSmemPerLine);
     float* dst = a.g_part + (long long)blockIdx.x * N;
-    for (int i = threadIdx.x; i < N; i += S::kThreads) dst[i] = gs[i];
+    for (int i = threadIdx.x; i < N; i += S::kThreads) {
+      float acc = 0.f;
+#pragma unroll
+      for (int gg = 0; gg < G; ++gg) acc += g0[gg * N + i];
+      dst[i] = acc;
+    }
   }
 }
 
@@ -234,15 +257,15 @@ template <int N, class TIn, bool BACKWARD>
 cudaError_t launch_af_n(const AfArgs& a, int* grid_out, cudaStream_t s) {
   using S = RowShape<N>;
   auto kern = af_kernel<N, TIn, BACKWARD>;
+  constexpr size_t kBytes = af_smem_bytes<N, BACKWARD>();
   static int cap = 0;
   if (cap == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::kSmemBytes));
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBytes));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::kThreads, S::kSmemBytes)) !=
-        cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::kThreads, kBytes)) != cudaSuccess)
       return e;
     cap = (per_sm > 0 ? per_sm : 1) * sms;
     if (cap > kAfMaxCtas) cap = kAfMaxCtas;
@@ -250,7 +273,7 @@ cudaError_t launch_af_n(const AfArgs& a, int* grid_out, cudaStream_t s) {
   const long long groups = (a.rows + S::G - 1) / S::G;
   const int grid = int(groups < cap ? groups : cap);
   *grid_out = grid;
-  kern<<<grid, S::kThreads, S::kSmemBytes, s>>>(a);
+  kern<<<grid, S::kThreads, kBytes, s>>>(a);
   return cudaGetLastError();
 }
 
