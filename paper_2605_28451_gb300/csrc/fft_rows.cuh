@@ -84,7 +84,7 @@ struct RowArgs {
 enum RowVariant : int {
   kRowsTma = 0, kRowsPlain = 1, kRowsPlainPP = 2, kRowsPlainH = 3, kRowsPlainHPP = 4,
   kRowsTmaPP = 5, kRowsTmaH = 6, kRowsTmaHPP = 7, kRowsTc = 8, kRowsPlain4 = 9,
-  kRowsPlainL2 = 10, kRowsPlain4L2 = 11
+  kRowsPlainL2 = 10, kRowsPlain4L2 = 11, kRowsPlainHL2 = 12, kRowsPlainH4L2 = 13
 };
 
 constexpr int kPointsPerThread = 16;
@@ -939,7 +939,10 @@ cudaError_t launch_fourstep_n(const RowArgs& a, cudaStream_t stream) {
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   cfg.gridDim = dim3(unsigned(grid));
   RowArgs b = a;
-  b.pf_ahead = (a.variant == kRowsPlainL2 || a.variant == kRowsPlain4L2) ? resident_clusters : 0;
+  b.pf_ahead = (a.variant == kRowsPlainL2 || a.variant == kRowsPlain4L2 || a.variant == kRowsPlainHL2 ||
+                a.variant == kRowsPlainH4L2)
+                   ? resident_clusters
+                   : 0;
   cudaError_t e = cudaLaunchKernelEx(&cfg, kern, b);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -1079,6 +1082,12 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
         case kRowsPlainH:
           if constexpr (kHalf) return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF16>(a, stream);
           break;
+        case kRowsPlainHL2:
+          if constexpr (kHalf) return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF16>(a, stream, true);
+          break;
+        case kRowsPlainH4L2:
+          if constexpr (kHalf) return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF16, 4>(a, stream, true);
+          break;
         case kRowsPlainHPP:
           if constexpr (kHalf) return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF16PP>(a, stream);
           break;
@@ -1128,7 +1137,8 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
   const long long grid = clusters * S::C;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   RowArgs b = a;
-  const bool l2 = a.variant == kRowsPlainL2 || a.variant == kRowsPlain4L2;
+  const bool l2 = a.variant == kRowsPlainL2 || a.variant == kRowsPlain4L2 || a.variant == kRowsPlainHL2 ||
+                  a.variant == kRowsPlainH4L2;
   b.pf_ahead = (l2 && !TLOAD && a.in_stride == N) ? resident : 0;
   if constexpr (S::C > 1) {
     cudaLaunchConfig_t cfg = {};

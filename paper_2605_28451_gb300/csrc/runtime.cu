@@ -162,7 +162,8 @@ int rows_variant() {
       {"tma", bfp::kRowsTma},         {"plain", bfp::kRowsPlain},    {"pp", bfp::kRowsPlainPP},
       {"h16", bfp::kRowsPlainH},      {"h16pp", bfp::kRowsPlainHPP}, {"tma_pp", bfp::kRowsTmaPP},
       {"tma_h16", bfp::kRowsTmaH},    {"tma_h16pp", bfp::kRowsTmaHPP}, {"tc", bfp::kRowsTc},
-      {"plain4", bfp::kRowsPlain4},   {"plain_l2", bfp::kRowsPlainL2}, {"plain4_l2", bfp::kRowsPlain4L2}};
+      {"plain4", bfp::kRowsPlain4},   {"plain_l2", bfp::kRowsPlainL2}, {"plain4_l2", bfp::kRowsPlain4L2},
+      {"h16_l2", bfp::kRowsPlainHL2}, {"h16_4_l2", bfp::kRowsPlainH4L2}};
   for (const auto& k : kNames)
     if (std::strcmp(v, k.name) == 0) return k.code;
   return bfp::kRowsTma;
@@ -327,7 +328,8 @@ static int exec_many(bfpfft_plan plan, const void* in, void* out, cudaStream_t s
   a.counter = plan->d_counter;
   a.status = plan->status;
   const int variant = rows_variant();   // the _l2 row variants also prefetch the next task into L2
-  a.prefetch = variant == bfp::kRowsPlainL2 || variant == bfp::kRowsPlain4L2;
+  a.prefetch = variant == bfp::kRowsPlainL2 || variant == bfp::kRowsPlain4L2 || variant == bfp::kRowsPlainHL2 ||
+               variant == bfp::kRowsPlainH4L2;
   const int want = plan->tuned_clusters > 0 ? plan->tuned_clusters : plan->clusters;
   const int clusters = std::min(want, std::max(1, plan->num_tasks));
   return cuda_status(bfp::launch_uneven(plan->kind, plan->direction == BFPFFT_INVERSE, a, clusters, s));
