@@ -897,7 +897,11 @@ __global__ void __launch_bounds__(256, BFP_MIN_BLOCKS) fft_fourstep_kernel(const
       prefetch_l2_bulk(static_cast<const TS*>(a.in) + (line + a.pf_ahead) * N + c * 4096,
                        uint32_t(4096 * sizeof(TS)));
   }
-  cluster.sync();                  // every CTA running, every barrier initialised
+  // Every CTA running, every mbarrier initialised: the initialisation is
+  // published by its own release fence, so the arrive can be relaxed (no
+  // memory barrier for the other threads).
+  cluster_arrive_relaxed();
+  cluster_wait_acquire();
   uint32_t phase = 0;
   fourstep_line<N1, TS, MODE, SCALED>(a, in, out, smem_fs, &bar, &bar_out, phase, c, 0, true);
   // No CTA leaves while a peer's asynchronous stores may still be in flight.

@@ -112,7 +112,9 @@ __global__ void __launch_bounds__(kCta, 3) uneven_kernel(const UnevenArgs a) {
     mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  cluster.sync();                                        // peers running, barriers initialised
+  // Peers running, mbarriers initialised (published by their release fence).
+  cluster_arrive_relaxed();
+  cluster_wait_acquire();
   uint32_t phase = 0;
   // Tasks hold 65,536 points each, so a static round-robin over the clusters
   // balances the work; no counter or broadcast is needed.
