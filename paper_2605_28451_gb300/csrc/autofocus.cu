@@ -40,6 +40,7 @@ struct AfArgs {
   double* stats;         // S, Q, E, ln S
   double* sq_part;       // [grid][2]
   float* g_part;         // [grid][n_az]
+  bool prefetch;         // rc in device memory: prefetch each CTA's next rows into L2
 };
 
 __global__ void af_phase_kernel(const float* __restrict__ phi, float2* __restrict__ ph, int n) {
@@ -144,7 +145,7 @@ af_kernel(const AfArgs a) {
   }
 
   for (long long grp = blockIdx.x; grp < groups; grp += gridDim.x) {
-    if (threadIdx.x == 0 && grp + gridDim.x < groups) {
+    if (a.prefetch && threadIdx.x == 0 && grp + gridDim.x < groups) {
       // The rows of this CTA's next group, into L2.
       const long long r0 = (grp + gridDim.x) * G;
       const long long cnt = a.rows - r0 < G ? a.rows - r0 : G;
@@ -299,7 +300,7 @@ size_t af_workspace_bytes(long long n_az) {
 
 cudaError_t launch_autofocus(int log2n, bool rc16, const void* rc, const float* phi, const float2* ha,
                              const float2* tw, long long n_rg, double* stats, float* grad, void* workspace,
-                             cudaStream_t s) {
+                             bool prefetch, cudaStream_t s) {
   const long long n_az = 1LL << log2n;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   AfArgs a;
@@ -313,6 +314,7 @@ cudaError_t launch_autofocus(int log2n, bool rc16, const void* rc, const float* 
   a.tw = tw;
   a.rows = n_rg;
   a.stats = stats;
+  a.prefetch = prefetch;
   af_phase_kernel<<<int((n_az + 255) / 256), 256, 0, s>>>(phi, ph, int(n_az));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -16,6 +16,6 @@ size_t af_workspace_bytes(long long n_az);
 // grad != nullptr, dE/dphi (grad[n_az], device).  rc is [n_rg][2^log2n].
 cudaError_t launch_autofocus(int log2n, bool rc16, const void* rc, const float* phi, const float2* ha,
                              const float2* tw, long long n_rg, double* stats, float* grad, void* workspace,
-                             cudaStream_t s);
+                             bool prefetch, cudaStream_t s);
 
 }  // namespace bfp

@@ -42,6 +42,27 @@ int log2_exact(int64_t n) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// True for device memory.  Inputs elsewhere (pinned host buffers that the
+// kernels read in place over the CPU-GPU link) get no bulk L2 prefetch.
+bool device_memory(const void* p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice;
+}
+
+int without_l2(int variant) {
+  switch (variant) {
+    case bfp::kRowsPlainL2: return bfp::kRowsPlain;
+    case bfp::kRowsPlain4L2: return bfp::kRowsPlain4;
+    case bfp::kRowsPlainHL2:
+    case bfp::kRowsPlainH4L2: return bfp::kRowsPlainH;
+    default: return variant;
+  }
+}
+
 // Host-side fault injection for the error paths: BFPFFT_FAULT=plan|alloc|launch
 // makes the named step fail without touching the GPU.
 bool fault(const char* step) {
@@ -328,8 +349,9 @@ static int exec_many(bfpfft_plan plan, const void* in, void* out, cudaStream_t s
   a.counter = plan->d_counter;
   a.status = plan->status;
   const int variant = rows_variant();   // the _l2 row variants also prefetch the next task into L2
-  a.prefetch = variant == bfp::kRowsPlainL2 || variant == bfp::kRowsPlain4L2 || variant == bfp::kRowsPlainHL2 ||
-               variant == bfp::kRowsPlainH4L2;
+  a.prefetch = (variant == bfp::kRowsPlainL2 || variant == bfp::kRowsPlain4L2 || variant == bfp::kRowsPlainHL2 ||
+                variant == bfp::kRowsPlainH4L2) &&
+               device_memory(in);
   const int want = plan->tuned_clusters > 0 ? plan->tuned_clusters : plan->clusters;
   const int clusters = std::min(want, std::max(1, plan->num_tasks));
   return cuda_status(bfp::launch_uneven(plan->kind, plan->direction == BFPFFT_INVERSE, a, clusters, s));
@@ -702,6 +724,7 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
   a.h = nullptr;
   a.status = plan->status;
   a.variant = std::getenv("BFPFFT_ROWS") == nullptr && plan->variant >= 0 ? plan->variant : rows_variant();
+  if (!device_memory(in)) a.variant = without_l2(a.variant);
   if (a.variant == bfp::kRowsTc && plan->log2n == 12 && plan->dtype == BFPFFT_F16_BFP) {
     const int stc = get_tc_matrix(const_cast<void**>(&a.tc_b));
     if (stc != BFPFFT_OK) return stc;
@@ -868,6 +891,7 @@ int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype,
   a.in = raw;
   a.out = out;
   a.h = static_cast<const float2*>(hr);
+  if (!device_memory(raw)) a.variant = without_l2(a.variant);
   a.lines = n_az;
   a.in_stride = n_rg;
   a.out_stride = transpose_out ? n_az : n_rg;
@@ -911,6 +935,7 @@ int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img,
   a.in = rc;
   a.out = img;
   a.h = static_cast<const float2*>(ha);
+  if (!device_memory(rc)) a.variant = without_l2(a.variant);
   a.lines = n_rg;                                   // one line per range column
   a.in_stride = rc_layout == 0 ? n_rg : n_az;       // [n_az][n_rg] column vs [n_rg][n_az] row
   a.out_stride = n_rg;                              // image is [n_az][n_rg]
@@ -970,7 +995,7 @@ static int autofocus_common(const void* rc, int rc_dtype, const float* phi, cons
   if (fault("launch")) return BFPFFT_ERR_CUDA;
   cudaError_t e = bfp::launch_autofocus(l, rc_dtype == BFPFFT_F16_BFP, rc, phi, static_cast<const float2*>(ha),
                                         a.tw, n_rg, static_cast<double*>(stats_out), grad_out, workspace,
-                                        static_cast<cudaStream_t>(stream));
+                                        device_memory(rc), static_cast<cudaStream_t>(stream));
   return cuda_status(e);
 }
 

@@ -224,3 +224,30 @@ def test_prefetching_variants_over_many_waves(variant, n, batch, monkeypatch):
         got = from_device(out[torch.as_tensor(rows, device=out.device)], B.F16_BFP)
         ok, worst = fp16_elementwise_ok(got, ref_fn(x[rows]))
         assert ok, (variant, n, direction, worst)
+
+
+@pytest.mark.parametrize("n,batch", [(4096, 300), (65536, 12)])
+def test_exec_reads_and_writes_pinned_host_buffers(n, batch):
+    """Pinned host buffers passed straight to bfpfft_exec: the kernels read
+    and write them in place over the CPU-GPU link (no staging copies, no L2
+    prefetch of host memory); results are bit-identical to device buffers."""
+    import torch
+    x = storage_round(synth.complex_gaussian(batch, n, seed=n + 1), B.F16_BFP)
+    dev_in = to_device(x, B.F16_BFP)
+    host_in = torch.empty(dev_in.shape, dtype=dev_in.dtype, pin_memory=True)
+    host_in.copy_(dev_in)
+    host_out = torch.empty_like(host_in, pin_memory=True)
+    mid = torch.empty_like(dev_in)
+    ref_mid, ref_out = torch.empty_like(dev_in), torch.empty_like(dev_in)
+    fwd = B.bfpfft_plan_create(n, batch, B.F16_BFP, B.FORWARD)
+    inv = B.bfpfft_plan_create(n, batch, B.F16_BFP, B.INVERSE)
+    B.bfpfft_exec(fwd, host_in, mid)
+    B.bfpfft_exec(inv, mid, host_out)
+    B.bfpfft_exec(fwd, dev_in, ref_mid)
+    B.bfpfft_exec(inv, ref_mid, ref_out)
+    torch.cuda.synchronize()
+    assert B.bfpfft_device_status() == B.OK
+    assert torch.equal(mid, ref_mid)
+    assert torch.equal(host_out.to(dev_in.device), ref_out)
+    ok, worst = fp16_elementwise_ok(from_device(mid[:4], B.F16_BFP), F.fft(x[:4]))
+    assert ok, worst
