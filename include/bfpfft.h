@@ -87,8 +87,11 @@ const char* bfpfft_error_string(int status);
 int bfpfft_plan_create(bfpfft_plan* out, int64_t n, int64_t batch, int dtype, int direction);
 
 /*
- * Enqueue the planned transforms on `stream`: in and out are device buffers of
- * batch * n points in the plan's dtype.  in == out is allowed.
+ * Enqueue the planned transforms on `stream`: in and out are buffers of
+ * batch * n points in the plan's dtype, 16-byte aligned.  in == out is allowed.
+ * Either may also be pinned host memory (cudaHostAlloc / cudaMallocHost),
+ * which the kernels then read or write in place over the CPU-GPU link; the
+ * caller keeps it alive and unmodified until the stream has passed the call.
  * Errors: INVALID_ARG (NULL plan or buffer), MISALIGNED, CUDA.
  */
 int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream);
