@@ -71,6 +71,7 @@ struct RowArgs {
   const float2* tw_4step;  // N >= 8192: four-step twiddles T[k1][n2] = W_N^{n2 k1}
   const void* tc_b;        // tensor-core variant: 16-point DFT matrix, real form, FP16 [32][32]
   int pf_ahead;            // > 0: each CTA prefetches into L2 the lines of the CTA pf_ahead blocks later
+  int no_prefetch;         // nonzero: the input is not device memory; no bulk L2 prefetch of it
 };
 
 // Row-kernel variants for dense rows of length <= 4096 (chosen by

@@ -724,7 +724,10 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
   a.h = nullptr;
   a.status = plan->status;
   a.variant = std::getenv("BFPFFT_ROWS") == nullptr && plan->variant >= 0 ? plan->variant : rows_variant();
-  if (!device_memory(in)) a.variant = without_l2(a.variant);
+  if (!device_memory(in)) {
+    a.variant = without_l2(a.variant);
+    a.no_prefetch = 1;
+  }
   if (a.variant == bfp::kRowsTc && plan->log2n == 12 && plan->dtype == BFPFFT_F16_BFP) {
     const int stc = get_tc_matrix(const_cast<void**>(&a.tc_b));
     if (stc != BFPFFT_OK) return stc;

@@ -220,6 +220,8 @@ __global__ void __launch_bounds__(256, 3) fft_tc_kernel(const RowArgs a) {
   bool ok = true;
 
   for (long long line = blockIdx.x; ok && line < a.lines; line += gridDim.x) {
+    if (a.pf_ahead > 0 && tid == 0 && line + gridDim.x < a.lines)   // next iteration's line, into L2
+      prefetch_l2_bulk(static_cast<const TS*>(a.in) + (line + gridDim.x) * a.in_stride, uint32_t(kN * sizeof(TS)));
     // Pass-0 inputs: butterfly j = tid takes x[j + 256 r]; coalesced loads.
     const TS* in = static_cast<const TS*>(a.in) + line * a.in_stride + tid;
     const int row = tc::row_of<0>(tid);
@@ -262,7 +264,9 @@ cudaError_t launch_tc_n(const RowArgs& a, cudaStream_t stream) {
   (void)kern;
   if (a.lines <= 0) return cudaSuccess;
   const int grid = int(a.lines < grid_cap ? a.lines : grid_cap);
-  kern<<<grid, 256, tc::kSmemBytes, stream>>>(a);
+  RowArgs b = a;
+  b.pf_ahead = a.no_prefetch ? 0 : 1;       // dense rows in device memory: prefetch the next line
+  kern<<<grid, 256, tc::kSmemBytes, stream>>>(b);
   return cudaGetLastError();
 }
 
