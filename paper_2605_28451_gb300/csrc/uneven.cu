@@ -139,8 +139,18 @@ __global__ void __launch_bounds__(kCta, 3) uneven_kernel(const UnevenArgs a) {
       default: break;
     }
     // A peer may write into this CTA's shared memory in the next task only
-    // after this CTA is done with it.
-    cluster_barrier_relaxed();
+    // after this CTA is done with it.  Between two four-step tasks of the
+    // same length with the output exchange (N1 >= 8) the data dependencies
+    // already guarantee that: the CTAs that send to this one in the next task
+    // are the same group, and each of them finished this task only after
+    // receiving this CTA's step-3 values (sent once its row buffer was read),
+    // and sends its own step-3 values of the next task only after receiving
+    // this CTA's step-1 values of it (sent once its output buffer was read).
+    // Every CTA of the cluster sees the same task sequence, so all skip or all
+    // keep the barrier.
+    const int next = task + clusters;
+    const bool chained = tk.log2n >= 15 && next < a.num_tasks && a.tasks[next].log2n == tk.log2n;
+    if (!chained) cluster_barrier_relaxed();
   }
 }
 
