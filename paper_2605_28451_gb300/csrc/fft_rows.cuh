@@ -879,7 +879,9 @@ __device__ __forceinline__ void fourstep_line(const RowArgs& a, const TS* in, TS
 // Uniform plans with N >= 8192: one line per group of N / 4096 CTAs, a
 // cluster per line.
 template <int N, class TS, int MODE, bool SCALED>
-__global__ void __launch_bounds__(256, BFP_MIN_BLOCKS) fft_fourstep_kernel(const RowArgs a) {
+// Four CTAs per SM (64 registers) where their shared memory fits, else three.
+__global__ void __launch_bounds__(256, fourstep_smem_bytes<TS, N / 4096>() * 4 <= 220 * 1024 ? 4 : 3)
+    fft_fourstep_kernel(const RowArgs a) {
   constexpr int N1 = N / 4096;
   extern __shared__ float2 smem_fs[];
   __shared__ __align__(8) uint64_t bar, bar_out;

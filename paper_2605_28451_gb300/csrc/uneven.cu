@@ -100,7 +100,10 @@ __device__ __forceinline__ void prefetch_task(const UnevenArgs& a, int task, int
 }
 
 template <class TS, int MODE, bool SCALED>
-__global__ void __launch_bounds__(kCta, 3) uneven_kernel(const UnevenArgs a) {
+// Four CTAs per SM (64 registers) where their shared memory fits (FP16
+// storage), else three.
+__global__ void __launch_bounds__(kCta, uneven_smem_bytes<TS>() * 4 <= 220 * 1024 ? 4 : 3)
+    uneven_kernel(const UnevenArgs a) {
   extern __shared__ float2 smem_u[];
   __shared__ __align__(8) uint64_t bar[2];   // row and output exchanges of four-step lines
   auto cluster = cooperative_groups::this_cluster();
