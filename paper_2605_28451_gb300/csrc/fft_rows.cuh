@@ -110,9 +110,10 @@ struct RowShape {
   static constexpr int kLinesPerCluster = C * G;
   // Resident CTAs per SM requested from the register allocator.
   static constexpr int kMinBlocks = kThreads >= 1024 ? 1 : (kThreads >= 512 ? 1 : BFP_MIN_BLOCKS);
-  // Dense-row (no corner turn) kernels: 4 CTAs per SM at 64 registers, which
-  // measured faster than 3 at 80 for every mode (spills stay within 16 bytes).
-  static constexpr int kMinBlocksDense = TURN ? kMinBlocks : (kThreads >= 512 ? 1 : 4);
+  // Dense-row (no corner turn) kernels: 64 registers, so 4 CTAs per SM of 256
+  // threads (faster than 3 at 80 in every mode; spills stay within 16 bytes)
+  // and 2 of 512 (N = 8192).
+  static constexpr int kMinBlocksDense = TURN ? kMinBlocks : (kThreads >= 1024 ? 1 : (kThreads >= 512 ? 2 : 4));
 };
 
 // Where a line lives between passes.  Every policy offers load / store of
@@ -1074,6 +1075,12 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
       if (a.tw_4step != nullptr && a.in_stride == N && a.out_stride == N)
         return launch_fourstep_n<N, TIn, MODE, SCALED>(a, stream);
     }
+  }
+  // Lines the four-step kernel does not take (compression, naive FP16, mixed
+  // storage, strided rows) run on one CTA of N / 16 threads up to N = 16384,
+  // which measured 1.4-1.5x faster than the per-pass cluster kernel; longer
+  // ones need the cluster.
+  if constexpr (!TLOAD && !TSTORE && N > 16384) {
     return launch_cluster_n<N, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
   } else {
   using S = RowShape<N, TLOAD || TSTORE>;
