@@ -1070,16 +1070,19 @@ cudaError_t launch_rows_plain_x(const RowArgs& a, cudaStream_t stream, bool l2_p
 template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, bool TLOAD = false,
           bool TSTORE = false>
 cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
-  if constexpr (!TLOAD && !TSTORE && N >= 8192) {
+  // Dense lines of 32768 and 65536 points: the four-step kernel over a
+  // cluster.  Lines of 8192 and 16384 points run on one CTA of N / 16 threads
+  // (512 at 2 CTAs per SM, or 1024), which measured 1.4x faster than the
+  // four-step kernel for plain transforms and 3x faster than the per-pass
+  // cluster kernel for compression; longer lines the four-step kernel does not
+  // take (compression, naive FP16, mixed storage, strided rows) need the
+  // cluster kernel.
+  if constexpr (!TLOAD && !TSTORE && N >= 32768) {
     if constexpr (MODE != kCompress && !NAIVE && std::is_same<TIn, TOut>::value) {
       if (a.tw_4step != nullptr && a.in_stride == N && a.out_stride == N)
         return launch_fourstep_n<N, TIn, MODE, SCALED>(a, stream);
     }
   }
-  // Lines the four-step kernel does not take (compression, naive FP16, mixed
-  // storage, strided rows) run on one CTA of N / 16 threads up to N = 16384,
-  // which measured 1.4-1.5x faster than the per-pass cluster kernel; longer
-  // ones need the cluster.
   if constexpr (!TLOAD && !TSTORE && N > 16384) {
     return launch_cluster_n<N, TIn, TOut, MODE, NAIVE, SCALED>(a, stream);
   } else {
