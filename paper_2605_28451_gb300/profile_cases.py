@@ -7,6 +7,9 @@ Cases (FP16-BFP unless named otherwise, N = 4096 lines):
   fft32_fwd              the same in FP32 storage
   range16                range compression of a 1024 x 4096 complex64 scene to FP16, corner-turned
   image16                range + azimuth compression of a 4096 x 4096 scene to an FP16 image
+  autofocus16            one autofocus gradient step on 4096 x 4096 FP16 range-compressed data
+  uneven16               a persistent uneven batch of B transforms (default 2000; lengths 256 .. 65536,
+                         Zipf weights, seed 3), FP16, forward
 Inputs are seeded and synthetic.  Nothing is checked here; the tests do that.
 """
 
@@ -67,6 +70,40 @@ def main():
             e1.record(stream)
             times.append((e0, e1))
         bytes_per_rep = n_az * n * (12 if args.case == "range16" else 20)
+    elif args.case == "autofocus16":
+        from . import autofocus as GA
+        rc = torch.randn((n, n, 2), device=dev, generator=g).to(torch.float16)
+        ha = torch.empty(n, dtype=torch.complex64, device=dev)
+        B.sar_make_filter(torch.from_numpy(synth.centred_reference(synth.azimuth_chirp(1024), n)
+                                           .astype("complex64")).to(dev), n, True, ha, stream)
+        phi = torch.from_numpy(synth.phase_error(n).astype("float32")).to(dev)
+        ws = GA.Workspace(n, dev)
+        grad = torch.empty(n, dtype=torch.float32, device=dev)
+        stats = torch.empty(4, dtype=torch.float64, device=dev)
+        for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.sar_autofocus_grad(rc, B.F16_BFP, phi, ha, n, n, grad, stats, ws.buf, ws.bytes, stream)
+            e1.record(stream)
+            times.append((e0, e1))
+        bytes_per_rep = n * n * 12
+    elif args.case == "uneven16":
+        import numpy as np
+        count = args.batch if args.batch != 16384 else 2000
+        lengths = synth.uneven_lengths(count, seed=3)
+        offsets = np.zeros_like(lengths)
+        offsets[1:] = np.cumsum(lengths)[:-1]
+        total = int(lengths.sum())
+        x = torch.randn((total, 2), device=dev, generator=g).to(torch.float16)
+        y = torch.empty_like(x)
+        plan = B.bfpfft_plan_create_many(lengths, offsets, B.F16_BFP, B.FORWARD)
+        for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.bfpfft_exec(plan, x, y, stream)
+            e1.record(stream)
+            times.append((e0, e1))
+        bytes_per_rep = total * 8
     else:
         raise SystemExit(f"unknown case {args.case}")
     torch.cuda.synchronize()
