@@ -199,10 +199,15 @@ int sar_make_filter(const void* ref, int64_t n, int peak_normalise, void* h_out,
  *   raw        [n_az][n_rg], raw_dtype BFPFFT_F32 (complex64) or BFPFFT_F16_BFP (half2)
  *   out        out_dtype BFPFFT_F32, BFPFFT_F16_BFP or BFPFFT_F16_NAIVE;
  *              transpose_out = 0: [n_az][n_rg];  transpose_out = 1: [n_rg][n_az]
- *              (the corner turn is done on chip by a thread-block cluster)
  *   hr         float2[n_rg], the range filter spectrum
+ * The corner turn of transpose_out = 1 is by default a tiled transpose of the
+ * compressed rows through stream-ordered scratch (n_az * n_rg points of the
+ * output type) from a library-owned CUDA memory pool that keeps its memory
+ * between calls; with the environment variable BFPFFT_SAR_TURN=fused it is
+ * done on chip by a thread-block cluster instead (no scratch).
  * n_az = 0 is a no-op.  out must not overlap raw when transpose_out = 1.
- * Errors: INVALID_ARG, MISALIGNED, UNSUPPORTED (n_rg or dtypes), CUDA.
+ * Errors: INVALID_ARG, MISALIGNED, UNSUPPORTED (n_rg or dtypes), OOM (scratch),
+ * CUDA.
  */
 int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype, const void* hr,
                        int64_t n_az, int64_t n_rg, int transpose_out, void* stream);
@@ -211,13 +216,18 @@ int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype,
  * Azimuth compression: for each of the n_rg range columns,
  * img[:, r] = IDFT(DFT(rc[:, r]) . Ha), lines of length n_az.
  *   rc         rc_dtype BFPFFT_F32 or BFPFFT_F16_BFP;
- *              rc_layout = 0: [n_az][n_rg] (columns are gathered on chip);
+ *              rc_layout = 0: [n_az][n_rg];
  *              rc_layout = 1: [n_rg][n_az] (as written by sar_range_compress
  *              with transpose_out = 1)
  *   img        [n_az][n_rg], img_dtype BFPFFT_F32, BFPFFT_F16_BFP or BFPFFT_F16_NAIVE
  *   ha         float2[n_az], the azimuth filter spectrum
+ * By default the azimuth lines are compressed as dense rows into
+ * stream-ordered scratch and turned into img by a tiled transpose (layout 0
+ * is first turned into scratch as well); BFPFFT_SAR_TURN=fused gathers and
+ * scatters the columns on chip through thread-block clusters instead.
  * n_rg = 0 is a no-op.  img must not overlap rc.
- * Errors: INVALID_ARG, MISALIGNED, UNSUPPORTED (n_az or dtypes), CUDA.
+ * Errors: INVALID_ARG, MISALIGNED, UNSUPPORTED (n_az or dtypes), OOM (scratch),
+ * CUDA.
  */
 int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img, int img_dtype,
                          const void* ha, int64_t n_az, int64_t n_rg, void* stream);
