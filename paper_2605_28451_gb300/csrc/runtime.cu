@@ -487,6 +487,7 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
     candidates = {bfp::kRowsPlain4L2, bfp::kRowsPlainL2, bfp::kRowsPlain, bfp::kRowsPlain4,
                   bfp::kRowsTma,        bfp::kRowsPlainPP, bfp::kRowsTmaPP};
     if (allow_fp16_exchange && (plan->dtype == BFPFFT_F16_BFP || plan->dtype == BFPFFT_F16_NAIVE)) {
+      candidates.push_back(bfp::kRowsPlainHL2);
       candidates.push_back(bfp::kRowsPlainH);
       candidates.push_back(bfp::kRowsPlainHPP);
       candidates.push_back(bfp::kRowsTmaH);

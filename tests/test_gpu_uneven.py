@@ -159,3 +159,23 @@ def test_tuner_uniform_and_uneven(tmp_path, monkeypatch):
     torch.cuda.synchronize()
     ok, worst = fp16_elementwise_ok(from_device(y, B.F16_BFP)[:8], F.fft(x[:8]))
     assert ok, worst
+
+
+def test_tuner_with_fp16_exchanges_allowed(tmp_path, monkeypatch):
+    """With allow_fp16_exchange the tuner also times the FP16-exchange and
+    tensor-core variants; whichever wins, the plan's results stay within the
+    FP16 budget (SQNR against the FP64 oracle well above the 55 dB bar)."""
+    import torch
+    monkeypatch.setenv("BFPFFT_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    monkeypatch.delenv("BFPFFT_ROWS", raising=False)
+    plan = B.bfpfft_plan_create(4096, 512, B.F16_BFP, B.FORWARD)
+    chosen, ms = B.bfpfft_plan_tune(plan, allow_fp16_exchange=True)
+    assert chosen in (0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12) and ms > 0
+    x = storage_round(synth.complex_gaussian(512, 4096, seed=10), B.F16_BFP)
+    xin = to_device(x, B.F16_BFP)
+    y = torch.empty_like(xin)
+    B.bfpfft_exec(plan, xin, y)
+    torch.cuda.synchronize()
+    assert B.bfpfft_device_status() == B.OK
+    got = from_device(y, B.F16_BFP)[:16]
+    assert metrics.sqnr_db(F.fft(x[:16]), got) >= 60.0, chosen
