@@ -51,6 +51,24 @@ def _dist():
     return world, rank, local
 
 
+def _max_over_ranks(value: float, dist, device) -> float:
+    """The largest value over all ranks (for times: the slowest rank's), or
+    the value itself when no process group is running."""
+    import torch
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_value(world: int, flops_per_rank_step: float, t_ms: float) -> float:
+    """Whole-job GFLOPS: every rank runs its own replica of the workload (no
+    data-path collective), so the job does `world` times one rank's work in
+    the slowest rank's time."""
+    return world * flops_per_rank_step / (t_ms * 1e-3) / 1e9
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -201,13 +219,9 @@ def run_ours(args):
         torch.cuda.synchronize()
     fwd_ms = [e[0].elapsed_time(e[1]) for e in events]
     inv_ms = [e[1].elapsed_time(e[2]) for e in events]
-    t_ms = t_start.elapsed_time(t_end) / args.steps
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = _max_over_ranks(t_start.elapsed_time(t_end) / args.steps, dist, dev)
     flops_step = 2.0 * FLOPS_PER_TRANSFORM * batch
-    value = world * flops_step / (t_ms * 1e-3) / 1e9
+    value = _job_value(world, flops_step, t_ms)
 
     # ---- SQNR of the FP16 path against the FP32 path on the same input ----------
     x32 = torch.view_as_complex(x16[:256].float().contiguous())
