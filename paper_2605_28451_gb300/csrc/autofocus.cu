@@ -259,18 +259,11 @@ cudaError_t launch_af_n(const AfArgs& a, int* grid_out, cudaStream_t s) {
   using S = RowShape<N>;
   auto kern = af_kernel<N, TIn, BACKWARD>;
   constexpr size_t kBytes = af_smem_bytes<N, BACKWARD>();
-  static int cap = 0;
-  if (cap == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBytes));
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::kThreads, kBytes)) != cudaSuccess)
-      return e;
-    cap = (per_sm > 0 ? per_sm : 1) * sms;
-    if (cap > kAfMaxCtas) cap = kAfMaxCtas;
-  }
+  // One-time, thread-safe set-up (function-local static): resident CTAs,
+  // capped by the workspace's partial-gradient slots.
+  static const LaunchSetup setup = setup_kernel(kern, S::kThreads, kBytes);
+  if (setup.err != cudaSuccess) return setup.err;
+  const int cap = setup.resident < kAfMaxCtas ? setup.resident : kAfMaxCtas;
   const long long groups = (a.rows + S::G - 1) / S::G;
   const int grid = int(groups < cap ? groups : cap);
   *grid_out = grid;

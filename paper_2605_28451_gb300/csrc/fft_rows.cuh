@@ -713,23 +713,40 @@ fft_rows_tma_kernel(const RowArgs a) {
   }
 }
 
+// One-time host set-up of a kernel: the dynamic shared-memory attribute when
+// above 48 KB, and the number of its CTAs resident on the whole device.
+// Launchers keep the result in a function-local static, which C++ initialises
+// exactly once even when several host threads make the first call together
+// (one process per GPU: the device of that first call).
+struct LaunchSetup {
+  cudaError_t err;
+  int resident;
+};
+
+template <class K>
+LaunchSetup setup_kernel(K kern, int threads, size_t smem) {
+  LaunchSetup r{cudaSuccess, 0};
+  if (smem > 48 * 1024) {
+    r.err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (r.err != cudaSuccess) return r;
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((r.err = cudaGetDevice(&dev)) != cudaSuccess) return r;
+  if ((r.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return r;
+  if ((r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) != cudaSuccess) return r;
+  r.resident = (per_sm > 0 ? per_sm : 1) * sms;
+  return r;
+}
+
 template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED, int XV = kXchF32>
 cudaError_t launch_rows_tma_n(const RowArgs& a, cudaStream_t stream) {
   using S = RowShape<N>;
   constexpr int kStages = 2;
   using L = TmaLayout<N, TIn, kStages, XV>;
   auto kern = fft_rows_tma_kernel<N, TIn, TOut, MODE, NAIVE, SCALED, kStages, XV>;
-  static int grid_cap = 0;   // resident CTAs on this device (computed once)
-  if (grid_cap == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::kBytes));
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::kThreads, L::kBytes);
-    if (e != cudaSuccess) return e;
-    grid_cap = (per_sm > 0 ? per_sm : 1) * sms;
-  }
+  static const LaunchSetup setup = setup_kernel(kern, S::kThreads, L::kBytes);
+  if (setup.err != cudaSuccess) return setup.err;
+  const int grid_cap = setup.resident;
   if (a.lines <= 0) return cudaSuccess;
   const long long groups = (a.lines + S::G - 1) / S::G;
   const int grid = int(groups < grid_cap ? groups : grid_cap);
@@ -920,8 +937,6 @@ cudaError_t launch_fourstep_n(const RowArgs& a, cudaStream_t stream) {
   constexpr int N1 = N / 4096;
   constexpr size_t kBytes = fourstep_smem_bytes<TS, N / 4096>();
   auto kern = fft_fourstep_kernel<N, TS, MODE, SCALED>;
-  static bool configured = false;
-  static int resident_clusters = 0;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = kBytes;
@@ -933,18 +948,23 @@ cudaError_t launch_fourstep_n(const RowArgs& a, cudaStream_t stream) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (!configured) {
+  // One-time set-up (thread-safe, see setup_kernel): attributes and the
+  // number of resident clusters.
+  static const LaunchSetup setup = [&]() -> LaunchSetup {
+    LaunchSetup r{cudaSuccess, 0};
     if (N1 > 8) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      if (e != cudaSuccess) return e;
+      r.err = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (r.err != cudaSuccess) return r;
     }
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBytes));
-    if (e != cudaSuccess) return e;
-    cfg.gridDim = dim3(N1);
-    e = cudaOccupancyMaxActiveClusters(&resident_clusters, kern, &cfg);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+    r.err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBytes));
+    if (r.err != cudaSuccess) return r;
+    cudaLaunchConfig_t probe = cfg;
+    probe.gridDim = dim3(N1);
+    r.err = cudaOccupancyMaxActiveClusters(&r.resident, kern, &probe);
+    return r;
+  }();
+  if (setup.err != cudaSuccess) return setup.err;
+  const int resident_clusters = setup.resident;
   if (a.lines <= 0) return cudaSuccess;
   const long long grid = a.lines * N1;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -1004,14 +1024,8 @@ template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED>
 cudaError_t launch_cluster_n(const RowArgs& a, cudaStream_t stream) {
   using S = ClusterShape<N>;
   auto kern = fft_cluster_kernel<N, TIn, TOut, MODE, NAIVE, SCALED>;
-  static bool configured = false;
-  if (!configured) {
-    if (S::kSmemBytes > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::kSmemBytes));
-      if (e != cudaSuccess) return e;
-    }
-    configured = true;
-  }
+  static const LaunchSetup setup = setup_kernel(kern, S::CTA_T, S::kSmemBytes);
+  if (setup.err != cudaSuccess) return setup.err;
   if (a.lines <= 0) return cudaSuccess;
   const long long grid = a.lines * S::C;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -1043,21 +1057,9 @@ cudaError_t launch_rows_plain_x(const RowArgs& a, cudaStream_t stream, bool l2_p
   using S = RowShape<N>;
   constexpr size_t kBytes = size_t(S::G) * XchSel<N, XV>::kLineBytes;
   auto kern = fft_rows_kernel<N, TIn, TOut, MODE, NAIVE, false, false, false, XV, MINB>;
-  static bool configured = false;
-  static int resident = 0;   // CTAs of this kernel resident on the whole GPU
-  if (!configured) {
-    if (kBytes > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBytes));
-      if (e != cudaSuccess) return e;
-    }
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::kThreads, kBytes);
-    if (e != cudaSuccess) return e;
-    resident = sms * per_sm;
-    configured = true;
-  }
+  static const LaunchSetup setup = setup_kernel(kern, S::kThreads, kBytes);
+  if (setup.err != cudaSuccess) return setup.err;
+  const int resident = setup.resident;   // CTAs of this kernel resident on the whole GPU
   if (a.lines <= 0) return cudaSuccess;
   const long long grid = (a.lines + S::G - 1) / S::G;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -1137,21 +1139,9 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
   }
   auto kern = fft_rows_kernel<N, TIn, TOut, MODE, NAIVE, SCALED, TLOAD, TSTORE>;
   constexpr size_t kBytes = S::kSmemBytes;
-  static bool configured = false;   // attributes are per function; set once
-  static int resident = 0;          // CTAs of this kernel resident on the whole GPU
-  if (!configured) {
-    if (kBytes > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBytes));
-      if (e != cudaSuccess) return e;
-    }
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::kThreads, kBytes);
-    if (e != cudaSuccess) return e;
-    resident = sms * (per_sm > 0 ? per_sm : 1);
-    configured = true;
-  }
+  static const LaunchSetup setup = setup_kernel(kern, S::kThreads, kBytes);
+  if (setup.err != cudaSuccess) return setup.err;
+  const int resident = setup.resident;   // CTAs of this kernel resident on the whole GPU
   if (a.lines <= 0) return cudaSuccess;
   const long long clusters = (a.lines + S::kLinesPerCluster - 1) / S::kLinesPerCluster;
   const long long grid = clusters * S::C;

@@ -326,12 +326,9 @@ cudaError_t launch_typed(const void* img, long long n_az, long long n_rg, const 
                          double* out, void* ws, cudaStream_t s) {
   const size_t smem = size_t(2 * kW * kW) * sizeof(double2) + size_t(2 * kFine) * sizeof(double);
   auto kern = target_kernel<T>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // Set once per instantiation, thread-safely (function-local static).
+  static const cudaError_t setup = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (setup != cudaSuccess) return setup;
   kern<<<k, kThreads, smem, s>>>(static_cast<const T*>(img), n_az, n_rg, targets, out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

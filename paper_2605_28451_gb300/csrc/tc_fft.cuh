@@ -250,17 +250,20 @@ __global__ void __launch_bounds__(256, 3) fft_tc_kernel(const RowArgs a) {
 template <class TS, int MODE>
 cudaError_t launch_tc_n(const RowArgs& a, cudaStream_t stream) {
   auto kern = fft_tc_kernel<TS, MODE>;
-  static int grid_cap = 0;
-  if (grid_cap == 0) {
-    // Three CTAs per SM: the register limit of __launch_bounds__(256, 3);
-    // tensor memory would allow eight (64 of 512 columns each), so the
-    // persistent CTAs never wait on each other's allocation.
+  // Three CTAs per SM: the register limit of __launch_bounds__(256, 3);
+  // tensor memory would allow eight (64 of 512 columns each), so the
+  // persistent CTAs never wait on each other's allocation.  Computed once,
+  // thread-safely (function-local static).
+  static const LaunchSetup setup = []() -> LaunchSetup {
+    LaunchSetup r{cudaSuccess, 0};
     int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    grid_cap = 3 * sms;
-  }
+    if ((r.err = cudaGetDevice(&dev)) != cudaSuccess) return r;
+    if ((r.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return r;
+    r.resident = 3 * sms;
+    return r;
+  }();
+  if (setup.err != cudaSuccess) return setup.err;
+  const int grid_cap = setup.resident;
   (void)kern;
   if (a.lines <= 0) return cudaSuccess;
   const int grid = int(a.lines < grid_cap ? a.lines : grid_cap);
