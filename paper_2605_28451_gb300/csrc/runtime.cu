@@ -53,12 +53,19 @@ bool device_memory(const void* p) {
   return attr.type == cudaMemoryTypeDevice;
 }
 
+// The variant to use when the input is not device memory: no bulk L2
+// prefetch of it, and no bulk (TMA) copies from it -- the same exchange with
+// plain loads instead.
 int without_l2(int variant) {
   switch (variant) {
     case bfp::kRowsPlainL2: return bfp::kRowsPlain;
-    case bfp::kRowsPlain4L2: return bfp::kRowsPlain4;
+    case bfp::kRowsPlain4L2:
+    case bfp::kRowsTma: return bfp::kRowsPlain4;
+    case bfp::kRowsTmaPP: return bfp::kRowsPlainPP;
     case bfp::kRowsPlainHL2:
-    case bfp::kRowsPlainH4L2: return bfp::kRowsPlainH;
+    case bfp::kRowsPlainH4L2:
+    case bfp::kRowsTmaH: return bfp::kRowsPlainH;
+    case bfp::kRowsTmaHPP: return bfp::kRowsPlainHPP;
     default: return variant;
   }
 }

@@ -226,12 +226,18 @@ def test_prefetching_variants_over_many_waves(variant, n, batch, monkeypatch):
         assert ok, (variant, n, direction, worst)
 
 
+@pytest.mark.parametrize("variant", [None, "tma"])
 @pytest.mark.parametrize("n,batch", [(4096, 300), (65536, 12)])
-def test_exec_reads_and_writes_pinned_host_buffers(n, batch):
+def test_exec_reads_and_writes_pinned_host_buffers(n, batch, variant, monkeypatch):
     """Pinned host buffers passed straight to bfpfft_exec: the kernels read
     and write them in place over the CPU-GPU link (no staging copies, no L2
-    prefetch of host memory); results are bit-identical to device buffers."""
+    prefetch and no bulk copies from host memory: a bulk-copy variant falls
+    back to plain loads); results are bit-identical to device buffers."""
     import torch
+    if variant is None:
+        monkeypatch.delenv("BFPFFT_ROWS", raising=False)
+    else:
+        monkeypatch.setenv("BFPFFT_ROWS", variant)
     x = storage_round(synth.complex_gaussian(batch, n, seed=n + 1), B.F16_BFP)
     dev_in = to_device(x, B.F16_BFP)
     host_in = torch.empty(dev_in.shape, dtype=dev_in.dtype, pin_memory=True)
