@@ -23,13 +23,17 @@ definition, in float64 / complex128:
 * ``oracle.autofocus`` -- image entropy of the azimuth-compressed image under
                           a per-pulse phase correction and its analytic
                           adjoint gradient.
+* ``oracle.emulate``   -- a radix-2 FFT with rounding hooks at storage points,
+                          products and sums: the precision modes of Tables I
+                          and V and Section VI, and the error model that
+                          predicts a storage schedule's SQNR.
 
 Pins: each function is checked by the ``-m "not gpu"`` tests against facts
 fixed by the mathematics or printed in the paper (brute-force DFT, Parseval,
 impulse / constant spectra, round trips, shift theorem, chirp closed forms,
-format edge values, finite differences).  Two readings stay unpinned by the
-paper and say so in their docstrings: the FP8 storage floor and the FP16
+format edge values, finite differences, the SQNRs of Tables I and V).  One
+reading stays unpinned by the paper and says so in its docstring: the FP16
 autofocus gradient tolerance.
 """
 
-from . import fft, quant, sar, metrics, autofocus  # noqa: F401
+from . import fft, quant, sar, metrics, autofocus, emulate  # noqa: F401
