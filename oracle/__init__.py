@@ -27,6 +27,10 @@ definition, in float64 / complex128:
                           products and sums: the precision modes of Tables I
                           and V and Section VI, and the error model that
                           predicts a storage schedule's SQNR.
+* ``oracle.conv``      -- circular convolution and correlation by their
+                          defining sums, and the forward-multiply-inverse
+                          pipeline that computes them (Section VIII).
+* ``oracle.bfp``       -- adaptive per-line block exponents (Section VIII).
 
 Pins: each function is checked by the ``-m "not gpu"`` tests against facts
 fixed by the mathematics or printed in the paper (brute-force DFT, Parseval,
@@ -36,4 +40,4 @@ reading stays unpinned by the paper and says so in its docstring: the FP16
 autofocus gradient tolerance.
 """
 
-from . import fft, quant, sar, metrics, autofocus, emulate  # noqa: F401
+from . import fft, quant, sar, metrics, autofocus, emulate, conv, bfp  # noqa: F401
