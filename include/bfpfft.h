@@ -206,6 +206,10 @@ int sar_make_filter(const void* ref, int64_t n, int peak_normalise, void* h_out,
  * between calls; with the environment variable BFPFFT_SAR_TURN=fused it is
  * done on chip by a thread-block cluster instead (no scratch).
  * n_az = 0 is a no-op.  out must not overlap raw when transpose_out = 1.
+ * With transpose_out = 0 this is the general batched forward-multiply-inverse
+ * pipeline of Section VIII (Generality) on dense lines: hr = DFT(g) gives the
+ * circular convolution of each line with g, hr = conj(DFT(g)) the circular
+ * correlation (the range matched filter is the correlation with the pulse).
  * Errors: INVALID_ARG, MISALIGNED, UNSUPPORTED (n_rg or dtypes), OOM (scratch),
  * CUDA.
  */
