@@ -31,6 +31,9 @@ definition, in float64 / complex128:
                           defining sums, and the forward-multiply-inverse
                           pipeline that computes them (Section VIII).
 * ``oracle.bfp``       -- adaptive per-line block exponents (Section VIII).
+* ``oracle.rda``       -- range-Doppler processing with range-cell migration
+                          correction and a range-dependent azimuth filter
+                          (Section VI's RCMC stage).
 
 Pins: each function is checked by the ``-m "not gpu"`` tests against facts
 fixed by the mathematics or printed in the paper (brute-force DFT, Parseval,
@@ -40,4 +43,4 @@ reading stays unpinned by the paper and says so in its docstring: the FP16
 autofocus gradient tolerance.
 """
 
-from . import fft, quant, sar, metrics, autofocus, emulate, conv, bfp  # noqa: F401
+from . import fft, quant, sar, metrics, autofocus, emulate, conv, bfp, rda  # noqa: F401

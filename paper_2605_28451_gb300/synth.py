@@ -16,7 +16,9 @@ Workload shapes follow the paper's experiments:
   samples, K = B / Tp), an azimuth chirp of L_a = 1024 pulses with a Doppler
   bandwidth of 0.8 PRF (normalised rate k_a = 0.8 / L_a), 8 targets with
   amplitudes 10^(-k/7), and complex AWGN of variance 0.01 (20 dB below the
-  unit-amplitude target per sample).  Range-cell migration is neglected.
+  unit-amplitude target per sample).  Range-cell migration is neglected in
+  point_target_scene; migrating_scene adds it (wavelength 0.03 m, exact
+  hyperbolic range history) for the range-cell-migration correction.
 """
 
 from __future__ import annotations
@@ -35,6 +37,15 @@ AZIMUTH_DOPPLER_FRACTION = 0.8
 NOISE_VARIANCE = 0.01
 N_TARGETS = 8
 MIN_TARGET_SEPARATION = 128
+
+# Geometry of the scene with range-cell migration (Section VI gives X band,
+# v = 100 m/s and R0 = 20 km; the completion adds a wavelength of 0.03 m and
+# a PRF chosen so that the azimuth FM rate at R0 gives the same normalised
+# rate k_a = 0.8 / L_a as the migration-free scene).
+WAVELENGTH_M = 0.03
+PLATFORM_SPEED_MPS = 100.0
+SCENE_CENTRE_RANGE_M = 20e3
+SPEED_OF_LIGHT_MPS = 299792458.0
 
 # Uneven-batch lengths (mixed-length workload, Zipf-like weights).
 UNEVEN_LENGTHS = (256, 1024, 4096, 16384, 65536)
@@ -153,6 +164,71 @@ def point_target_scene(n_az: int, n_rg: int, aperture: int = AZIMUTH_APERTURE,
     return Scene(raw=raw,
                  ref_range=centred_reference(sr, n_rg),
                  ref_azimuth=centred_reference(sa[: min(aperture, n_az)], n_az),
+                 targets=list(targets))
+
+
+@dataclass
+class Geometry:
+    range_cell_m: float           # slant-range sample spacing c / (2 fs)
+    prf_hz: float                 # pulse repetition frequency
+    wavelength_m: float
+    speed_mps: float
+    centre_range_m: float         # slant range of range cell n_rg / 2
+
+
+def radar_geometry(aperture: int = AZIMUTH_APERTURE,
+                   doppler_fraction: float = AZIMUTH_DOPPLER_FRACTION) -> Geometry:
+    """Scene geometry: the PRF makes Ka(R0) / PRF^2 = doppler_fraction / aperture,
+    with Ka(R) = 2 v^2 / (lambda R) the azimuth FM rate in Hz/s."""
+    ka_hz = 2.0 * PLATFORM_SPEED_MPS ** 2 / (WAVELENGTH_M * SCENE_CENTRE_RANGE_M)
+    prf = math.sqrt(ka_hz * aperture / doppler_fraction)
+    return Geometry(range_cell_m=SPEED_OF_LIGHT_MPS / (2.0 * RANGE_SAMPLE_RATE_HZ), prf_hz=prf,
+                    wavelength_m=WAVELENGTH_M, speed_mps=PLATFORM_SPEED_MPS,
+                    centre_range_m=SCENE_CENTRE_RANGE_M)
+
+
+def slant_range_m(r_cell, n_rg: int, geo: Geometry):
+    """Slant range of range cell r (cell n_rg / 2 is at the scene-centre range)."""
+    return geo.centre_range_m + (np.asarray(r_cell, dtype=np.float64) - n_rg / 2) * geo.range_cell_m
+
+
+def migrating_scene(n_az: int, n_rg: int, targets, aperture: int = AZIMUTH_APERTURE,
+                    noise: bool = False, noise_seed: int = 2) -> Scene:
+    """Raw echo with range-cell migration and the exact hyperbolic range history.
+
+    Target (eta_k, r_k, a_k) at slant range R_k = slant_range_m(r_k) is seen
+    over the pulses |eta - eta_k| < L_a / 2 at range
+        R_k(eta) = sqrt(R_k^2 + (v (eta - eta_k) / PRF)^2),
+    so its echo is
+        a_k chirp((r - r_k - d) / fs) exp(-j 4 pi (R_k(eta) - R_k) / lambda),
+        d = (R_k(eta) - R_k) / range_cell,
+    with chirp(tau) = exp(j pi K tau^2) for -Tp/2 <= tau < Tp/2 (the pulse of
+    range_chirp, evaluated at the delayed sample times).  With d = 0 and the
+    phase expanded to second order this is point_target_scene's echo.
+    Noise, when asked for, is as in point_target_scene.
+    """
+    m, k, fs = range_chirp_params()
+    geo = radar_geometry(aperture)
+    tp = m / fs
+    raw = np.zeros((n_az, n_rg), dtype=np.complex128)
+    rr = np.arange(n_rg)
+    for eta, r, a in targets:
+        r_k = float(slant_range_m(r, n_rg, geo))
+        for e in range(max(eta - aperture // 2, 0), min(eta - aperture // 2 + aperture, n_az)):
+            t = (e - eta) / geo.prf_hz
+            r_e = math.sqrt(r_k * r_k + (geo.speed_mps * t) ** 2)
+            d = (r_e - r_k) / geo.range_cell_m
+            tau = (rr - r - d) / fs
+            inside = (tau >= -tp / 2) & (tau < tp / 2)
+            phase = np.pi * k * tau * tau - 4.0 * np.pi * (r_e - r_k) / geo.wavelength_m
+            raw[e] += np.where(inside, a * np.exp(1j * phase), 0.0)
+    if noise:
+        rng = np.random.default_rng(noise_seed)
+        s = math.sqrt(NOISE_VARIANCE / 2.0)
+        raw += s * rng.standard_normal((n_az, n_rg))
+        raw += 1j * s * rng.standard_normal((n_az, n_rg))
+    return Scene(raw=raw, ref_range=centred_reference(range_chirp(), n_rg),
+                 ref_azimuth=centred_reference(azimuth_chirp(aperture)[: min(aperture, n_az)], n_az),
                  targets=list(targets))
 
 

@@ -111,3 +111,18 @@ def test_uneven_batch_packs_transforms_contiguously():
     data, offsets = synth.uneven_batch(lengths, seed=1)
     assert data.shape == (256 + 16 + 4096,)
     assert offsets.tolist() == [0, 256, 272]
+
+
+def test_migrating_scene_support_and_phase():
+    """Each pulse of the aperture carries one unit-modulus pulse of M samples
+    (give or take one where the fractional delay moves the window), and the
+    pulse at the aperture centre has no migration: it equals the
+    migration-free echo there."""
+    m = synth.range_chirp_params()[0]
+    sc = synth.migrating_scene(2048, 1024, [(1024, 512, 1.0)])
+    rows = np.count_nonzero(sc.raw, axis=1)
+    assert np.all((rows[512:1536] >= m - 1) & (rows[512:1536] <= m + 1))
+    assert rows[:512].sum() == 0 and rows[1536:].sum() == 0
+    assert np.allclose(np.abs(sc.raw[sc.raw != 0]), 1.0)
+    flat = synth.point_target_scene(2048, 1024, noise=False, targets=[(1024, 512, 1.0)])
+    assert np.allclose(sc.raw[1024], flat.raw[1024], atol=1e-9)

@@ -149,3 +149,24 @@ def test_block_exponent_off_by_one_is_caught(monkeypatch):
     monkeypatch.setattr(bfp, "np", _Proxy(np, ceil=lambda a: real_ceil(a) + 1,
                                           where=lambda c, a, b: b))      # skip the exactness corrections
     assert not np.array_equal(bfp.block_exponent(v), want)
+
+
+def test_rcmc_in_the_wrong_direction_is_caught(monkeypatch):
+    """RCMC that moves each Doppler row the wrong way doubles the migration
+    instead of removing it; the straightened-peak pin sees about a cell."""
+    from oracle import rda
+    geo = synth.radar_geometry()
+    sc = synth.migrating_scene(2048, 1024, [(1024, 512, 1.0)])
+    rd = rda.range_doppler(sar.range_compress(sc.raw, sar.matched_filter(sc.ref_range, False)))
+    f = rda.doppler_frequencies(2048, geo.prf_hz)
+    k = int(np.argmin(np.abs(f - 0.33 * geo.prf_hz)))
+
+    def peak(row):
+        up = np.abs(np.fft.ifft(np.concatenate([np.fft.fft(row)[:512], np.zeros(31 * 1024),
+                                                np.fft.fft(row)[512:]])))
+        return float(np.argmax(up)) / 32
+
+    assert abs(peak(rda.rcmc(rd, geo, 1024)[k]) - 512) <= 0.05
+    real_shift = rda.shift_rows
+    monkeypatch.setattr(rda, "shift_rows", lambda x, cells: real_shift(x, -np.asarray(cells)))
+    assert abs(peak(rda.rcmc(rd, geo, 1024)[k]) - 512) > 0.5
