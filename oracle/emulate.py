@@ -122,3 +122,94 @@ def count_storage_points(n: int, store_stages=None, store_input: bool = True) ->
 def predict_sqnr_db(points: int, fraction_bits: int, c: float) -> float:
     """SQNR of ``points`` independent roundings of relative noise power c 2^(-2p) each."""
     return -10.0 * np.log10(points * c * 2.0 ** (-2 * fraction_bits))
+
+
+# ---- radix-16 schedule with every operation rounded -------------------------
+#
+# The same precision mode ("pure FP16": every add and multiply in the storage
+# format) on a radix-16 Stockham schedule instead of radix 2: each pass
+# multiplies point r of butterfly j by W_{16 Ns}^{(j mod Ns) r}, runs a 16-point
+# DFT as two layers of 4-point DFTs around the internal twiddles W16^{r1 k2},
+# and writes point r to (j / Ns) 16 Ns + (j mod Ns) + r Ns.  The complex
+# product by a stored twiddle w = (c, s) takes two rounded steps,
+#     t = rn(a.re * (c, s)),   a w = rn(a.im * (-s, c) + t)   (fused),
+# and the products by W16^2, W16^6 and -i are a rounded sum and a rounded
+# product by the stored sqrt(1/2), and an exact swap.  Twiddles are rounded
+# once from their exact values.  With op = None it is the exact DFT.
+
+
+def _r(op, v):
+    return v if op is None else op(v)
+
+
+def _cmul16(op, ar, ai, wr, wi):
+    tr, ti = _r(op, ar * wr), _r(op, ar * wi)
+    return _r(op, ai * (-wi) + tr), _r(op, ai * wr + ti)
+
+
+def _dft4_16(op, a):
+    (r0, i0), (r1, i1), (r2, i2), (r3, i3) = a
+    t0 = (_r(op, r0 + r2), _r(op, i0 + i2))
+    t1 = (_r(op, r0 - r2), _r(op, i0 - i2))
+    t2 = (_r(op, r1 + r3), _r(op, i1 + i3))
+    e = (_r(op, i1 - i3), -_r(op, r1 - r3))              # -i (a1 - a3), rounded once
+    return [(_r(op, t0[0] + t2[0]), _r(op, t0[1] + t2[1])),
+            (_r(op, t1[0] + e[0]), _r(op, t1[1] + e[1])),
+            (_r(op, t0[0] - t2[0]), _r(op, t0[1] - t2[1])),
+            (_r(op, t1[0] - e[0]), _r(op, t1[1] - e[1]))]
+
+
+def _dft16_rounded(op, v):
+    v = list(v)
+    for r1 in range(4):
+        v[r1], v[r1 + 4], v[r1 + 8], v[r1 + 12] = _dft4_16(op, [v[r1], v[r1 + 4], v[r1 + 8], v[r1 + 12]])
+    c1, s1, h = _r(op, np.cos(np.pi / 8)), _r(op, np.sin(np.pi / 8)), _r(op, np.sqrt(0.5))
+
+    def w2(a):
+        return _r(op, _r(op, a[0] + a[1]) * h), _r(op, _r(op, a[1] - a[0]) * h)
+
+    def w6(a):
+        return _r(op, _r(op, a[1] - a[0]) * h), _r(op, _r(op, -a[0] - a[1]) * h)
+
+    v[5] = _cmul16(op, *v[5], c1, -s1)
+    v[9] = w2(v[9])
+    v[13] = _cmul16(op, *v[13], s1, -c1)
+    v[6] = w2(v[6])
+    v[10] = (v[10][1], -v[10][0])
+    v[14] = w6(v[14])
+    v[7] = _cmul16(op, *v[7], s1, -c1)
+    v[11] = w6(v[11])
+    v[15] = _cmul16(op, *v[15], -c1, s1)
+    out = [None] * 16
+    for k2 in range(4):
+        a = _dft4_16(op, [v[4 * k2], v[4 * k2 + 1], v[4 * k2 + 2], v[4 * k2 + 3]])
+        for k1 in range(4):
+            out[k2 + 4 * k1] = a[k1]
+    return out
+
+
+def fft_radix16_rounded(x: np.ndarray, op: Hook = None) -> np.ndarray:
+    """Forward DFT along the last axis (N a power of 16) on the radix-16 schedule, rounding every operation."""
+    x = np.asarray(x, dtype=np.complex128)
+    n = x.shape[-1]
+    if n < 16 or 16 ** round(np.log(n) / np.log(16)) != n:
+        raise ValueError(f"length {n} is not a power of 16")
+    re, im = _r(op, x.real.copy()), _r(op, x.imag.copy())
+    q = n // 16
+    j = np.arange(q)
+    ns = 1
+    while ns < n:
+        k = j % ns
+        u = [(re[..., j + q * r], im[..., j + q * r]) for r in range(16)]
+        if ns > 1:
+            for r in range(1, 16):
+                w = np.exp(-2j * np.pi * k * r / (16 * ns))
+                u[r] = _cmul16(op, *u[r], _r(op, w.real), _r(op, w.imag))
+        o = _dft16_rounded(op, u)
+        nre, nim = np.empty_like(re), np.empty_like(im)
+        base = (j // ns) * ns * 16 + k
+        for r in range(16):
+            nre[..., base + r * ns], nim[..., base + r * ns] = o[r]
+        re, im = nre, nim
+        ns *= 16
+    return re + 1j * im

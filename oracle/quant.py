@@ -98,9 +98,7 @@ def _round_bf16_real(x: np.ndarray) -> np.ndarray:
         q = np.round(a / quantum) * quantum       # ties to even
     q = np.where(q > BF16_MAX, np.inf, q)        # round-to-nearest overflows to infinity
     q = np.where(np.isinf(a), np.inf, q)
-    out = np.copysign(q, x)
-    out[nan] = np.nan
-    return out
+    return np.where(nan, np.nan, np.copysign(q, x))
 
 
 def round_bfloat16(x: np.ndarray) -> np.ndarray:

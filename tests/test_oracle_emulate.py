@@ -201,3 +201,35 @@ def test_planted_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(E.np, "exp", bad_exp)
     got = E.fft_rounded(x)
     assert np.max(np.abs(got - ref)) > 1e-3
+
+
+@pytest.mark.parametrize("n", [16, 256])
+def test_radix16_schedule_unrounded_is_the_dft(n):
+    x = synth.complex_gaussian(3, n, seed=n + 5)
+    ref = F.dft_bruteforce(x, -1)
+    got = E.fft_radix16_rounded(x)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert np.array_equal(E.fft_radix16_rounded(x, lambda v: v), got)
+
+
+def test_radix16_schedule_at_4096_matches_the_radix2_fft():
+    x = synth.complex_gaussian(2, 4096, seed=9)
+    assert metrics.rel_l2(F.fft(x), E.fft_radix16_rounded(x)) <= 1e-13
+
+
+def test_radix16_schedule_rejects_other_lengths():
+    with pytest.raises(ValueError):
+        E.fft_radix16_rounded(np.ones((1, 512), complex))
+
+
+def test_radix16_pure_fp16_rounds_less_than_radix2_and_follows_the_mantissa_rule():
+    """Radix 16 takes fewer rounded operations per point than radix 2, so its
+    pure-FP16 SQNR is at least Table I's radix-2 figure; bfloat16 on the same
+    schedule loses the three fraction bits' 18.06 dB."""
+    x = synth.complex_gaussian(LINES, 4096, seed=80)
+    x16, xb = Q.round_binary16(x), Q.round_bfloat16(x)
+    r16 = metrics.sqnr_db(F.fft(x16), E.fft_radix16_rounded(x16, Q.round_binary16))
+    r2 = metrics.sqnr_db(F.fft(x16), E.fft_mode(x16, "pure_fp16"))
+    rb = metrics.sqnr_db(F.fft(xb), E.fft_radix16_rounded(xb, Q.round_bfloat16))
+    assert r16 > r2 >= 55.0
+    assert abs((r16 - rb) - 20.0 * math.log10(8.0)) <= 0.5, (r16, rb)
