@@ -233,3 +233,27 @@ def test_radix16_pure_fp16_rounds_less_than_radix2_and_follows_the_mantissa_rule
     rb = metrics.sqnr_db(F.fft(xb), E.fft_radix16_rounded(xb, Q.round_bfloat16))
     assert r16 > r2 >= 55.0
     assert abs((r16 - rb) - 20.0 * math.log10(8.0)) <= 0.5, (r16, rb)
+
+
+@pytest.mark.parametrize("plant", ["products_exact", "sums_exact"])
+def test_table_1_pin_catches_a_dropped_rounding(plant):
+    """Leaving the products (or the sums) unrounded moves the pure-FP16 SQNR
+    by more than the Table I tolerance."""
+    want = GOLDEN["fp16_fft_sqnr_context_db"]["standard_butterfly"][1]
+    x = Q.round_binary16(_gauss(4096, 11))
+    mul = None if plant == "products_exact" else Q.round_binary16
+    add = None if plant == "sums_exact" else Q.round_binary16
+    s = metrics.sqnr_db(F.fft(x), E.fft_rounded(x, store=Q.round_binary16, mul=mul, add=add))
+    assert abs(s - want) > 0.5, s
+
+
+@pytest.mark.parametrize("plant", ["every_other_stage", "unrounded_input"])
+def test_table_5_pin_catches_a_wrong_storage_schedule(plant):
+    want = GOLDEN["fp8_sqnr_context_db"]["fp16"][1]
+    x = _gauss(4096, 21)
+    if plant == "every_other_stage":
+        got = E.fft_rounded(x, store=Q.round_binary16, store_stages=set(range(2, 13, 2)))
+    else:
+        got = E.fft_rounded(x, store=Q.round_binary16, store_input=False)
+    s = metrics.sqnr_db(F.fft(x), got)
+    assert abs(s - want) > 0.3, s
