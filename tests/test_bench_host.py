@@ -1,0 +1,46 @@
+"""Host-side helpers of bench.py on CPU: the clock summary, the traffic record
+lookup and the roofline peak source.  No GPU is involved."""
+
+import json
+
+import bench
+
+
+def test_clock_summary_median_max_and_reasons():
+    c = bench.ClockSampler(0)
+    c.samples = [
+        ["2070", "2070", "Not Active", "Not Active", "Not Active", "Not Active"],
+        ["1980", "2070", "Not Active", "Not Active", "Not Active", "Active"],
+        ["2055", "2070", "Not Active", "Not Active", "Not Active", "Not Active"],
+        ["[N/A]", "2070", "Not Active", "Not Active", "Not Active", "Not Active"],
+    ]
+    s = c.summary()
+    assert s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 4
+
+
+def test_clock_summary_without_samples():
+    s = bench.ClockSampler(0).summary()
+    assert s["sm_mhz"] is None and s["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_traffic_record_is_used_only_for_the_current_sources(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic.txt").write_text(
+        "# tag hash launch bytes\n"
+        "rows16 aaaa 1 100\n"
+        "rows16 bbbb 1 200\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "_kernel_source_hash", lambda: "bbbb")
+    assert bench._profiled_traffic("rows16") == 200.0
+    monkeypatch.setattr(bench, "_kernel_source_hash", lambda: "cccc")
+    assert bench._profiled_traffic("rows16") is None         # sources changed since the capture
+    assert bench._profiled_traffic("other") is None
+
+
+def test_peak_source(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._peaks() == (bench.FALLBACK_HBM_GBS, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6701.5}))
+    assert bench._peaks() == (6701.5, "measured")
