@@ -53,7 +53,15 @@ enum bfpfft_dtype {
   BFPFFT_F16_BFP = 1,    /* FP16 storage with the fixed 1/N block shift (Eq. 1) */
   BFPFFT_F16_NAIVE = 2,  /* FP16 storage without the shift (Section III-B's failing path) */
   BFPFFT_E4M3_BFP = 3,   /* FP8 E4M3 storage, static block exponents (Section VII) */
-  BFPFFT_E5M2_BFP = 4    /* FP8 E5M2 storage, static block exponents (Section VII) */
+  BFPFFT_E5M2_BFP = 4,   /* FP8 E5M2 storage, static block exponents (Section VII) */
+  BFPFFT_F16_ADAPTIVE = 5  /* FP16 mantissas (half2) plus one int32 exponent per line, chosen from
+                              the line's block maximum (Section VIII): bfpfft_exec_adaptive */
+};
+
+/* Plan flags (bfpfft_plan_set_flags). */
+enum bfpfft_flags {
+  BFPFFT_CHECK_FINITE = 1  /* every output store checks its value; a non-finite one sets the
+                              plan's status to BFPFFT_ERR_NONFINITE (read by bfpfft_plan_status) */
 };
 
 enum bfpfft_direction {
@@ -161,13 +169,95 @@ int bfpfft_plan_scale_exp(bfpfft_plan plan, int* in_exp, int* out_exp);
 
 /*
  * Read and clear the current device's status word after a device-wide
- * synchronisation.  Kernels with bounded device-side waits (the pipelined row
- * kernels that stream lines through shared memory with bulk asynchronous
- * copies) record BFPFFT_ERR_TIMEOUT there instead of spinning forever;
- * BFPFFT_OK means no wait expired since the last call.  Errors: INVALID_ARG
- * (status NULL), CUDA.
+ * synchronisation.  The calls that take no plan (the SAR compressions,
+ * sar_make_filter and autofocus) record errors of their device-side bounded
+ * waits there: BFPFFT_ERR_TIMEOUT where a wait expired instead of spinning
+ * forever; BFPFFT_OK means no wait expired since the last call.  Plans have
+ * a word of their own (bfpfft_plan_status).  Errors: INVALID_ARG (status
+ * NULL), CUDA.
  */
 int bfpfft_device_status(int* status);
+
+/*
+ * Read and clear the plan's own status word after a device-wide
+ * synchronisation (call it on the plan's device).  Its kernels record there:
+ *   BFPFFT_ERR_TIMEOUT   a bounded device-side wait expired (bulk-copy
+ *                        pipelines, four-step exchanges, tensor-core commits);
+ *                        the kernel stopped working and returned, and its
+ *                        output is not valid;
+ *   BFPFFT_ERR_NONFINITE with BFPFFT_CHECK_FINITE set: an output value was Inf
+ *                        or NaN (the naive FP16 schedule of Section III-B
+ *                        overflows; the shifted schedule of Eq. 1 does not).
+ * The first error recorded since the last read is kept (a timeout may replace
+ * a non-finite report, not the reverse).  BFPFFT_OK: neither happened.
+ * Errors: INVALID_ARG (NULL plan or status), CUDA.
+ */
+int bfpfft_plan_status(bfpfft_plan plan, int* status);
+
+/*
+ * Set the plan's flags: 0 or BFPFFT_CHECK_FINITE (the output stores of every
+ * later exec check their values; the check costs no extra memory traffic).
+ * A graph captured by bfpfft_exec_graph is dropped and captured again.
+ * Errors: INVALID_ARG (NULL plan or an unknown flag bit).
+ */
+int bfpfft_plan_set_flags(bfpfft_plan plan, int flags);
+
+/*
+ * Failure-detection self-test (not in the paper): enqueue on `stream` one
+ * small kernel that arms a device-side barrier for a copy that is never
+ * issued and waits for it with the same bounded wait the transform kernels
+ * use.  The bound (one second of GPU wall time) expires, the kernel records
+ * BFPFFT_ERR_TIMEOUT in the plan's status word and returns; the context stays
+ * usable.  bfpfft_plan_status then reads BFPFFT_ERR_TIMEOUT.  The plan's
+ * buffers and tables are not touched.  Errors: INVALID_ARG, CUDA.
+ */
+int bfpfft_plan_selftest_wait(bfpfft_plan plan, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Adaptive per-line block exponents (Section VIII, Limitations).
+ *
+ * The fixed 1/N shift of Eq. 1 suits inputs of known scale.  For inputs of any
+ * amplitude the paper names the alternative: one exponent per block, picked
+ * by a block-max reduction.  Here a block is one line.  After the line's
+ * transform(s) in FP32, m = max over the line of |Re| and |Im|; the exponent
+ * e is the smallest integer with m * 2^-e <= 2^14, read from the bits of the
+ * FP32 maximum; the line is stored as FP16 mantissas RN(v * 2^-e) (largest
+ * component in (2^13, 2^14]) plus e.  Its value is mantissa * 2^e.  A zero
+ * line gets e = 0; a line holding Inf or NaN is stored unscaled with e = 0.
+ * Mantissas: half2 [lines][n]; exponents: int32 [lines] device arrays.
+ * Lengths: powers of two in [16, 16384].
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Execute a plan of dtype BFPFFT_F16_ADAPTIVE (created by bfpfft_plan_create;
+ * n <= 16384; bfpfft_exec rejects such a plan with INVALID_ARG).  in: FP16
+ * mantissas [batch][n]; in_exp: int32 [batch] input exponents, or NULL for all
+ * zero (values = the FP16 numbers themselves; exponents are clamped to
+ * [-252, 252]); out: FP16 mantissas [batch][n]; out_exp: int32 [batch],
+ * written.  Forward: X = DFT(x); inverse: the normalised inverse DFT with its
+ * 1/N folded into the pre-inverse conjugate (Eq. 1).  Arithmetic FP32.
+ * in == out is allowed (and in_exp == out_exp).  Asynchronous on `stream`.
+ * Errors: INVALID_ARG (NULL plan / buffer / out_exp, or a plan of another
+ * dtype), MISALIGNED, CUDA.
+ */
+int bfpfft_exec_adaptive(bfpfft_plan plan, const void* in, const int32_t* in_exp, void* out, int32_t* out_exp,
+                         void* stream);
+
+/*
+ * Forward-multiply-inverse with an adaptive output exponent per line (the
+ * general pipeline of Section VIII's Generality paragraph, stored as above):
+ * out, out_exp = IDFT(DFT(x) . H) per line of n points, `lines` lines.
+ *   x      x_dtype BFPFFT_F32 (complex64 values; x_exp must be NULL) or
+ *          BFPFFT_F16_ADAPTIVE (FP16 mantissas with x_exp, or NULL for zeros)
+ *   h      float2[n] filter spectrum (conj(DFT(ref)) for a matched filter)
+ *   out    FP16 mantissas [lines][n]; out_exp int32 [lines]
+ * A SAR range line of any amplitude compresses without overflow: the fixed
+ * shift keeps an unnormalised matched filter's output in FP16 range only for
+ * unit-scale echoes.  lines = 0 is a no-op.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, UNSUPPORTED (n or x_dtype), MISALIGNED, CUDA.
+ */
+int bfp_spectral_adaptive(const void* x, int x_dtype, const int32_t* x_exp, const void* h, void* out,
+                          int32_t* out_exp, int64_t n, int64_t lines, void* stream);
 
 /* ---------------------------------------------------------------------------
  * SAR range-Doppler compression (Section VI, Fig. 1).

@@ -29,11 +29,14 @@ F16_BFP = 1
 F16_NAIVE = 2
 E4M3_BFP = 3
 E5M2_BFP = 4
+F16_ADAPTIVE = 5
 
 FORWARD = -1
 INVERSE = +1
 
-BYTES_PER_POINT = {F32: 8, F16_BFP: 4, F16_NAIVE: 4, E4M3_BFP: 2, E5M2_BFP: 2}
+CHECK_FINITE = 1   # plan flag (enum bfpfft_flags)
+
+BYTES_PER_POINT = {F32: 8, F16_BFP: 4, F16_NAIVE: 4, E4M3_BFP: 2, E5M2_BFP: 2, F16_ADAPTIVE: 4}
 
 _c_int64 = ctypes.c_int64
 _vp = ctypes.c_void_p
@@ -51,6 +54,11 @@ SIGNATURES = {
     "bfpfft_plan_destroy": (ctypes.c_int, [_vp]),
     "bfpfft_plan_scale_exp": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "bfpfft_device_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
+    "bfpfft_plan_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "bfpfft_plan_set_flags": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "bfpfft_plan_selftest_wait": (ctypes.c_int, [_vp, _vp]),
+    "bfpfft_exec_adaptive": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "bfp_spectral_adaptive": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _c_int64, _c_int64, _vp]),
     "sar_make_filter": (ctypes.c_int, [_vp, _c_int64, ctypes.c_int, _vp, _vp]),
     "sar_range_compress": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _c_int64, _c_int64,
                                           ctypes.c_int, _vp]),
@@ -207,6 +215,32 @@ def bfpfft_device_status() -> int:
     st = ctypes.c_int()
     _check(lib().bfpfft_device_status(ctypes.byref(st)), "bfpfft_device_status")
     return st.value
+
+
+def bfpfft_plan_status(plan: Plan) -> int:
+    """Synchronise the device, then read and clear the plan's status word."""
+    st = ctypes.c_int()
+    _check(lib().bfpfft_plan_status(plan.handle, ctypes.byref(st)), "bfpfft_plan_status")
+    return st.value
+
+
+def bfpfft_plan_set_flags(plan: Plan, flags: int):
+    _check(lib().bfpfft_plan_set_flags(plan.handle, int(flags)), "bfpfft_plan_set_flags")
+
+
+def bfpfft_plan_selftest_wait(plan: Plan, stream=None):
+    _check(lib().bfpfft_plan_selftest_wait(plan.handle, _stream(stream)), "bfpfft_plan_selftest_wait")
+
+
+def bfpfft_exec_adaptive(plan: Plan, inp, in_exp, out, out_exp, stream=None):
+    """FP16 mantissas + int32 per-line exponents in and out (in_exp may be None)."""
+    _check(lib().bfpfft_exec_adaptive(plan.handle, _ptr(inp), _ptr(in_exp), _ptr(out), _ptr(out_exp),
+                                      _stream(stream)), "bfpfft_exec_adaptive")
+
+
+def bfp_spectral_adaptive(x, x_dtype: int, x_exp, h, out, out_exp, n: int, lines: int, stream=None):
+    _check(lib().bfp_spectral_adaptive(_ptr(x), int(x_dtype), _ptr(x_exp), _ptr(h), _ptr(out), _ptr(out_exp),
+                                       int(n), int(lines), _stream(stream)), "bfp_spectral_adaptive")
 
 
 def sar_make_filter(ref, n: int, peak_normalise: bool, h_out, stream=None):

@@ -35,6 +35,7 @@ SOURCES = [
     "uneven.cu",
     "pt_metrics.cu",
     "transpose.cu",
+    "rows_adaptive.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -12,7 +12,27 @@ namespace bfp {
 
 constexpr uint32_t kMaxPolls = 1u << 22;
 constexpr unsigned long long kMaxWaitNs = 1000000000ull;   // 1 s of wall time per wait
-constexpr int kStatusTimeout = 5;   // BFPFFT_ERR_TIMEOUT
+constexpr int kStatusTimeout = 5;     // BFPFFT_ERR_TIMEOUT
+constexpr int kStatusNonfinite = 6;   // BFPFFT_ERR_NONFINITE
+
+// Output check of plans with BFPFFT_CHECK_FINITE: a thread that stored a
+// non-finite value records BFPFFT_ERR_NONFINITE in the plan's status word,
+// unless an earlier error is already recorded there.
+__device__ __forceinline__ void note_nonfinite(int* flag, bool bad) {
+  if (bad) atomicCAS(flag, 0, kStatusNonfinite);
+}
+// The check runs as its own loop behind `if (flag != nullptr)`, after the
+// stores, so plans without the flag issue none of its instructions.  value(m)
+// gives the m-th value the thread stored; S::finite says whether it is finite
+// in that storage format.
+template <class S, int P, class F>
+__device__ __forceinline__ void check_finite(int* flag, F value) {
+  if (flag == nullptr) return;
+  bool bad = false;
+#pragma unroll
+  for (int m = 0; m < P; ++m) bad |= !S::finite(value(m));
+  note_nonfinite(flag, bad);
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;

@@ -72,6 +72,9 @@ struct RowArgs {
   const void* tc_b;        // tensor-core variant: 16-point DFT matrix, real form, FP16 [32][32]
   int pf_ahead;            // > 0: each CTA prefetches into L2 the lines of the CTA pf_ahead blocks later
   int no_prefetch;         // nonzero: the input is not device memory; no bulk L2 prefetch of it
+  int* finite_flag;        // non-null: dense-row stores record non-finite outputs here (BFPFFT_CHECK_FINITE)
+  const int* in_exp;       // adaptive exponents: per-line input exponents (value = stored * 2^e), or null
+  int* out_exp;            // adaptive exponents: per-line output exponents written by the kernel
 };
 
 // Row-kernel variants for dense rows of length <= 4096 (chosen by
@@ -616,6 +619,7 @@ fft_rows_kernel(const RowArgs a) {
     TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;
 #pragma unroll
     for (int m = 0; m < P; ++m) Storage<TOut>::store(out + T * m, v[m]);
+    check_finite<Storage<TOut>, P>(a.finite_flag, [&](int m) { return v[m]; });
   }
 }
 
@@ -709,6 +713,7 @@ fft_rows_tma_kernel(const RowArgs a) {
       TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;
 #pragma unroll
       for (int m = 0; m < P; ++m) Storage<TOut>::store(out + T * m, v[m]);
+      check_finite<Storage<TOut>, P>(a.finite_flag, [&](int m) { return v[m]; });
     }
   }
 }
@@ -785,6 +790,13 @@ cudaError_t launch_rows_tma_n(const RowArgs& a, cudaStream_t stream) {
 // by the output buffer (fourstep_smem_bytes in all), initialises `bar` and
 // `bar_out` (one arrival each) and makes them visible to the cluster before
 // the first line.
+// Expired waits.  Both receive waits are bounded (mbar_wait_bounded); the
+// threads of the CTA agree on an expiry with __syncthreads_or, and the line
+// then returns false at once, with `pending` naming the receive barriers whose
+// phase `phase` has not completed (bit 0: row, bit 1: output).  The caller
+// must then stop sending and waiting (no further line on these barriers) and,
+// before the CTA exits, call fourstep_drain so that peers' stores still in
+// flight land before its shared memory goes away.
 template <class TS> struct FsSend {           // step-3 send type: float2, or half2 words for FP16 storage
   using Word = float2;
 };
@@ -801,9 +813,9 @@ __host__ __device__ constexpr size_t fourstep_smem_bytes() {
 }
 
 template <int N1, class TS, int MODE, bool SCALED>
-__device__ __forceinline__ void fourstep_line(const RowArgs& a, const TS* in, TS* out, float2* smem, uint64_t* bar,
-                                              uint64_t* bar_out, uint32_t& phase, int c, int base_rank,
-                                              bool active) {
+__device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS* out, float2* smem, uint64_t* bar,
+                                              uint64_t* bar_out, uint32_t& phase, int& pending, int c,
+                                              int base_rank, bool active) {
   constexpr int N = N1 * 4096, S = 4096 / N1, NB = 16 / N1, P = kPointsPerThread;
   const int t = threadIdx.x;
   const float inv_n = 1.0f / float(N);
@@ -847,10 +859,13 @@ __device__ __forceinline__ void fourstep_line(const RowArgs& a, const TS* in, TS
     }
   }
   // The row is complete when all 32 KB have landed (bounded wait).
-  mbar_wait_bounded(bar, phase, a.status);
+  const bool row_ok = mbar_wait_bounded(bar, phase, a.status);
 #pragma unroll
   for (int m = 0; m < P; ++m) v[m] = smem[pad16(t + 256 * m)];
-  __syncthreads();
+  if (__syncthreads_or(!row_ok)) {
+    pending = kOutXch ? 3 : 1;
+    return false;
+  }
   line_dft<4096>(v, a.tw_line, smem, t);
 #pragma unroll
   for (int m = 0; m < P; ++m) {
@@ -862,7 +877,9 @@ __device__ __forceinline__ void fourstep_line(const RowArgs& a, const TS* in, TS
     if (active) {
 #pragma unroll
       for (int m = 0; m < P; ++m) Storage<TS>::store(out + c + N1 * (t + 256 * m), v[m]);
+      check_finite<Storage<TS>, P>(a.finite_flag, [&](int m) { return v[m]; });
     }
+    return true;
   } else {
     // The owner's buffer holds the values as [k1][k2 mod S] with kPadOut
     // padding slots per segment, so a warp's 32 sends are contiguous; the
@@ -879,7 +896,11 @@ __device__ __forceinline__ void fourstep_line(const RowArgs& a, const TS* in, TS
         st_async_f2(mapa(slot, dst), v[m], mapa(bar_out_local, dst));
       }
     }
-    mbar_wait_bounded(bar_out, phase, a.status);
+    const bool out_ok = mbar_wait_bounded(bar_out, phase, a.status);
+    if (__syncthreads_or(!out_ok)) {
+      pending = 2;
+      return false;
+    }
     phase ^= 1;
     if (active) {
       const Word* ob = reinterpret_cast<const Word*>(smem_out);
@@ -893,8 +914,31 @@ __device__ __forceinline__ void fourstep_line(const RowArgs& a, const TS* in, TS
           Storage<TS>::store(out + c * 4096 + j, w);
         }
       }
+      if constexpr (sizeof(Word) == 4) {
+        check_finite<Storage<TS>, P>(a.finite_flag, [&](int m) {
+          const int j = t + 256 * m;
+          return bits_half2(ob[(j % N1) * (S + kPadOut) + j / N1]);
+        });
+      } else {
+        check_finite<Storage<TS>, P>(a.finite_flag, [&](int m) {
+          const int j = t + 256 * m;
+          return ob[(j % N1) * (S + kPadOut) + j / N1];
+        });
+      }
     }
+    return true;
   }
+}
+
+// After a fourstep_line that returned false: wait (bounded, once more) for the
+// pending receive phases, so that no peer's asynchronous store still targets
+// this CTA's shared memory when it exits.  Peers send into this CTA only what
+// the line's protocol owes it, so these phases complete unless a peer stopped
+// sending; then nothing is in flight and the wait simply expires.
+__device__ __forceinline__ void fourstep_drain(uint64_t* bar, uint64_t* bar_out, uint32_t phase, int pending) {
+  if (pending & 1) mbar_wait_bounded(bar, phase, nullptr);
+  if (pending & 2) mbar_wait_bounded(bar_out, phase, nullptr);
+  __syncthreads();
 }
 
 // Uniform plans with N >= 8192: one line per group of N / 4096 CTAs, a
@@ -927,8 +971,11 @@ __global__ void __launch_bounds__(256, fourstep_smem_bytes<TS, N / 4096>() * 4 <
   cluster_arrive_relaxed();
   cluster_wait_acquire();
   uint32_t phase = 0;
-  fourstep_line<N1, TS, MODE, SCALED>(a, in, out, smem_fs, &bar, &bar_out, phase, c, 0, true);
-  // No CTA leaves while a peer's asynchronous stores may still be in flight.
+  int pending = 0;
+  if (!fourstep_line<N1, TS, MODE, SCALED>(a, in, out, smem_fs, &bar, &bar_out, phase, pending, c, 0, true))
+    fourstep_drain(&bar, &bar_out, phase, pending);
+  // No CTA leaves while a peer's asynchronous stores may still be in flight:
+  // every CTA has received what it waited for (or drained it) before arriving.
   cluster_barrier_relaxed();
 }
 
@@ -1018,6 +1065,7 @@ fft_cluster_kernel(const RowArgs a) {
   TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;
 #pragma unroll
   for (int m = 0; m < P; ++m) Storage<TOut>::store(out + T * m, v[m]);
+  check_finite<Storage<TOut>, P>(a.finite_flag, [&](int m) { return v[m]; });
 }
 
 template <int N, class TIn, class TOut, int MODE, bool NAIVE, bool SCALED>

@@ -17,6 +17,14 @@ cudaError_t launch_compress_f16_to_c64(int log2n, const RowArgs& a, cudaStream_t
 // FP8 rows (fmt 0 = E4M3, 1 = E5M2); mode in {kForward, kInverse}.
 cudaError_t launch_rows_fp8(int log2n, int mode, int fmt, const RowArgs& a, cudaStream_t s);
 
+// Adaptive per-line block exponents (adaptive.cuh), log2n in [4, 14]: FP16
+// mantissas with a.in_exp (may be null) in, FP16 mantissas and a.out_exp out;
+// mode in {kForward, kInverse, kCompress}.  The c64 form reads complex64
+// values and runs the compress (spectral) mode.
+constexpr int kAdaptiveMaxLog2 = 14;
+cudaError_t launch_rows_adaptive_f16(int log2n, int mode, const RowArgs& a, cudaStream_t s);
+cudaError_t launch_spectral_adaptive_c64(int log2n, const RowArgs& a, cudaStream_t s);
+
 // SAR compression lines (Section VI, Fig. 1): float2 or __half2 in and out,
 // optional naive FP16 output, optional cluster corner turn on load / store.
 // Supported log2n: [kSarMinLog2, 14].

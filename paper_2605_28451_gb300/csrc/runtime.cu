@@ -265,7 +265,7 @@ int row_args(int log2n, bfp::RowArgs* a) {
   return fourstep_tables(log2n, a);
 }
 
-bool valid_dtype(int d) { return d >= BFPFFT_F32 && d <= BFPFFT_E5M2_BFP; }
+bool valid_dtype(int d) { return d >= BFPFFT_F32 && d <= BFPFFT_F16_ADAPTIVE; }
 
 // H = conj(H) / max_k |H[k]| (or conj only), one CTA.
 __global__ void conj_normalise_kernel(float2* h, int n, int peak_normalise) {
@@ -298,7 +298,8 @@ struct bfpfft_plan_s {
   int direction;
   int device;
   float2* tw;          // shared table from the per-device cache (not owned)
-  int* status;         // the device's status word (not owned)
+  int* status;         // the plan's own device status word (owned): timeouts, non-finite outputs
+  int flags = 0;       // BFPFFT_CHECK_FINITE
   int in_exp;
   int out_exp;
   int variant = -1;     // row-kernel variant chosen by the tuner (-1: library default)
@@ -324,11 +325,41 @@ namespace {
 
 void free_plan_resources(bfpfft_plan p) {
   if (p->graph) cudaGraphExecDestroy(p->graph);
+  if (p->status) cudaFree(p->status);
   if (p->d_line_off) cudaFree(p->d_line_off);
   if (p->d_tasks) cudaFree(p->d_tasks);
   if (p->d_tw) cudaFree(p->d_tw);
   if (p->d_tw4) cudaFree(p->d_tw4);
   if (p->d_counter) cudaFree(p->d_counter);
+}
+
+// The plan's status word: one device int, zeroed.
+int alloc_plan_status(int** out) {
+  *out = nullptr;
+  int* w = nullptr;
+  cudaError_t e = cudaMalloc(&w, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(w, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    if (w) cudaFree(w);
+    return cuda_status(e);
+  }
+  *out = w;
+  return BFPFFT_OK;
+}
+
+// Wait self-test: one warp arms an mbarrier for 16 bytes that no copy will
+// ever deliver and waits for it with the bounded wait every kernel of the
+// library uses; the bound expires, BFPFFT_ERR_TIMEOUT goes to `status` and
+// the kernel returns.  Nothing is in flight when it exits.
+__global__ void wait_selftest_kernel(int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    bfp::mbar_init(&bar, 1);
+    bfp::fence_proxy_async_shared();
+    bfp::mbar_arrive_expect_tx(&bar, 16);
+  }
+  __syncthreads();
+  bfp::mbar_wait_bounded(&bar, 0, status);
 }
 
 int uneven_kind(int dtype) {
@@ -355,6 +386,7 @@ static int exec_many(bfpfft_plan plan, const void* in, void* out, cudaStream_t s
   a.tw4 = plan->d_tw4;
   a.counter = plan->d_counter;
   a.status = plan->status;
+  a.finite_flag = (plan->flags & BFPFFT_CHECK_FINITE) ? plan->status : nullptr;
   const int variant = rows_variant();   // the _l2 row variants also prefetch the next task into L2
   a.prefetch = (variant == bfp::kRowsPlainL2 || variant == bfp::kRowsPlain4L2 || variant == bfp::kRowsPlainHL2 ||
                 variant == bfp::kRowsPlainH4L2) &&
@@ -437,7 +469,8 @@ size_t storage_bytes(int dtype) {
   switch (dtype) {
     case BFPFFT_F32: return 8;
     case BFPFFT_F16_BFP:
-    case BFPFFT_F16_NAIVE: return 4;
+    case BFPFFT_F16_NAIVE:
+    case BFPFFT_F16_ADAPTIVE: return 4;
     default: return 2;
   }
 }
@@ -448,7 +481,7 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
   if (plan == nullptr || chosen == nullptr) return BFPFFT_ERR_INVALID_ARG;
   *chosen = -1;
   if (best_ms) *best_ms = 0.f;
-  if (plan->batch == 0) return BFPFFT_OK;
+  if (plan->batch == 0 || plan->dtype == BFPFFT_F16_ADAPTIVE) return BFPFFT_OK;   // one kernel, nothing to choose
   // Scratch: a bounded sample of the plan's own shape.
   int64_t points = 0;
   int64_t sample_batch = plan->batch;
@@ -588,7 +621,9 @@ int bfpfft_plan_create(bfpfft_plan* out, int64_t n, int64_t batch, int dtype, in
   if (direction != BFPFFT_FORWARD && direction != BFPFFT_INVERSE) return BFPFFT_ERR_INVALID_ARG;
   const int l = log2_exact(n);
   if (l < kMinLog2 || l > kMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
+  if (dtype == BFPFFT_F16_ADAPTIVE && l > bfp::kAdaptiveMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
   if (fault("plan")) return BFPFFT_ERR_CUDA;
+  if (fault("alloc")) return BFPFFT_ERR_OOM;
   bfpfft_plan p = new (std::nothrow) bfpfft_plan_s();
   if (p == nullptr) return BFPFFT_ERR_OOM;
   p->n = n;
@@ -604,8 +639,9 @@ int bfpfft_plan_create(bfpfft_plan* out, int64_t n, int64_t batch, int dtype, in
   }
   cudaError_t e = cudaGetDevice(&p->device);
   int st = e == cudaSuccess ? get_twiddles(l, &p->tw) : cuda_status(e);
-  if (st == BFPFFT_OK) st = get_status_word(&p->status);
+  if (st == BFPFFT_OK) st = alloc_plan_status(&p->status);
   if (st != BFPFFT_OK) {
+    free_plan_resources(p);
     delete p;
     return st;
   }
@@ -633,6 +669,7 @@ int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, c
     by_class[l].push_back(i);
   }
   if (fault("plan")) return BFPFFT_ERR_CUDA;
+  if (fault("alloc")) return BFPFFT_ERR_OOM;
   std::vector<long long> line_off;
   std::vector<bfp::UnevenTask> tasks;
   line_off.reserve(size_t(count));
@@ -663,7 +700,7 @@ int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, c
   int st = BFPFFT_OK;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) st = cuda_status(e);
-  if (st == BFPFFT_OK) st = get_status_word(&p->status);
+  if (st == BFPFFT_OK) st = alloc_plan_status(&p->status);
   const float2* tw_host[kMaxLog2 + 1] = {};
   const float2* tw4_host[kMaxLog2 + 1] = {};
   for (int l = kMinLog2; l <= kMaxLog2 && st == BFPFFT_OK; ++l) {
@@ -678,7 +715,6 @@ int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, c
       tw4_host[l] = tmp.tw_4step;
     }
   }
-  if (st == BFPFFT_OK && fault("alloc")) st = BFPFFT_ERR_OOM;
   if (st == BFPFFT_OK && count > 0) {
     e = cudaMalloc(&p->d_line_off, sizeof(long long) * line_off.size());
     if (e == cudaSuccess) e = cudaMalloc(&p->d_tasks, sizeof(bfp::UnevenTask) * tasks.size());
@@ -723,6 +759,7 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
     return exec_many(plan, in, out, static_cast<cudaStream_t>(stream));
   }
   if (in == nullptr || out == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (plan->dtype == BFPFFT_F16_ADAPTIVE) return BFPFFT_ERR_INVALID_ARG;   // needs bfpfft_exec_adaptive
   if (!aligned16(in) || !aligned16(out)) return BFPFFT_ERR_MISALIGNED;
   if (fault("launch")) return BFPFFT_ERR_CUDA;
   bfp::RowArgs a{};
@@ -731,6 +768,7 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
   a.tw = plan->tw;
   a.h = nullptr;
   a.status = plan->status;
+  a.finite_flag = (plan->flags & BFPFFT_CHECK_FINITE) ? plan->status : nullptr;
   a.variant = std::getenv("BFPFFT_ROWS") == nullptr && plan->variant >= 0 ? plan->variant : rows_variant();
   if (!device_memory(in)) {
     a.variant = without_l2(a.variant);
@@ -822,15 +860,93 @@ int bfpfft_device_status(int* status) {
   return cuda_status(e);
 }
 
+int bfpfft_plan_status(bfpfft_plan plan, int* status) {
+  if (plan == nullptr || status == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(status, plan->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(plan->status, 0, sizeof(int));
+  return cuda_status(e);
+}
+
+int bfpfft_plan_set_flags(bfpfft_plan plan, int flags) {
+  if (plan == nullptr || (flags & ~BFPFFT_CHECK_FINITE) != 0) return BFPFFT_ERR_INVALID_ARG;
+  plan->flags = flags;
+  if (plan->graph) {   // a captured graph holds the old flags: capture again on the next call
+    cudaGraphExecDestroy(plan->graph);
+    plan->graph = nullptr;
+  }
+  return BFPFFT_OK;
+}
+
+int bfpfft_plan_selftest_wait(bfpfft_plan plan, void* stream) {
+  if (plan == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
+  wait_selftest_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(plan->status);
+  return cuda_status(cudaGetLastError());
+}
+
+int bfpfft_exec_adaptive(bfpfft_plan plan, const void* in, const int32_t* in_exp, void* out, int32_t* out_exp,
+                         void* stream) {
+  if (plan == nullptr || in == nullptr || out == nullptr || out_exp == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (plan->dtype != BFPFFT_F16_ADAPTIVE) return BFPFFT_ERR_INVALID_ARG;
+  if (plan->batch == 0) return BFPFFT_OK;
+  if (!aligned16(in) || !aligned16(out)) return BFPFFT_ERR_MISALIGNED;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
+  bfp::RowArgs a{};
+  a.in = in;
+  a.out = out;
+  a.tw = plan->tw;
+  a.status = plan->status;
+  a.finite_flag = (plan->flags & BFPFFT_CHECK_FINITE) ? plan->status : nullptr;
+  a.no_prefetch = device_memory(in) ? 0 : 1;
+  a.lines = plan->batch;
+  a.in_stride = plan->n;
+  a.out_stride = plan->n;
+  a.in_scale = a.out_scale = 1.f;
+  a.in_exp = in_exp;
+  a.out_exp = out_exp;
+  const int mode = plan->direction == BFPFFT_FORWARD ? bfp::kForward : bfp::kInverse;
+  return cuda_status(bfp::launch_rows_adaptive_f16(plan->log2n, mode, a, static_cast<cudaStream_t>(stream)));
+}
+
+int bfp_spectral_adaptive(const void* x, int x_dtype, const int32_t* x_exp, const void* h, void* out,
+                          int32_t* out_exp, int64_t n, int64_t lines, void* stream) {
+  if (lines < 0) return BFPFFT_ERR_INVALID_ARG;
+  const int l = log2_exact(n);
+  if (l < kMinLog2 || l > bfp::kAdaptiveMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
+  if (x_dtype != BFPFFT_F32 && x_dtype != BFPFFT_F16_ADAPTIVE) return BFPFFT_ERR_UNSUPPORTED;
+  if (x_dtype == BFPFFT_F32 && x_exp != nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (lines == 0) return BFPFFT_OK;
+  if (x == nullptr || h == nullptr || out == nullptr || out_exp == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (!aligned16(x) || !aligned16(h) || !aligned16(out)) return BFPFFT_ERR_MISALIGNED;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
+  bfp::RowArgs a;
+  int st = row_args(l, &a);
+  if (st != BFPFFT_OK) return st;
+  a.in = x;
+  a.out = out;
+  a.h = static_cast<const float2*>(h);
+  a.no_prefetch = device_memory(x) ? 0 : 1;
+  a.lines = lines;
+  a.in_stride = n;
+  a.out_stride = n;
+  a.in_exp = x_exp;
+  a.out_exp = out_exp;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cudaError_t e = x_dtype == BFPFFT_F32 ? bfp::launch_spectral_adaptive_c64(l, a, s)
+                                              : bfp::launch_rows_adaptive_f16(l, bfp::kCompress, a, s);
+  return cuda_status(e);
+}
+
 int sar_make_filter(const void* ref, int64_t n, int peak_normalise, void* h_out, void* stream) {
   if (ref == nullptr || h_out == nullptr) return BFPFFT_ERR_INVALID_ARG;
   if (!aligned16(ref) || !aligned16(h_out)) return BFPFFT_ERR_MISALIGNED;
   const int l = log2_exact(n);
   if (l < kMinLog2 || l > kMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
   bfp::RowArgs a;
   int st = row_args(l, &a);
   if (st != BFPFFT_OK) return st;
-  if (fault("launch")) return BFPFFT_ERR_CUDA;
   a.in = ref;
   a.out = h_out;
   a.lines = 1;
@@ -895,10 +1011,10 @@ int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype,
   if (out_dtype != BFPFFT_F32 && out_dtype != BFPFFT_F16_BFP && out_dtype != BFPFFT_F16_NAIVE)
     return BFPFFT_ERR_UNSUPPORTED;
   if (transpose_out != 0 && transpose_out != 1) return BFPFFT_ERR_INVALID_ARG;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
   bfp::RowArgs a;
   int st = row_args(l, &a);
   if (st != BFPFFT_OK) return st;
-  if (fault("launch")) return BFPFFT_ERR_CUDA;
   a.in = raw;
   a.out = out;
   a.h = static_cast<const float2*>(hr);
@@ -939,10 +1055,10 @@ int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img,
   if (img_dtype != BFPFFT_F32 && img_dtype != BFPFFT_F16_BFP && img_dtype != BFPFFT_F16_NAIVE)
     return BFPFFT_ERR_UNSUPPORTED;
   if (rc_layout != 0 && rc_layout != 1) return BFPFFT_ERR_INVALID_ARG;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
   bfp::RowArgs a;
   int st = row_args(l, &a);
   if (st != BFPFFT_OK) return st;
-  if (fault("launch")) return BFPFFT_ERR_CUDA;
   a.in = rc;
   a.out = img;
   a.h = static_cast<const float2*>(ha);
@@ -1000,10 +1116,10 @@ static int autofocus_common(const void* rc, int rc_dtype, const float* phi, cons
       (grad_out != nullptr && !aligned16(grad_out)))
     return BFPFFT_ERR_MISALIGNED;
   if (ws_bytes < bfp::af_workspace_bytes(n_az)) return BFPFFT_ERR_INVALID_ARG;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
   bfp::RowArgs a;
   int st = row_args(l, &a);
   if (st != BFPFFT_OK) return st;
-  if (fault("launch")) return BFPFFT_ERR_CUDA;
   cudaError_t e = bfp::launch_autofocus(l, rc_dtype == BFPFFT_F16_BFP, rc, phi, static_cast<const float2*>(ha),
                                         a.tw, n_rg, static_cast<double*>(stats_out), grad_out, workspace,
                                         device_memory(rc), static_cast<cudaStream_t>(stream));

@@ -13,6 +13,8 @@
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
+#include <cfloat>
+
 namespace bfp {
 
 struct E4M3 {};
@@ -27,6 +29,8 @@ template <> struct Storage<float2> {
   __device__ __forceinline__ static float2 load(const float2* p) { return __ldcs(p); }
   __device__ __forceinline__ static void store(float2* p, float2 v) { __stcs(p, v); }
   __device__ __forceinline__ static float2 load_smem(const float2* p) { return *p; }
+  // True when the stored value is finite (NaN fails both comparisons).
+  __device__ __forceinline__ static bool finite(float2 v) { return fabsf(v.x) <= FLT_MAX && fabsf(v.y) <= FLT_MAX; }
 };
 
 template <> struct Storage<__half2> {
@@ -40,6 +44,8 @@ template <> struct Storage<__half2> {
     __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&h));
   }
   __device__ __forceinline__ static float2 load_smem(const __half2* p) { return __half22float2(*p); }
+  // Round-to-nearest-even turns every magnitude >= 65520 into +-Inf.
+  __device__ __forceinline__ static bool finite(float2 v) { return fabsf(v.x) < 65520.f && fabsf(v.y) < 65520.f; }
 };
 
 template <> struct Storage<Fp8x2<E4M3>> {
@@ -52,6 +58,8 @@ template <> struct Storage<Fp8x2<E4M3>> {
     p->bits = __nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E4M3);
   }
   __device__ __forceinline__ static float2 load_smem(const Fp8x2<E4M3>* p) { return load(p); }
+  // Satfinite stores turn +-Inf into the largest finite value; NaN stays NaN.
+  __device__ __forceinline__ static bool finite(float2 v) { return v.x == v.x && v.y == v.y; }
 };
 
 template <> struct Storage<Fp8x2<E5M2>> {
@@ -64,6 +72,8 @@ template <> struct Storage<Fp8x2<E5M2>> {
     p->bits = __nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E5M2);
   }
   __device__ __forceinline__ static float2 load_smem(const Fp8x2<E5M2>* p) { return load(p); }
+  // Satfinite stores turn +-Inf into the largest finite value; NaN stays NaN.
+  __device__ __forceinline__ static bool finite(float2 v) { return v.x == v.x && v.y == v.y; }
 };
 
 // Eight consecutive complex values (one 8-line segment of a corner-turned

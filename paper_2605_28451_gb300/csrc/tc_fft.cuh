@@ -183,6 +183,9 @@ __device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsign
       if (MODE == kInverse) y = cconj(y);
       Storage<TS>::store(out + 256 * q, y);
     }
+    check_finite<Storage<TS>, 16>(a.finite_flag, [&](int m) {
+      return make_float2(__uint_as_float(d[2 * m]), __uint_as_float(d[2 * m + 1]));
+    });
   }
   fence_before();
   return true;

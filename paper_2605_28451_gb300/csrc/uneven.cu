@@ -29,14 +29,17 @@ constexpr int kCta = 256;
 constexpr int kClusterCtas = 16;
 constexpr int kSlab = 4096;     // points of one line per CTA (N >= 4096)
 
+// Returns false when a bounded wait of a four-step line expired (the CTA
+// then stops working, see uneven_kernel); `pending` as in fourstep_line.
 template <class TS, int MODE, bool SCALED, int LOG2N>
-__device__ __noinline__ void run_task(const UnevenArgs& a, const UnevenTask& tk, int rank, float2* smem,
-                                      uint64_t* bar, uint32_t& phase) {
+__device__ __noinline__ bool run_task(const UnevenArgs& a, const UnevenTask& tk, int rank, float2* smem,
+                                      uint64_t* bar, uint32_t& phase, int& pending) {
   constexpr int N = 1 << LOG2N;
   constexpr int P = kPointsPerThread, T = N / P;
   RowArgs ra{};
   ra.tw = a.tw[LOG2N];
   ra.status = a.status;
+  ra.finite_flag = a.finite_flag;
   const int s = (LOG2N + 1) / 2;                        // FP8 block exponent
   ra.in_scale = SCALED && MODE == kInverse ? float(1 << s) : 1.f;
   ra.out_scale = SCALED && MODE == kForward ? 1.f / float(1 << s) : 1.f;
@@ -61,7 +64,9 @@ __device__ __noinline__ void run_task(const UnevenArgs& a, const UnevenTask& tk,
       TS* out = static_cast<TS*>(a.out) + off + t;
 #pragma unroll
       for (int m = 0; m < P; ++m) Storage<TS>::store(out + T * m, v[m]);
+      check_finite<Storage<TS>, P>(a.finite_flag, [&](int m) { return v[m]; });
     }
+    return true;
   } else {
     constexpr int C = N / kSlab;                         // CTAs per line
     const int idx = rank / C;                            // line within the task
@@ -70,8 +75,9 @@ __device__ __noinline__ void run_task(const UnevenArgs& a, const UnevenTask& tk,
     const long long off = active ? a.line_off[tk.first + idx] : 0;
     ra.tw_line = a.tw[12];
     ra.tw_4step = a.tw4[LOG2N];
-    fourstep_line<C, TS, MODE, SCALED>(ra, static_cast<const TS*>(a.in) + off, static_cast<TS*>(a.out) + off,
-                                       smem, bar, bar + 1, phase, rank - base, base, active);
+    return fourstep_line<C, TS, MODE, SCALED>(ra, static_cast<const TS*>(a.in) + off,
+                                              static_cast<TS*>(a.out) + off, smem, bar, bar + 1, phase, pending,
+                                              rank - base, base, active);
   }
 }
 
@@ -119,27 +125,40 @@ __global__ void __launch_bounds__(kCta, uneven_smem_bytes<TS>() * 4 <= 220 * 102
   cluster_arrive_relaxed();
   cluster_wait_acquire();
   uint32_t phase = 0;
+  // A bounded wait that expired (recorded in a.status) puts this CTA in abort
+  // mode: it stops loading, sending and waiting, but walks the rest of the
+  // task list so that it passes exactly the cluster barriers its peers pass
+  // (the barrier decisions below depend on the task list only).  A peer that
+  // waits for data this CTA no longer sends expires once (one bound) and
+  // aborts too, so a failing launch ends after a few bounds instead of one
+  // bound per remaining task.
+  bool aborted = false;
+  int pending = 0;
   // Tasks hold 65,536 points each, so a static round-robin over the clusters
   // balances the work; no counter or broadcast is needed.
   if (a.prefetch) prefetch_task<TS>(a, cluster_id, rank);
   for (int task = cluster_id; task < a.num_tasks; task += clusters) {
-    if (a.prefetch) prefetch_task<TS>(a, task + clusters, rank);
     const UnevenTask tk = a.tasks[task];
-    switch (tk.log2n) {
-      case 4: run_task<TS, MODE, SCALED, 4>(a, tk, rank, smem_u, bar, phase); break;
-      case 5: run_task<TS, MODE, SCALED, 5>(a, tk, rank, smem_u, bar, phase); break;
-      case 6: run_task<TS, MODE, SCALED, 6>(a, tk, rank, smem_u, bar, phase); break;
-      case 7: run_task<TS, MODE, SCALED, 7>(a, tk, rank, smem_u, bar, phase); break;
-      case 8: run_task<TS, MODE, SCALED, 8>(a, tk, rank, smem_u, bar, phase); break;
-      case 9: run_task<TS, MODE, SCALED, 9>(a, tk, rank, smem_u, bar, phase); break;
-      case 10: run_task<TS, MODE, SCALED, 10>(a, tk, rank, smem_u, bar, phase); break;
-      case 11: run_task<TS, MODE, SCALED, 11>(a, tk, rank, smem_u, bar, phase); break;
-      case 12: run_task<TS, MODE, SCALED, 12>(a, tk, rank, smem_u, bar, phase); break;
-      case 13: run_task<TS, MODE, SCALED, 13>(a, tk, rank, smem_u, bar, phase); break;
-      case 14: run_task<TS, MODE, SCALED, 14>(a, tk, rank, smem_u, bar, phase); break;
-      case 15: run_task<TS, MODE, SCALED, 15>(a, tk, rank, smem_u, bar, phase); break;
-      case 16: run_task<TS, MODE, SCALED, 16>(a, tk, rank, smem_u, bar, phase); break;
-      default: break;
+    if (!aborted) {
+      if (a.prefetch) prefetch_task<TS>(a, task + clusters, rank);
+      bool ok = true;
+      switch (tk.log2n) {
+        case 4: ok = run_task<TS, MODE, SCALED, 4>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 5: ok = run_task<TS, MODE, SCALED, 5>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 6: ok = run_task<TS, MODE, SCALED, 6>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 7: ok = run_task<TS, MODE, SCALED, 7>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 8: ok = run_task<TS, MODE, SCALED, 8>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 9: ok = run_task<TS, MODE, SCALED, 9>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 10: ok = run_task<TS, MODE, SCALED, 10>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 11: ok = run_task<TS, MODE, SCALED, 11>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 12: ok = run_task<TS, MODE, SCALED, 12>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 13: ok = run_task<TS, MODE, SCALED, 13>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 14: ok = run_task<TS, MODE, SCALED, 14>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 15: ok = run_task<TS, MODE, SCALED, 15>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 16: ok = run_task<TS, MODE, SCALED, 16>(a, tk, rank, smem_u, bar, phase, pending); break;
+        default: break;
+      }
+      aborted = !ok;
     }
     // A peer may write into this CTA's shared memory in the next task only
     // after this CTA is done with it.  Between two four-step tasks of the
@@ -155,6 +174,10 @@ __global__ void __launch_bounds__(kCta, uneven_smem_bytes<TS>() * 4 <= 220 * 102
     const bool chained = tk.log2n >= 15 && next < a.num_tasks && a.tasks[next].log2n == tk.log2n;
     if (!chained) cluster_barrier_relaxed();
   }
+  // The last task of every cluster ends with a barrier, so every peer has
+  // issued all its stores by now; an aborted CTA still waits (bounded) for
+  // those owed to its pending phases before its shared memory goes away.
+  if (aborted) fourstep_drain(&bar[0], &bar[1], phase, pending);
 }
 
 template <class TS, int MODE, bool SCALED>

@@ -25,6 +25,7 @@ struct UnevenArgs {
   int* counter;                  // task counter (reset before every launch)
   int* status;
   int prefetch;                  // nonzero: prefetch each CTA's lines of the next task into L2
+  int* finite_flag;              // non-null: record non-finite outputs here (BFPFFT_CHECK_FINITE)
 };
 
 // Row and output buffers of the longest four-step line (N1 = 16), for the

@@ -85,3 +85,55 @@ def test_fault_injection_plan(lib, monkeypatch):
     with pytest.raises(B.BfpfftError) as e:
         B.bfpfft_plan_create(4096, 4, B.F16_BFP, B.FORWARD)
     assert e.value.status == B.ERR_CUDA
+
+
+def test_fault_injection_alloc(lib, monkeypatch):
+    """BFPFFT_FAULT=alloc: plan creation reports OOM before touching a GPU."""
+    import numpy as np
+    monkeypatch.setenv("BFPFFT_FAULT", "alloc")
+    with pytest.raises(B.BfpfftError) as e:
+        B.bfpfft_plan_create(4096, 4, B.F16_BFP, B.FORWARD)
+    assert e.value.status == B.ERR_OOM
+    with pytest.raises(B.BfpfftError) as e:
+        B.bfpfft_plan_create_many(np.array([256, 4096]), np.array([0, 256]), B.F16_BFP, B.FORWARD)
+    assert e.value.status == B.ERR_OOM
+
+
+def test_fault_injection_launch(lib, monkeypatch):
+    """BFPFFT_FAULT=launch: every plan-less call fails its launch with ERR_CUDA after
+    checking its arguments and before any device work (addresses 16 are fake)."""
+    monkeypatch.setenv("BFPFFT_FAULT", "launch")
+    assert lib.sar_range_compress(16, 0, 16, 1, 16, 8, 4096, 0, None) == B.ERR_CUDA
+    assert lib.sar_range_compress(16, 0, 16, 1, 16, 8, 4096, 1, None) == B.ERR_CUDA
+    assert lib.sar_azimuth_compress(16, 1, 1, 16, 1, 16, 4096, 8, None) == B.ERR_CUDA
+    assert lib.sar_make_filter(16, 4096, 1, 32, None) == B.ERR_CUDA
+    ws = 1 << 26
+    assert lib.sar_autofocus_grad(16, 1, 16, 16, 4096, 8, 16, 16, 16, ws, None) == B.ERR_CUDA
+    assert lib.sar_point_target_metrics(16, 1, 64, 64, 16, 1, 8, 16, 16, 1 << 30, None) == B.ERR_CUDA
+    assert lib.bfp_sqnr_sums(16, 0, 16, 1, 100, 16, 16, 1 << 20, None) == B.ERR_CUDA
+    # argument errors still come first
+    assert lib.sar_range_compress(None, 0, 16, 1, 16, 8, 4096, 0, None) == B.ERR_INVALID_ARG
+    assert lib.sar_range_compress(16, 0, 16, 1, 16, 8, 4095, 0, None) == B.ERR_UNSUPPORTED
+
+
+def test_status_and_flag_argument_checks(lib):
+    import ctypes
+    st = ctypes.c_int(-1)
+    assert lib.bfpfft_plan_status(None, ctypes.byref(st)) == B.ERR_INVALID_ARG
+    assert lib.bfpfft_plan_set_flags(None, B.CHECK_FINITE) == B.ERR_INVALID_ARG
+    assert lib.bfpfft_plan_selftest_wait(None, None) == B.ERR_INVALID_ARG
+    assert lib.bfpfft_device_status(None) == B.ERR_INVALID_ARG
+
+
+def test_adaptive_argument_checks(lib):
+    """Adaptive exponents: lengths above 16384 and bad dtypes are refused before any device work."""
+    with pytest.raises(B.BfpfftError) as e:
+        B.bfpfft_plan_create(32768, 4, B.F16_ADAPTIVE, B.FORWARD)
+    assert e.value.status == B.ERR_UNSUPPORTED
+    assert lib.bfp_spectral_adaptive(16, B.F32, None, 16, 16, 16, 32768, 4, None) == B.ERR_UNSUPPORTED
+    assert lib.bfp_spectral_adaptive(16, B.E4M3_BFP, None, 16, 16, 16, 4096, 4, None) == B.ERR_UNSUPPORTED
+    assert lib.bfp_spectral_adaptive(16, B.F32, 16, 16, 16, 16, 4096, 4, None) == B.ERR_INVALID_ARG
+    assert lib.bfp_spectral_adaptive(16, B.F32, None, 16, 16, 16, 4096, 0, None) == B.OK
+    assert lib.bfp_spectral_adaptive(16, B.F32, None, 16, 16, None, 4096, 4, None) == B.ERR_INVALID_ARG
+    assert lib.bfp_spectral_adaptive(17, B.F32, None, 16, 16, 16, 4096, 4, None) == B.ERR_MISALIGNED
+    assert lib.bfpfft_exec_adaptive(None, 16, None, 16, 16, None) == B.ERR_INVALID_ARG

@@ -59,6 +59,79 @@ def case():
     return make_case(1024, 96, 512, quad=2.0)
 
 
+def make_sized_case(n_az, n_rg, seed=5):
+    """A case for any azimuth length: aperture min(1024, n_az / 2), three targets
+    placed by fractions of the scene, quadratic error of 2 rad."""
+    ap = min(1024, n_az // 2)
+    targets = [(n_az // 2, n_rg // 3, 1.0), (n_az // 2 + n_az // 10, (2 * n_rg) // 3, 0.5),
+               (n_az // 2 - n_az // 7, n_rg // 2, 0.3)]
+    rc = synth.range_compressed_scene(n_az, n_rg, ap, targets)
+    ha = sar.matched_filter(synth.centred_reference(synth.azimuth_chirp(ap), n_az), True)
+    eps = synth.phase_error(n_az, seed=seed, quad_rad=2.0)
+    return targets, rc * np.exp(1j * eps)[:, None], ha, eps
+
+
+@pytest.mark.parametrize("n_az", [256, 4096, 8192])
+def test_fp32_gradient_every_kernel_length(n_az):
+    """The kernels are specialised per azimuth length (256 .. 8192): FP32 storage
+    against the oracle's analytic adjoint (relative L2 <= 1e-4) and FP64 central
+    differences on 16 pulses drawn with default_rng(4)."""
+    _, u, ha, eps = make_sized_case(n_az, 64)
+    phi = 0.3 * eps.astype(np.float32).astype(np.float64)
+    stats, g, stored = gpu_entropy_grad(u, ha, phi, B.F32)
+    ha32 = storage_round(ha, B.F32)
+    e_ref, g_ref = AF.entropy_and_grad(stored, phi, ha32)
+    assert stats[2] == pytest.approx(e_ref, rel=1e-5)
+    assert metrics.rel_l2(g_ref, g) <= 1e-4
+    pulses = np.random.default_rng(4).choice(n_az, 16, replace=False)
+    fd = AF.central_difference(stored, phi, ha32, pulses, h=1e-4)
+    assert np.linalg.norm(g_ref[pulses] - fd) <= 1e-6 * np.linalg.norm(fd)
+    assert np.linalg.norm(g[pulses] - fd) <= 2e-4 * np.linalg.norm(fd)
+
+
+@pytest.mark.parametrize("n_az", [256, 4096, 8192])
+def test_fp16_bfp_gradient_every_kernel_length(n_az):
+    _, u, ha, eps = make_sized_case(n_az, 64)
+    phi = 0.3 * eps.astype(np.float32).astype(np.float64)
+    stats, g, _ = gpu_entropy_grad(u, ha, phi, B.F16_BFP)
+    e_ref, g_ref = AF.entropy_and_grad(u, phi, storage_round(ha, B.F32))
+    assert stats[2] == pytest.approx(e_ref, rel=1e-3)
+    assert metrics.rel_l2(g_ref, g) <= 3e-2
+    assert np.dot(g, g_ref) / (np.linalg.norm(g) * np.linalg.norm(g_ref)) >= 0.999
+
+
+@pytest.fixture(scope="module")
+def config5():
+    """Config 5: the 4096 x 4096 point-target scene of config 3, range-compressed
+    once (FP64 oracle), with the injected per-pulse phase error (a 4 pi quadratic
+    plus N(0, 0.3^2), default_rng(5))."""
+    n = 4096
+    sc = synth.point_target_scene(n, n)
+    hr = storage_round(sar.matched_filter(storage_round(sc.ref_range, B.F32), False), B.F32)
+    ha = storage_round(sar.matched_filter(storage_round(sc.ref_azimuth, B.F32), True), B.F32)
+    rc = sar.range_compress(storage_round(sc.raw, B.F32), hr)
+    eps = synth.phase_error(n)
+    u = rc * np.exp(1j * eps)[:, None]
+    return sc, u, ha, eps
+
+
+@pytest.mark.parametrize("dtype", [B.F16_BFP, B.F32])
+def test_config5_gradient_at_full_size(config5, dtype):
+    """The 4096 x 4096 kernel specialisation the bench times, against one
+    evaluation of the oracle's analytic adjoint on the stored data at phi = 0."""
+    _, u, ha, _ = config5
+    phi = np.zeros(u.shape[0])
+    stats, g, stored = gpu_entropy_grad(u, ha, phi, dtype)
+    e_ref, g_ref = AF.entropy_and_grad(stored, phi, ha)
+    if dtype == B.F32:
+        assert stats[2] == pytest.approx(e_ref, rel=1e-5)
+        assert metrics.rel_l2(g_ref, g) <= 1e-4
+    else:
+        assert stats[2] == pytest.approx(e_ref, rel=1e-3)
+        assert metrics.rel_l2(g_ref, g) <= 3e-2
+        assert np.dot(g, g_ref) / (np.linalg.norm(g) * np.linalg.norm(g_ref)) >= 0.999
+
+
 @pytest.mark.parametrize("n_rg", [96, 5])
 def test_fp32_entropy_and_gradient(case, n_rg):
     _, u, ha, eps = case
