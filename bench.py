@@ -219,6 +219,7 @@ def run_ours(args):
         torch.cuda.synchronize()
     fwd_ms = [e[0].elapsed_time(e[1]) for e in events]
     inv_ms = [e[1].elapsed_time(e[2]) for e in events]
+    step_ms = [e[0].elapsed_time(e[2]) for e in events]
     t_ms = _max_over_ranks(t_start.elapsed_time(t_end) / args.steps, dist, dev)
     flops_step = 2.0 * FLOPS_PER_TRANSFORM * batch
     value = _job_value(world, flops_step, t_ms)
@@ -292,6 +293,12 @@ def run_ours(args):
     gflops_small = 2.0 * FLOPS_PER_TRANSFORM * 256 / (t_small * 1e-3) / 1e9
     del flush
 
+    # ---- precision modes and adaptive exponents on the same workload ------------------
+    modes = _bench_precision_modes(B, torch, dev, stream, x16, flops_step, k32)
+
+    # ---- batch sweep of the FP16-BFP transform (Table II's batch 256 up to 2 GiB) -----
+    sweep = _bench_batch_sweep(B, torch, dev, stream)
+
     # ---- SAR: range compression 1024 x 4096 and the 4096 x 4096 image ---------------
     sar = _bench_sar(B, torch, dev, stream)
 
@@ -327,11 +334,7 @@ def run_ours(args):
             "vs_baseline": None,
             "dtype": "f16 storage, f32 arithmetic",
             "data": "synthetic (re, im ~ N(0,1), seeded)",
-            "config": {
-                "workload": f"forward + 1/N-shifted inverse FFT, N={N}, batch {batch} per GPU, FP16-BFP (half2)",
-                "l2": "inputs 1 GiB > L2, no flush needed",
-                "parallelism": f"replicas x{world}",
-            },
+            "config": _config(batch, world),
             "roofline": {
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -347,6 +350,10 @@ def run_ours(args):
             "fp16_over_fp32": round(value / world / gflops32, 3),
             "inverse_launch_ms": round(inv_avg, 5),
             "table2_batch256_l2_flushed": {"gflops": round(gflops_small, 1), "ms_median": round(t_small, 5)},
+            "precision_modes": modes,
+            "batch_sweep": sweep,
+            "ms_per_step_median": round(statistics.median(step_ms), 4),
+            "gflops_at_median_step": round(_job_value(world, flops_step, statistics.median(step_ms)), 1),
             "sar": sar,
             "autofocus_4096x4096": autofocus,
             "uneven_20000": uneven,
@@ -358,6 +365,127 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def _bench_batch_sweep(B, torch, dev, stream, batches=(256, 4096, 32768, 131072), steps: int = 30):
+    """FP16-BFP forward + shifted inverse at N = 4096 for several batches:
+    median of `steps` steps after 5 warm-ups, L2 flushed between steps when
+    the input is smaller than 512 MiB (the largest batch moves 2 GiB each way)."""
+    peak, _ = _peaks()
+    out = {}
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for batch in batches:
+        g = torch.Generator(device=dev).manual_seed(batch)
+        x = torch.randn((batch, N, 2), device=dev, generator=g).to(torch.float16)
+        y, z = torch.empty_like(x), torch.empty_like(x)
+        pf = B.bfpfft_plan_create(N, batch, B.F16_BFP, B.FORWARD)
+        pi = B.bfpfft_plan_create(N, batch, B.F16_BFP, B.INVERSE)
+        small = x.numel() * x.element_size() < 512 * 1024 * 1024
+        fw, tot = [], []
+        for i in range(steps + 5):
+            if small:
+                flush.fill_(i & 0xFF)
+            e[0].record(stream)
+            B.bfpfft_exec(pf, x, y, stream)
+            e[1].record(stream)
+            B.bfpfft_exec(pi, y, z, stream)
+            e[2].record(stream)
+            e[2].synchronize()
+            if i >= 5:
+                fw.append(e[0].elapsed_time(e[1]))
+                tot.append(e[0].elapsed_time(e[2]))
+        t, t_f = statistics.median(tot), statistics.median(fw)
+        gbs = 8.0 * N * batch / (t_f * 1e-3) / 1e9
+        out[str(batch)] = {"gflops": round(2.0 * FLOPS_PER_TRANSFORM * batch / (t * 1e-3) / 1e9, 1),
+                           "ms_median": round(t, 5), "forward_gbs": round(gbs, 1),
+                           "forward_frac_of_measured_hbm": round(gbs / peak, 4), "l2_flushed": small}
+        del x, y, z, pf, pi
+    del flush
+    return out
+
+
+def _sqnr_vs(B, torch, ref_c64, test, test_dtype, count, stream):
+    """Aligned SQNR (dB) of `test` against a complex64 reference, by the library's FP64 sums."""
+    ws_bytes = B.bfp_sqnr_workspace_bytes()
+    ws = torch.empty(ws_bytes // 8, dtype=torch.float64, device=ref_c64.device)
+    sums = torch.empty(8, dtype=torch.float64, device=ref_c64.device)
+    B.bfp_sqnr_sums(ref_c64, B.F32, test, test_dtype, count, sums, ws, ws_bytes, stream)
+    return round(B.sqnr_from_sums(sums[:5].cpu().tolist())["aligned_db"], 2)
+
+
+def _bench_precision_modes(B, torch, dev, stream, x16, flops_step, steps):
+    """The paper's precision modes on the headline workload (N = 4096, batch of
+    x16, forward + shifted inverse): pure FP16 arithmetic, FP16 operands with
+    FP32 accumulation (tensor-core DFT blocks), bfloat16, and FP16 with
+    adaptive per-line exponents.  Each: GFLOPS, the forward launch's GB/s and
+    fraction of the measured HBM copy bandwidth, and the forward output's
+    SQNR against the FP32-storage path on the first 256 lines."""
+    batch = x16.shape[0]
+    peak, _ = _peaks()
+    ref_x = torch.view_as_complex(x16[:256].float().contiguous())
+    ref_y = torch.empty_like(ref_x)
+    B.bfpfft_exec(B.bfpfft_plan_create(N, 256, B.F32, B.FORWARD), ref_x, ref_y, stream)
+    out = {}
+
+    def timed(run_fwd, run_inv):
+        for _ in range(3):
+            run_fwd()
+            run_inv()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fw, tot = [], []
+        for _ in range(steps):
+            e[0].record(stream)
+            run_fwd()
+            e[1].record(stream)
+            run_inv()
+            e[2].record(stream)
+            e[2].synchronize()
+            fw.append(e[0].elapsed_time(e[1]))
+            tot.append(e[0].elapsed_time(e[2]))
+        return statistics.median(fw), statistics.median(tot)
+
+    cases = (("pure_fp16", B.F16_BFP, B.ARITH_F16, x16),
+             ("fp16_operands_fp32_accumulate_tensor_cores", B.F16_BFP, B.ARITH_F16_MUL_F32_ACC, x16),
+             ("bf16", B.BF16, B.ARITH_BF16, None))
+    for name, dtype, arith, xin in cases:
+        if xin is None:
+            xin = x16.to(torch.bfloat16)
+        y, z = torch.empty_like(xin), torch.empty_like(xin)
+        pf = B.bfpfft_plan_create(N, batch, dtype, B.FORWARD)
+        pi = B.bfpfft_plan_create(N, batch, dtype, B.INVERSE)
+        B.bfpfft_plan_set_arith(pf, arith)
+        B.bfpfft_plan_set_arith(pi, arith)
+        t_f, t = timed(lambda: B.bfpfft_exec(pf, xin, y, stream), lambda: B.bfpfft_exec(pi, y, z, stream))
+        gbs = 8.0 * N * batch / (t_f * 1e-3) / 1e9
+        y32 = torch.view_as_complex(y[:256].float().contiguous())
+        out[name] = {"gflops": round(flops_step / (t * 1e-3) / 1e9, 1), "ms_per_step": round(t, 4),
+                     "forward_launch_ms": round(t_f, 5), "forward_gbs": round(gbs, 1),
+                     "forward_frac_of_measured_hbm": round(gbs / peak, 4),
+                     "sqnr_vs_fp32_db": _sqnr_vs(B, torch, ref_y, y32, B.F32, 256 * N, stream)}
+        del y, z
+    # adaptive exponents: the same input, and the same input scaled by 2^20
+    e_in = torch.zeros(batch, dtype=torch.int32, device=dev)
+    e_mid = torch.empty_like(e_in)
+    e_out = torch.empty_like(e_in)
+    y, z = torch.empty_like(x16), torch.empty_like(x16)
+    pf = B.bfpfft_plan_create(N, batch, B.F16_ADAPTIVE, B.FORWARD)
+    pi = B.bfpfft_plan_create(N, batch, B.F16_ADAPTIVE, B.INVERSE)
+    t_f, t = timed(lambda: B.bfpfft_exec_adaptive(pf, x16, e_in, y, e_mid, stream),
+                   lambda: B.bfpfft_exec_adaptive(pi, y, e_mid, z, e_out, stream))
+    gbs = 8.0 * N * batch / (t_f * 1e-3) / 1e9
+    e20 = torch.full_like(e_in, 20)
+    B.bfpfft_exec_adaptive(pf, x16, e20, y, e_mid, stream)
+    vals = (torch.view_as_complex(y[:256].float().contiguous())
+            * torch.pow(2.0, e_mid[:256].float() - 20.0)[:, None])
+    out["adaptive_exponents_fp16"] = {
+        "gflops": round(flops_step / (t * 1e-3) / 1e9, 1), "ms_per_step": round(t, 4),
+        "forward_launch_ms": round(t_f, 5), "forward_gbs": round(gbs, 1),
+        "forward_frac_of_measured_hbm": round(gbs / peak, 4),
+        "input_scaled_2^20_finite": bool(torch.isfinite(y).all().item()),
+        "sqnr_vs_fp32_db_input_scaled_2^20": _sqnr_vs(B, torch, ref_y, vals.to(torch.complex64), B.F32, 256 * N,
+                                                       stream)}
+    return out
 
 
 def _bench_sar(B, torch, dev, stream):
@@ -602,63 +730,120 @@ def _bench_e2e(B, torch, dev, stream, x16, fwd, inv, flops_step, args, chunks: i
             "pipeline": f"{chunks} chunks over copy-in / transform / copy-out streams"}
 
 
-def _cpu_baseline(seconds: float = 10.0):
-    """The FP64 oracle as it stands (numpy, one thread), timed on a bounded
-    sample of the workload: forward + inverse of as many N = 4096 lines as
-    fit in `seconds`, starting from 8 lines and doubling."""
-    import numpy as np
+# The oracle's timing sample: lines of N = 4096 (the headline line length),
+# forward + inverse, the same per-line work as one GPU step.
+ORACLE_LINES = 64
 
+
+def _cpu_model() -> str:
+    """The host CPU's model name (x86 'model name', Arm 'CPU part' / lscpu)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_lines(lines: int, seed: int = 0) -> float:
+    """Time one forward + inverse of `lines` oracle lines (seconds).  Runs in
+    a worker process of the spawned pool, or in the caller."""
     from oracle import fft as F
     from paper_2605_28451_gb300 import synth
-    lines = 8
-    while True:
-        x = synth.complex_gaussian(lines, N, seed=0)
-        t0 = time.perf_counter()
-        F.ifft(F.fft(x))
-        dt = time.perf_counter() - t0
-        if dt >= seconds / 4 or lines >= 4096:
-            break
-        lines *= 2
-    reps = max(1, int(seconds / max(dt, 1e-3)))
+    x = synth.complex_gaussian(lines, N, seed=seed)
     t0 = time.perf_counter()
-    for _ in range(reps):
-        F.ifft(F.fft(x))
-    dt = (time.perf_counter() - t0) / reps
-    gflops = 2.0 * FLOPS_PER_TRANSFORM * lines / dt / 1e9
-    del np
-    return {"value": round(gflops, 3), "unit": "GFLOPS", "cores": 1, "kind": "oracle",
-            "sample": f"{lines} lines of N={N}, forward + inverse, {reps} reps, FP64 numpy radix-2"}
+    F.ifft(F.fft(x))
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """The FP64 oracle on every host core: one spawned worker per core, each
+    transforming its own ORACLE_LINES lines (the oracle itself is single-
+    threaded numpy; spawned, not forked, so no CUDA state is inherited)."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        self.cores = os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.pool.map(_oracle_lines, [1] * self.cores)          # imports done in every worker
+
+    def step(self) -> float:
+        """Wall time (s) of one step: every core runs ORACLE_LINES lines."""
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_lines, [ORACLE_LINES] * self.cores)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _cpu_baseline(seconds: float = 10.0):
+    """The FP64 oracle as it stands, on a bounded sample of the workload:
+    ORACLE_LINES lines of N = 4096 forward + inverse per core, repeated for
+    about `seconds` on one core and then on all cores at once."""
+    flops_line = 2.0 * FLOPS_PER_TRANSFORM
+    _oracle_lines(ORACLE_LINES)                                   # warm-up
+    reps, t1, t_end = 0, 0.0, time.perf_counter() + seconds / 2
+    while reps < 2 or time.perf_counter() < t_end:
+        t1 += _oracle_lines(ORACLE_LINES)
+        reps += 1
+    one_core = flops_line * ORACLE_LINES * reps / t1 / 1e9
+    pool = OraclePool()
+    try:
+        ts, t_end = [], time.perf_counter() + seconds / 2
+        while len(ts) < 2 or time.perf_counter() < t_end:
+            ts.append(pool.step())
+    finally:
+        pool.close()
+    all_cores = flops_line * ORACLE_LINES * pool.cores / statistics.median(ts) / 1e9
+    return {"value": round(all_cores, 3), "unit": "GFLOPS", "cores": pool.cores, "kind": "oracle",
+            "sample": f"{ORACLE_LINES} lines of N={N} per core, forward + inverse, FP64 numpy radix-2; "
+                      f"{len(ts)} all-core steps (median), {reps} single-core reps",
+            "single_core_value": round(one_core, 3), "cpu_model": _cpu_model()}
+
+
+def _config(batch: int, world: int) -> dict:
+    """The workload both arms report (the reference arm times a bounded
+    sample of it, described in its cpu_baseline)."""
+    return {"workload": f"forward + 1/N-shifted inverse FFT, N={N}, batch {batch} per GPU, FP16-BFP (half2)",
+            "l2": "inputs 1 GiB > L2, no flush needed", "parallelism": f"replicas x{world}"}
 
 
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
-
-    from oracle import fft as F
-    from paper_2605_28451_gb300 import synth
-    lines = args.ref_lines
-    x = synth.complex_gaussian(lines, N, seed=0)
-    for _ in range(args.warmup):
-        F.ifft(F.fft(x))
-    ts = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        F.ifft(F.fft(x))
-        ts.append(time.perf_counter() - t0)
+    pool = OraclePool()
+    try:
+        for _ in range(args.warmup):
+            pool.step()
+        ts = [pool.step() for _ in range(args.steps)]
+    finally:
+        pool.close()
     t = sum(ts) / len(ts)
-    value = 2.0 * FLOPS_PER_TRANSFORM * lines / t / 1e9
-    sample = f"{lines} lines of N={N} per step (of the {BATCH}-line workload), forward + inverse, FP64 numpy radix-2"
+    value = 2.0 * FLOPS_PER_TRANSFORM * ORACLE_LINES * pool.cores / t / 1e9
+    sample = (f"{ORACLE_LINES} lines of N={N} per core per step on {pool.cores} cores (of the {args.batch}-line "
+              f"workload), forward + inverse, FP64 numpy radix-2")
     print(json.dumps({
         "impl": "reference",
         "metric": "batched FFT GFLOPS (5 N log2 N per transform), FP16-BFP storage, N=4096",
         "value": round(value, 4), "unit": "GFLOPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(t * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (re, im ~ N(0,1), seeded)",
-        "config": {"workload": f"forward + 1/N-shifted inverse FFT, N={N}, batch {BATCH} per GPU, FP16-BFP (half2)",
-                   "parallelism": "host cores"},
-        "cpu_baseline": {"value": round(value, 4), "unit": "GFLOPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "config": _config(args.batch, world),
+        "sample": sample,
+        "cpu_baseline": {"value": round(value, 4), "unit": "GFLOPS", "cores": pool.cores, "kind": "oracle",
+                         "sample": sample, "cpu_model": _cpu_model()},
         "e2e": {"value": round(value, 4), "unit": "GFLOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -671,7 +856,6 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--ref-lines", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -54,8 +54,26 @@ enum bfpfft_dtype {
   BFPFFT_F16_NAIVE = 2,  /* FP16 storage without the shift (Section III-B's failing path) */
   BFPFFT_E4M3_BFP = 3,   /* FP8 E4M3 storage, static block exponents (Section VII) */
   BFPFFT_E5M2_BFP = 4,   /* FP8 E5M2 storage, static block exponents (Section VII) */
-  BFPFFT_F16_ADAPTIVE = 5  /* FP16 mantissas (half2) plus one int32 exponent per line, chosen from
-                              the line's block maximum (Section VIII): bfpfft_exec_adaptive */
+  BFPFFT_F16_ADAPTIVE = 5,  /* FP16 mantissas (half2) plus one int32 exponent per line, chosen from
+                               the line's block maximum (Section VIII): bfpfft_exec_adaptive */
+  BFPFFT_BF16 = 6           /* bfloat16 storage (re, im pairs, 4 B / point) and bfloat16 arithmetic,
+                               with the 1/N shift (Section IV-C); n <= 16384, uniform plans */
+};
+
+/*
+ * Arithmetic of a plan's transforms (bfpfft_plan_set_arith), the precision
+ * modes of Section VI (and Table I's pure FP16, Section IV-C's bfloat16).
+ * The storage dtype is unchanged by the mode.
+ */
+enum bfpfft_arith {
+  BFPFFT_ARITH_F32 = 0,             /* FP32 registers and shared memory (default; FP16 storage + FP32
+                                       compute for the FP16 dtypes) */
+  BFPFFT_ARITH_F16 = 1,             /* pure FP16: every add and multiply in half2, FP16 twiddles, FP16
+                                       shared-memory exchange (F16_BFP / F16_NAIVE, n <= 16384) */
+  BFPFFT_ARITH_F16_MUL_F32_ACC = 2, /* FP16 operands, FP32 accumulation: each radix-16 DFT block on the
+                                       tensor cores (tcgen05.mma kind::f16), twiddles FP32 (F16_BFP,
+                                       n = 4096) */
+  BFPFFT_ARITH_BF16 = 3             /* bfloat16 arithmetic; the one mode of BFPFFT_BF16 plans */
 };
 
 /* Plan flags (bfpfft_plan_set_flags). */
@@ -203,6 +221,18 @@ int bfpfft_plan_status(bfpfft_plan plan, int* status);
 int bfpfft_plan_set_flags(bfpfft_plan plan, int flags);
 
 /*
+ * Select the arithmetic of a uniform plan's transforms (enum bfpfft_arith).
+ * The 16-bit twiddle table a mode needs is built here, so call it before any
+ * stream capture.  A graph captured by bfpfft_exec_graph is captured again.
+ * Results change with the mode within its error budget: pure FP16 rounds every
+ * operation (about 60 dB SQNR at N = 4096 on N(0,1) lines against the ~74 dB
+ * of FP16 storage with FP32 compute); bfloat16 about 18 dB lower than FP16.
+ * Errors: INVALID_ARG (NULL plan, unknown mode), UNSUPPORTED (a mode the
+ * plan's dtype, length or kind does not offer), OOM, CUDA.
+ */
+int bfpfft_plan_set_arith(bfpfft_plan plan, int arith);
+
+/*
  * Failure-detection self-test (not in the paper): enqueue on `stream` one
  * small kernel that arms a device-side barrier for a copy that is never
  * issued and waits for it with the same bounded wait the transform kernels
@@ -325,6 +355,42 @@ int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype,
  */
 int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img, int img_dtype,
                          const void* ha, int64_t n_az, int64_t n_rg, void* stream);
+
+/*
+ * Range-Doppler image with range-cell-migration correction and a
+ * range-dependent azimuth filter (Section VI: the RCMC stage of the
+ * range-Doppler chain).  For the hyperbolic range history sqrt(R^2 + v^2 t^2)
+ * a target at Doppler frequency f sits dR(f) = R (1/D(f) - 1) further out,
+ * D(f) = sqrt(1 - (lambda f / (2 v))^2), and its azimuth chirp has the FM
+ * rate k_a(R) = 2 v^2 / (lambda R PRF^2) cycles per pulse^2.  Steps:
+ *   1. range compression of every azimuth line (as sar_range_compress);
+ *   2. azimuth DFT of every range line: the range-Doppler domain;
+ *   3. SAR_RDA_RCMC: every Doppler row f (signed bin k, f = k PRF / n_az) moved
+ *      back by dR(f, R0) / range_cell cells by an exact band-limited shift
+ *      (DFT along range, linear phase, 1/N shift, inverse);
+ *   4. every range bin r: the filter conj(DFT(ref_r)) of its own reference
+ *      chirp exp(-i pi k_a(R_r) n^2), n in [-L/2, L/2), circularly centred at
+ *      index 0, with R_r = R0 + (r - n_rg/2) range_cell (SAR_RDA_RANGE_DEPENDENT;
+ *      else R_r = R0), divided by its largest magnitude with
+ *      SAR_RDA_PEAK_NORMALISE; times the line; the 1/N-shifted inverse DFT.
+ *   raw       [n_az][n_rg], raw_dtype BFPFFT_F32 or BFPFFT_F16_BFP
+ *   img       [n_az][n_rg], img_dtype BFPFFT_F32 or BFPFFT_F16_BFP (FP16
+ *             requires SAR_RDA_PEAK_NORMALISE: an unnormalised filter lifts a
+ *             unit target's image peak past 65504)
+ *   hr        float2[n_rg], the range filter spectrum
+ *   geometry  host double[5]: range cell (m), PRF (Hz), wavelength (m), speed
+ *             (m/s), slant range of cell n_rg/2 (m)
+ *   aperture  azimuth chirp length L (even, 2 <= L <= n_az)
+ * n_az, n_rg: powers of two in [256, 8192].  Intermediates are stored in the
+ * image's format; scratch (2 n_az n_rg points) comes from the library's
+ * stream-ordered pool, as for the corner turns of the SAR calls.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG (NULL, flags, geometry with
+ * lambda PRF / (4 v) >= 1, aperture), UNSUPPORTED (sizes, dtypes), MISALIGNED,
+ * OOM, CUDA.
+ */
+enum sar_rda_flags { SAR_RDA_RCMC = 1, SAR_RDA_RANGE_DEPENDENT = 2, SAR_RDA_PEAK_NORMALISE = 4 };
+int sar_rda_image(const void* raw, int raw_dtype, void* img, int img_dtype, const void* hr, int64_t n_az,
+                  int64_t n_rg, const double* geometry, int64_t aperture, int flags, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Entropy phase autofocus with a hand-written adjoint.

@@ -213,3 +213,55 @@ def fft_radix16_rounded(x: np.ndarray, op: Hook = None) -> np.ndarray:
         re, im = nre, nim
         ns *= 16
     return re + 1j * im
+
+
+# ---- radix-16 schedule with FP16 operands and FP32 accumulation ---------------
+#
+# Section VI lists an "FP16 multiply / FP32 accumulate" mode.  On a radix-16
+# Stockham schedule whose 16-point DFT blocks are dense 16 x 16 products, the
+# mode reads: every pass takes its 16 inputs as FP16 operands, multiplies them
+# by the DFT-16 coefficients W16^(q r) held in FP16, and sums the (exact)
+# products in FP32; the pass twiddles W_{16 Ns}^{k r} multiply the FP32 sums
+# in FP32 (the two products and the fused sum of a complex multiply, each
+# rounded), and only the next pass's operand rounding returns them to FP16.
+# The output is stored in FP16.  Hooks: ``operand`` (pass inputs), ``coeff``
+# (the DFT-16 coefficients), ``acc`` (the dot-product sums, the twiddle
+# products and the twiddle table), ``store`` (the output).  All None gives
+# the exact DFT.  The order of the FP32 additions inside a dot product is not
+# modelled: the exact sum is rounded once.
+
+
+def fft_radix16_mma(x: np.ndarray, operand: Hook = quant.round_binary16, coeff: Hook = quant.round_binary16,
+                    acc: Hook = quant.round_binary32, store: Hook = quant.round_binary16) -> np.ndarray:
+    """Forward DFT along the last axis (N a power of 16) with FP16 operands and FP32 accumulation."""
+    x = np.asarray(x, dtype=np.complex128)
+    n = x.shape[-1]
+    if n < 16 or 16 ** round(np.log(n) / np.log(16)) != n:
+        raise ValueError(f"length {n} is not a power of 16")
+    qr = np.outer(np.arange(16), np.arange(16)) % 16
+    w16 = np.exp(-2j * np.pi * qr / 16)
+    w16 = _r(coeff, w16.real) + 1j * _r(coeff, w16.imag)
+    vals = x.copy()
+    q = n // 16
+    j = np.arange(q)
+    ns = 1
+    while ns < n:
+        k = j % ns
+        u = np.stack([vals[..., j + q * r] for r in range(16)], axis=-2)      # [..., 16, q]
+        if ns > 1:
+            r = np.arange(16)[:, None]
+            w = np.exp(-2j * np.pi * k[None, :] * r / (16 * ns))
+            wr, wi = _r(acc, w.real), _r(acc, w.imag)
+            ur, ui = u.real, u.imag
+            # fmaf(a.re, w.re, -rn(a.im w.im)), fmaf(a.re, w.im, rn(a.im w.re))
+            u = _r(acc, ur * wr - _r(acc, ui * wi)) + 1j * _r(acc, ur * wi + _r(acc, ui * wr))
+        a = _r(operand, u.real) + 1j * _r(operand, u.imag)
+        y = np.einsum("qr,...rj->...qj", w16, a)
+        y = _r(acc, y.real) + 1j * _r(acc, y.imag)
+        out = np.empty_like(vals)
+        base = (j // ns) * ns * 16 + k
+        for r in range(16):
+            out[..., base + r * ns] = y[..., r, :]
+        vals = out
+        ns *= 16
+    return _r(store, vals.real) + 1j * _r(store, vals.imag)

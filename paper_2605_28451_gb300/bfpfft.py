@@ -30,13 +30,20 @@ F16_NAIVE = 2
 E4M3_BFP = 3
 E5M2_BFP = 4
 F16_ADAPTIVE = 5
+BF16 = 6
+
+# Arithmetic modes (enum bfpfft_arith).
+ARITH_F32 = 0
+ARITH_F16 = 1
+ARITH_F16_MUL_F32_ACC = 2
+ARITH_BF16 = 3
 
 FORWARD = -1
 INVERSE = +1
 
 CHECK_FINITE = 1   # plan flag (enum bfpfft_flags)
 
-BYTES_PER_POINT = {F32: 8, F16_BFP: 4, F16_NAIVE: 4, E4M3_BFP: 2, E5M2_BFP: 2, F16_ADAPTIVE: 4}
+BYTES_PER_POINT = {F32: 8, F16_BFP: 4, F16_NAIVE: 4, E4M3_BFP: 2, E5M2_BFP: 2, F16_ADAPTIVE: 4, BF16: 4}
 
 _c_int64 = ctypes.c_int64
 _vp = ctypes.c_void_p
@@ -57,6 +64,7 @@ SIGNATURES = {
     "bfpfft_plan_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "bfpfft_plan_set_flags": (ctypes.c_int, [_vp, ctypes.c_int]),
     "bfpfft_plan_selftest_wait": (ctypes.c_int, [_vp, _vp]),
+    "bfpfft_plan_set_arith": (ctypes.c_int, [_vp, ctypes.c_int]),
     "bfpfft_exec_adaptive": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "bfp_spectral_adaptive": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _c_int64, _c_int64, _vp]),
     "sar_make_filter": (ctypes.c_int, [_vp, _c_int64, ctypes.c_int, _vp, _vp]),
@@ -64,6 +72,8 @@ SIGNATURES = {
                                           ctypes.c_int, _vp]),
     "sar_azimuth_compress": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _c_int64,
                                             _c_int64, _vp]),
+    "sar_rda_image": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _c_int64, _c_int64, _vp, _c_int64,
+                                     ctypes.c_int, _vp]),
     "sar_autofocus_workspace_bytes": (ctypes.c_size_t, [_c_int64]),
     "sar_autofocus_entropy": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_int64, _c_int64, _vp, _vp,
                                              ctypes.c_size_t, _vp]),
@@ -228,6 +238,10 @@ def bfpfft_plan_set_flags(plan: Plan, flags: int):
     _check(lib().bfpfft_plan_set_flags(plan.handle, int(flags)), "bfpfft_plan_set_flags")
 
 
+def bfpfft_plan_set_arith(plan: Plan, arith: int):
+    _check(lib().bfpfft_plan_set_arith(plan.handle, int(arith)), "bfpfft_plan_set_arith")
+
+
 def bfpfft_plan_selftest_wait(plan: Plan, stream=None):
     _check(lib().bfpfft_plan_selftest_wait(plan.handle, _stream(stream)), "bfpfft_plan_selftest_wait")
 
@@ -258,6 +272,19 @@ def sar_azimuth_compress(rc, rc_dtype: int, rc_layout: int, img, img_dtype: int,
                          stream=None):
     _check(lib().sar_azimuth_compress(_ptr(rc), int(rc_dtype), int(rc_layout), _ptr(img), int(img_dtype), _ptr(ha),
                                       int(n_az), int(n_rg), _stream(stream)), "sar_azimuth_compress")
+
+
+RDA_RCMC = 1
+RDA_RANGE_DEPENDENT = 2
+RDA_PEAK_NORMALISE = 4
+
+
+def sar_rda_image(raw, raw_dtype: int, img, img_dtype: int, hr, n_az: int, n_rg: int, geometry, aperture: int,
+                  flags: int, stream=None):
+    """geometry: (range cell m, PRF Hz, wavelength m, speed m/s, centre slant range m)."""
+    g = (ctypes.c_double * 5)(*[float(v) for v in geometry])
+    _check(lib().sar_rda_image(_ptr(raw), int(raw_dtype), _ptr(img), int(img_dtype), _ptr(hr), int(n_az), int(n_rg),
+                               ctypes.cast(g, _vp), int(aperture), int(flags), _stream(stream)), "sar_rda_image")
 
 
 def bfp_sqnr_workspace_bytes() -> int:

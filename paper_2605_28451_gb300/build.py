@@ -36,6 +36,8 @@ SOURCES = [
     "pt_metrics.cu",
     "transpose.cu",
     "rows_adaptive.cu",
+    "rows16.cu",
+    "rda.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -73,6 +73,7 @@ struct RowArgs {
   int pf_ahead;            // > 0: each CTA prefetches into L2 the lines of the CTA pf_ahead blocks later
   int no_prefetch;         // nonzero: the input is not device memory; no bulk L2 prefetch of it
   int* finite_flag;        // non-null: dense-row stores record non-finite outputs here (BFPFFT_CHECK_FINITE)
+  const void* tw16;        // 16-bit arithmetic rows: pass-major table of (w, -i conj w) 16-bit pairs
   const int* in_exp;       // adaptive exponents: per-line input exponents (value = stored * 2^e), or null
   int* out_exp;            // adaptive exponents: per-line output exponents written by the kernel
 };
@@ -88,7 +89,7 @@ struct RowArgs {
 enum RowVariant : int {
   kRowsTma = 0, kRowsPlain = 1, kRowsPlainPP = 2, kRowsPlainH = 3, kRowsPlainHPP = 4,
   kRowsTmaPP = 5, kRowsTmaH = 6, kRowsTmaHPP = 7, kRowsTc = 8, kRowsPlain4 = 9,
-  kRowsPlainL2 = 10, kRowsPlain4L2 = 11, kRowsPlainHL2 = 12, kRowsPlainH4L2 = 13
+  kRowsPlainL2 = 10, kRowsPlain4L2 = 11, kRowsPlainHL2 = 12, kRowsPlainH4L2 = 13, kRowsPlainHS4L2 = 14
 };
 
 constexpr int kPointsPerThread = 16;
@@ -159,6 +160,22 @@ struct LocalXchH {
   __device__ __forceinline__ void sync_war() const { __syncthreads(); }
 };
 
+// FP16 exchange without padding: the slot of point i is i XOR h(i >> 5) on
+// its low five bits, h(q) = (q & 15) | (bit 3 of q) << 4, which makes the
+// stride-16 stores of the first pass, the 256-apart half-warps of the second
+// and the consecutive loads free of bank conflicts for every length from 256
+// (with 4-byte slots, where one padding slot per 16 leaves a two-way conflict
+// on every consecutive load).
+__host__ __device__ constexpr int swz32(int i) { return i ^ (((i >> 5) & 15) | ((((i >> 5) >> 3) & 1) << 4)); }
+
+struct LocalXchHS {
+  __half2* sm;
+  template <int Q> __device__ __forceinline__ float2 load(int i) const { return __half22float2(sm[swz32(i)]); }
+  template <int Q> __device__ __forceinline__ void store(int i, float2 v) const { sm[swz32(i)] = __float22half2_rn(v); }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ void sync_war() const { __syncthreads(); }
+};
+
 template <int LINE>
 struct LocalXchHPP {
   __half2* sm;
@@ -187,7 +204,7 @@ struct ClusterXch {
 __host__ __device__ constexpr int ilog16(int ns) { return ns <= 1 ? 0 : 1 + ilog16(ns / 16); }
 
 // Exchange variants of the single-CTA row kernels.
-enum XchVariant : int { kXchF32 = 0, kXchF32PP = 1, kXchF16 = 2, kXchF16PP = 3 };
+enum XchVariant : int { kXchF32 = 0, kXchF32PP = 1, kXchF16 = 2, kXchF16PP = 3, kXchF16S = 4 };
 
 template <int N, int XV> struct XchSel;
 template <int N> struct XchSel<N, kXchF32> {
@@ -203,6 +220,10 @@ template <int N> struct XchSel<N, kXchF32PP> {
 template <int N> struct XchSel<N, kXchF16> {
   static constexpr size_t kLineBytes = size_t(pad16(N)) * sizeof(__half2);
   __device__ __forceinline__ static LocalXchH make(unsigned char* p) { return LocalXchH{reinterpret_cast<__half2*>(p)}; }
+};
+template <int N> struct XchSel<N, kXchF16S> {
+  static constexpr size_t kLineBytes = size_t(N) * sizeof(__half2);
+  __device__ __forceinline__ static LocalXchHS make(unsigned char* p) { return LocalXchHS{reinterpret_cast<__half2*>(p)}; }
 };
 template <int N> struct XchSel<N, kXchF16PP> {
   static constexpr size_t kLineBytes = 2 * size_t(pad16(N)) * sizeof(__half2);
@@ -1018,7 +1039,7 @@ cudaError_t launch_fourstep_n(const RowArgs& a, cudaStream_t stream) {
   cfg.gridDim = dim3(unsigned(grid));
   RowArgs b = a;
   b.pf_ahead = (a.variant == kRowsPlainL2 || a.variant == kRowsPlain4L2 || a.variant == kRowsPlainHL2 ||
-                a.variant == kRowsPlainH4L2)
+                a.variant == kRowsPlainH4L2 || a.variant == kRowsPlainHS4L2)
                    ? resident_clusters
                    : 0;
   cudaError_t e = cudaLaunchKernelEx(&cfg, kern, b);
@@ -1158,6 +1179,9 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
         case kRowsPlainH4L2:
           if constexpr (kHalf) return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF16, 4>(a, stream, true);
           break;
+        case kRowsPlainHS4L2:
+          if constexpr (kHalf) return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF16S, 4>(a, stream, true);
+          break;
         case kRowsPlainHPP:
           if constexpr (kHalf) return launch_rows_plain_x<N, TIn, TOut, MODE, NAIVE, kXchF16PP>(a, stream);
           break;
@@ -1196,7 +1220,7 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   RowArgs b = a;
   const bool l2 = a.variant == kRowsPlainL2 || a.variant == kRowsPlain4L2 || a.variant == kRowsPlainHL2 ||
-                  a.variant == kRowsPlainH4L2;
+                  a.variant == kRowsPlainH4L2 || a.variant == kRowsPlainHS4L2;
   b.pf_ahead = (l2 && !TLOAD && a.in_stride == N) ? resident : 0;
   if constexpr (S::C > 1) {
     cudaLaunchConfig_t cfg = {};

@@ -25,6 +25,13 @@ constexpr int kAdaptiveMaxLog2 = 14;
 cudaError_t launch_rows_adaptive_f16(int log2n, int mode, const RowArgs& a, cudaStream_t s);
 cudaError_t launch_spectral_adaptive_c64(int log2n, const RowArgs& a, cudaStream_t s);
 
+// Rows in 16-bit arithmetic (fft_half.cuh), log2n in [4, 14]; a.tw16 holds the
+// table written by launch_twiddles16 (n entries of 8 bytes).
+constexpr int kRows16MaxLog2 = 14;
+cudaError_t launch_rows16_f16(int log2n, int mode, bool naive, const RowArgs& a, cudaStream_t s);
+cudaError_t launch_rows16_bf16(int log2n, int mode, const RowArgs& a, cudaStream_t s);
+cudaError_t launch_twiddles16(void* tw, int n, bool bf16);
+
 // SAR compression lines (Section VI, Fig. 1): float2 or __half2 in and out,
 // optional naive FP16 output, optional cluster corner turn on load / store.
 // Supported log2n: [kSarMinLog2, 14].

@@ -26,6 +26,7 @@
 #include "autofocus.h"
 #include "uneven.h"
 #include "pt_metrics.h"
+#include "rda.h"
 
 namespace {
 
@@ -64,6 +65,7 @@ int without_l2(int variant) {
     case bfp::kRowsTmaPP: return bfp::kRowsPlainPP;
     case bfp::kRowsPlainHL2:
     case bfp::kRowsPlainH4L2:
+    case bfp::kRowsPlainHS4L2:
     case bfp::kRowsTmaH: return bfp::kRowsPlainH;
     case bfp::kRowsTmaHPP: return bfp::kRowsPlainHPP;
     default: return variant;
@@ -153,6 +155,37 @@ int get_twiddles(int log2n, float2** out) {
   return BFPFFT_OK;
 }
 
+// 16-bit twiddle tables (pairs w, wp per entry, 8 bytes) for the rows computed
+// in FP16 or bfloat16 arithmetic, cached like the FP32 tables under keys
+// 200 + log2 n (FP16) and 300 + log2 n (bfloat16).
+int get_twiddles16(int log2n, bool bf16, const void** out) {
+  *out = nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int key = (bf16 ? 300 : 200) + log2n;
+  std::lock_guard<std::mutex> lock(g_tw_mutex);
+  auto it = g_tw.find({dev, key});
+  if (it != g_tw.end()) {
+    *out = it->second;
+    return BFPFFT_OK;
+  }
+  if (fault("alloc")) return BFPFFT_ERR_OOM;
+  const int n = 1 << log2n;
+  float2* tw = nullptr;   // n entries of 8 bytes
+  e = cudaMalloc(&tw, sizeof(float2) * n);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = bfp::launch_twiddles16(tw, n, bf16);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(tw);
+    return cuda_status(e);
+  }
+  g_tw[{dev, key}] = tw;
+  *out = tw;
+  return BFPFFT_OK;
+}
+
 // One device status word per device (bounded device-side waits record
 // BFPFFT_ERR_TIMEOUT here); read and cleared by bfpfft_device_status().
 std::map<int, int*> g_status;
@@ -191,7 +224,7 @@ int rows_variant() {
       {"h16", bfp::kRowsPlainH},      {"h16pp", bfp::kRowsPlainHPP}, {"tma_pp", bfp::kRowsTmaPP},
       {"tma_h16", bfp::kRowsTmaH},    {"tma_h16pp", bfp::kRowsTmaHPP}, {"tc", bfp::kRowsTc},
       {"plain4", bfp::kRowsPlain4},   {"plain_l2", bfp::kRowsPlainL2}, {"plain4_l2", bfp::kRowsPlain4L2},
-      {"h16_l2", bfp::kRowsPlainHL2}, {"h16_4_l2", bfp::kRowsPlainH4L2}};
+      {"h16_l2", bfp::kRowsPlainHL2}, {"h16_4_l2", bfp::kRowsPlainH4L2}, {"h16s_4_l2", bfp::kRowsPlainHS4L2}};
   for (const auto& k : kNames)
     if (std::strcmp(v, k.name) == 0) return k.code;
   return bfp::kRowsTma;
@@ -265,7 +298,7 @@ int row_args(int log2n, bfp::RowArgs* a) {
   return fourstep_tables(log2n, a);
 }
 
-bool valid_dtype(int d) { return d >= BFPFFT_F32 && d <= BFPFFT_F16_ADAPTIVE; }
+bool valid_dtype(int d) { return d >= BFPFFT_F32 && d <= BFPFFT_BF16; }
 
 // H = conj(H) / max_k |H[k]| (or conj only), one CTA.
 __global__ void conj_normalise_kernel(float2* h, int n, int peak_normalise) {
@@ -300,6 +333,7 @@ struct bfpfft_plan_s {
   float2* tw;          // shared table from the per-device cache (not owned)
   int* status;         // the plan's own device status word (owned): timeouts, non-finite outputs
   int flags = 0;       // BFPFFT_CHECK_FINITE
+  int arith = 0;       // enum bfpfft_arith: the arithmetic the transforms run in
   int in_exp;
   int out_exp;
   int variant = -1;     // row-kernel variant chosen by the tuner (-1: library default)
@@ -389,7 +423,7 @@ static int exec_many(bfpfft_plan plan, const void* in, void* out, cudaStream_t s
   a.finite_flag = (plan->flags & BFPFFT_CHECK_FINITE) ? plan->status : nullptr;
   const int variant = rows_variant();   // the _l2 row variants also prefetch the next task into L2
   a.prefetch = (variant == bfp::kRowsPlainL2 || variant == bfp::kRowsPlain4L2 || variant == bfp::kRowsPlainHL2 ||
-                variant == bfp::kRowsPlainH4L2) &&
+                variant == bfp::kRowsPlainH4L2 || variant == bfp::kRowsPlainHS4L2) &&
                device_memory(in);
   const int want = plan->tuned_clusters > 0 ? plan->tuned_clusters : plan->clusters;
   const int clusters = std::min(want, std::max(1, plan->num_tasks));
@@ -470,7 +504,8 @@ size_t storage_bytes(int dtype) {
     case BFPFFT_F32: return 8;
     case BFPFFT_F16_BFP:
     case BFPFFT_F16_NAIVE:
-    case BFPFFT_F16_ADAPTIVE: return 4;
+    case BFPFFT_F16_ADAPTIVE:
+    case BFPFFT_BF16: return 4;
     default: return 2;
   }
 }
@@ -481,7 +516,8 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
   if (plan == nullptr || chosen == nullptr) return BFPFFT_ERR_INVALID_ARG;
   *chosen = -1;
   if (best_ms) *best_ms = 0.f;
-  if (plan->batch == 0 || plan->dtype == BFPFFT_F16_ADAPTIVE) return BFPFFT_OK;   // one kernel, nothing to choose
+  // Adaptive exponents and 16-bit or tensor-core arithmetic run one kernel each: nothing to choose.
+  if (plan->batch == 0 || plan->dtype == BFPFFT_F16_ADAPTIVE || plan->arith != BFPFFT_ARITH_F32) return BFPFFT_OK;
   // Scratch: a bounded sample of the plan's own shape.
   int64_t points = 0;
   int64_t sample_batch = plan->batch;
@@ -527,6 +563,7 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
     candidates = {bfp::kRowsPlain4L2, bfp::kRowsPlainL2, bfp::kRowsPlain, bfp::kRowsPlain4,
                   bfp::kRowsTma,        bfp::kRowsPlainPP, bfp::kRowsTmaPP};
     if (allow_fp16_exchange && (plan->dtype == BFPFFT_F16_BFP || plan->dtype == BFPFFT_F16_NAIVE)) {
+      candidates.push_back(bfp::kRowsPlainHS4L2);
       candidates.push_back(bfp::kRowsPlainHL2);
       candidates.push_back(bfp::kRowsPlainH);
       candidates.push_back(bfp::kRowsPlainHPP);
@@ -622,6 +659,7 @@ int bfpfft_plan_create(bfpfft_plan* out, int64_t n, int64_t batch, int dtype, in
   const int l = log2_exact(n);
   if (l < kMinLog2 || l > kMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
   if (dtype == BFPFFT_F16_ADAPTIVE && l > bfp::kAdaptiveMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
+  if (dtype == BFPFFT_BF16 && l > bfp::kRows16MaxLog2) return BFPFFT_ERR_UNSUPPORTED;
   if (fault("plan")) return BFPFFT_ERR_CUDA;
   if (fault("alloc")) return BFPFFT_ERR_OOM;
   bfpfft_plan p = new (std::nothrow) bfpfft_plan_s();
@@ -633,6 +671,7 @@ int bfpfft_plan_create(bfpfft_plan* out, int64_t n, int64_t batch, int dtype, in
   p->direction = direction;
   p->in_exp = 0;
   p->out_exp = 0;
+  p->arith = dtype == BFPFFT_BF16 ? BFPFFT_ARITH_BF16 : BFPFFT_ARITH_F32;
   if (dtype == BFPFFT_E4M3_BFP || dtype == BFPFFT_E5M2_BFP) {
     const int s = (l + 1) / 2;            // ceil(log2(n) / 2)
     if (direction == BFPFFT_FORWARD) p->out_exp = s; else p->in_exp = s;
@@ -774,6 +813,20 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
     a.variant = without_l2(a.variant);
     a.no_prefetch = 1;
   }
+  if (plan->arith == BFPFFT_ARITH_F16_MUL_F32_ACC) a.variant = bfp::kRowsTc;
+  if (plan->arith == BFPFFT_ARITH_F16 || plan->arith == BFPFFT_ARITH_BF16) {
+    const bool bf16 = plan->arith == BFPFFT_ARITH_BF16;
+    const int st16 = get_twiddles16(plan->log2n, bf16, &a.tw16);
+    if (st16 != BFPFFT_OK) return st16;
+    a.lines = plan->batch;
+    a.in_stride = plan->n;
+    a.out_stride = plan->n;
+    a.no_prefetch = device_memory(in) ? 0 : 1;
+    const int mode16 = plan->direction == BFPFFT_FORWARD ? bfp::kForward : bfp::kInverse;
+    cudaStream_t s16 = static_cast<cudaStream_t>(stream);
+    return cuda_status(bf16 ? bfp::launch_rows16_bf16(plan->log2n, mode16, a, s16)
+                            : bfp::launch_rows16_f16(plan->log2n, mode16, plan->dtype == BFPFFT_F16_NAIVE, a, s16));
+  }
   if (a.variant == bfp::kRowsTc && plan->log2n == 12 && plan->dtype == BFPFFT_F16_BFP) {
     const int stc = get_tc_matrix(const_cast<void**>(&a.tc_b));
     if (stc != BFPFFT_OK) return stc;
@@ -872,6 +925,32 @@ int bfpfft_plan_set_flags(bfpfft_plan plan, int flags) {
   if (plan == nullptr || (flags & ~BFPFFT_CHECK_FINITE) != 0) return BFPFFT_ERR_INVALID_ARG;
   plan->flags = flags;
   if (plan->graph) {   // a captured graph holds the old flags: capture again on the next call
+    cudaGraphExecDestroy(plan->graph);
+    plan->graph = nullptr;
+  }
+  return BFPFFT_OK;
+}
+
+int bfpfft_plan_set_arith(bfpfft_plan plan, int arith) {
+  if (plan == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (arith < BFPFFT_ARITH_F32 || arith > BFPFFT_ARITH_BF16) return BFPFFT_ERR_INVALID_ARG;
+  const bool f16 = plan->dtype == BFPFFT_F16_BFP || plan->dtype == BFPFFT_F16_NAIVE;
+  bool ok = false;
+  switch (arith) {
+    case BFPFFT_ARITH_F32: ok = plan->dtype != BFPFFT_BF16; break;
+    case BFPFFT_ARITH_F16: ok = !plan->many && f16 && plan->log2n <= bfp::kRows16MaxLog2; break;
+    case BFPFFT_ARITH_F16_MUL_F32_ACC: ok = !plan->many && plan->dtype == BFPFFT_F16_BFP && plan->log2n == 12; break;
+    case BFPFFT_ARITH_BF16: ok = plan->dtype == BFPFFT_BF16; break;
+    default: break;
+  }
+  if (!ok) return BFPFFT_ERR_UNSUPPORTED;
+  if (arith == BFPFFT_ARITH_F16 || arith == BFPFFT_ARITH_BF16) {   // the table now, not inside a capture
+    const void* tw16 = nullptr;
+    const int st = get_twiddles16(plan->log2n, arith == BFPFFT_ARITH_BF16, &tw16);
+    if (st != BFPFFT_OK) return st;
+  }
+  plan->arith = arith;
+  if (plan->graph) {
     cudaGraphExecDestroy(plan->graph);
     plan->graph = nullptr;
   }
@@ -1095,6 +1174,98 @@ int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img,
   }
   cudaError_t e = bfp::launch_sar(l, in16, out16, naive, /*tload=*/rc_layout == 0, /*tstore=*/true, a, s);
   return cuda_status(e);
+}
+
+int sar_rda_image(const void* raw, int raw_dtype, void* img, int img_dtype, const void* hr, int64_t n_az,
+                  int64_t n_rg, const double* geometry, int64_t aperture, int flags, void* stream) {
+  if (n_az < 0 || n_rg < 0) return BFPFFT_ERR_INVALID_ARG;
+  const int la = log2_exact(n_az), lr = log2_exact(n_rg);
+  if (la < bfp::kRdaMinLog2 || la > bfp::kRdaMaxLog2 || lr < bfp::kRdaMinLog2 || lr > bfp::kRdaMaxLog2)
+    return BFPFFT_ERR_UNSUPPORTED;
+  if (raw_dtype != BFPFFT_F32 && raw_dtype != BFPFFT_F16_BFP) return BFPFFT_ERR_UNSUPPORTED;
+  if (img_dtype != BFPFFT_F32 && img_dtype != BFPFFT_F16_BFP) return BFPFFT_ERR_UNSUPPORTED;
+  if ((flags & ~(SAR_RDA_RCMC | SAR_RDA_RANGE_DEPENDENT | SAR_RDA_PEAK_NORMALISE)) != 0) return BFPFFT_ERR_INVALID_ARG;
+  if (img_dtype == BFPFFT_F16_BFP && !(flags & SAR_RDA_PEAK_NORMALISE)) return BFPFFT_ERR_UNSUPPORTED;
+  if (geometry == nullptr || aperture < 2 || aperture > n_az || (aperture & 1)) return BFPFFT_ERR_INVALID_ARG;
+  bfp::RdaGeometry geo{geometry[0], geometry[1], geometry[2], geometry[3], geometry[4]};
+  if (!(geo.range_cell_m > 0 && geo.prf_hz > 0 && geo.wavelength_m > 0 && geo.speed_mps > 0 &&
+        geo.centre_range_m > 0.5 * double(n_rg) * geo.range_cell_m))
+    return BFPFFT_ERR_INVALID_ARG;
+  if (geo.wavelength_m * geo.prf_hz / (4.0 * geo.speed_mps) >= 1.0) return BFPFFT_ERR_INVALID_ARG;   // D(f) real
+  if (raw == nullptr || img == nullptr || hr == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (!aligned16(raw) || !aligned16(img) || !aligned16(hr)) return BFPFFT_ERR_MISALIGNED;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
+  const bool f16 = img_dtype == BFPFFT_F16_BFP;
+  const int eb = f16 ? 4 : 8;
+  const size_t bytes = size_t(n_az) * size_t(n_rg) * eb;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bfp::RowArgs ra;
+  int st = row_args(lr, &ra);
+  if (st != BFPFFT_OK) return st;
+  float2* tw_az = nullptr;
+  st = get_twiddles(la, &tw_az);
+  if (st != BFPFFT_OK) return st;
+  void* sa = nullptr;
+  void* sb = nullptr;
+  cudaError_t e = scratch_alloc(&sa, bytes, s);
+  if (e == cudaSuccess) e = scratch_alloc(&sb, bytes, s);
+  // 1. range compression: rows of raw into sb [n_az][n_rg], turned into sa [n_rg][n_az]
+  if (e == cudaSuccess) {
+    ra.in = raw;
+    ra.out = sb;
+    ra.h = static_cast<const float2*>(hr);
+    if (!device_memory(raw)) ra.variant = without_l2(ra.variant);
+    ra.lines = n_az;
+    ra.in_stride = n_rg;
+    ra.out_stride = n_rg;
+    e = bfp::launch_sar(lr, raw_dtype == BFPFFT_F16_BFP, f16, false, false, false, ra, s);
+  }
+  if (e == cudaSuccess) e = bfp::launch_transpose(sb, sa, n_az, n_rg, eb, s);
+  // 2. azimuth DFT of every range line, in place: sa holds S[r][f]
+  if (e == cudaSuccess) {
+    bfp::RowArgs az;
+    st = row_args(la, &az);
+    if (st != BFPFFT_OK) e = cudaErrorUnknown;
+    az.in = sa;
+    az.out = sa;
+    az.lines = n_rg;
+    az.in_stride = n_az;
+    az.out_stride = n_az;
+    if (e == cudaSuccess)
+      e = f16 ? bfp::launch_rows_f16(la, bfp::kForward, false, az, s) : bfp::launch_rows_f32(la, bfp::kForward, az, s);
+  }
+  bfp::RdaArgs r{};
+  r.geo = geo;
+  r.aperture = int(aperture);
+  r.range_dependent = (flags & SAR_RDA_RANGE_DEPENDENT) ? 1 : 0;
+  r.peak_normalise = (flags & SAR_RDA_PEAK_NORMALISE) ? 1 : 0;
+  // 3. RCMC along range, one line per Doppler bin ([f][r] layout)
+  if (e == cudaSuccess && (flags & SAR_RDA_RCMC)) {
+    e = bfp::launch_transpose(sa, sb, n_rg, n_az, eb, s);
+    r.in = sb;
+    r.out = sb;
+    r.tw = ra.tw;
+    r.lines = n_az;
+    r.other = n_az;
+    if (e == cudaSuccess) e = bfp::launch_rcmc_rows(lr, f16, r, s);
+    if (e == cudaSuccess) e = bfp::launch_transpose(sb, sa, n_az, n_rg, eb, s);
+  }
+  // 4. per range bin: its own azimuth filter and the inverse DFT, into sb [n_rg][n_az]
+  if (e == cudaSuccess) {
+    r.in = sa;
+    r.out = sb;
+    r.tw = tw_az;
+    r.lines = n_rg;
+    r.other = n_rg;
+    e = bfp::launch_azimuth_rows(la, f16, r, s);
+  }
+  // 5. turned into the image [n_az][n_rg]
+  if (e == cudaSuccess) e = bfp::launch_transpose(sb, img, n_rg, n_az, eb, s);
+  cudaError_t f = cudaSuccess;
+  if (sb != nullptr) f = cudaFreeAsync(sb, s);
+  if (sa != nullptr && f == cudaSuccess) f = cudaFreeAsync(sa, s);
+  if (st != BFPFFT_OK) return st;
+  return cuda_status(e != cudaSuccess ? e : f);
 }
 
 size_t sar_autofocus_workspace_bytes(int64_t n_az) {

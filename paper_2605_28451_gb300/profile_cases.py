@@ -3,8 +3,11 @@
     python -m paper_2605_28451_gb300.profile_cases <case> [--batch B] [--reps R]
 
 Cases (FP16-BFP unless named otherwise, N = 4096 lines):
-  fft16_fwd, fft16_inv   batched transform, batch B (default 16384: 256 MiB in)
+  fft16_fwd, fft16_inv   batched transform, batch B (default 16384: 256 MiB in); --arith f16 | f16mul | bf16
+                         selects pure FP16, FP16 operands / FP32 accumulation (tensor cores) or bfloat16
   fft32_fwd              the same in FP32 storage
+  adaptive16_fwd         FP16 with adaptive per-line exponents, batch B
+  rda16                  range-Doppler image with RCMC and range-dependent filters, 4096 x 4096, FP16
   range16                range compression of a 1024 x 4096 complex64 scene to FP16, corner-turned
   image16                range + azimuth compression of a 4096 x 4096 scene to an FP16 image
   autofocus16            one autofocus gradient step on 4096 x 4096 FP16 range-compressed data
@@ -30,6 +33,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--n", type=int, default=4096, help="transform length of the fft* cases")
     ap.add_argument("--time", action="store_true", help="print the median ms per rep (CUDA events)")
+    ap.add_argument("--arith", default="f32", choices=["f32", "f16", "f16mul", "bf16"])
     args = ap.parse_args()
     times = []
     build.build()
@@ -38,12 +42,15 @@ def main():
     n = args.n if args.case.startswith("fft") else 4096
     g = torch.Generator(device=dev).manual_seed(0)
     if args.case in ("fft16_fwd", "fft16_inv", "fft32_fwd"):
-        dtype = B.F32 if args.case == "fft32_fwd" else B.F16_BFP
+        dtype = B.F32 if args.case == "fft32_fwd" else (B.BF16 if args.arith == "bf16" else B.F16_BFP)
         direction = B.INVERSE if args.case == "fft16_inv" else B.FORWARD
         x = torch.randn((args.batch, n, 2), device=dev, generator=g)
-        x = x if dtype == B.F32 else x.to(torch.float16)
+        x = x if dtype == B.F32 else x.to(torch.bfloat16 if dtype == B.BF16 else torch.float16)
         y = torch.empty_like(x)
         plan = B.bfpfft_plan_create(n, args.batch, dtype, direction)
+        arith = {"f32": None, "f16": B.ARITH_F16, "f16mul": B.ARITH_F16_MUL_F32_ACC, "bf16": None}[args.arith]
+        if arith is not None:
+            B.bfpfft_plan_set_arith(plan, arith)
         for _ in range(args.reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -51,6 +58,35 @@ def main():
             e1.record(stream)
             times.append((e0, e1))
         bytes_per_rep = args.batch * n * (16 if dtype == B.F32 else 8)
+    elif args.case == "adaptive16_fwd":
+        x = torch.randn((args.batch, n, 2), device=dev, generator=g).to(torch.float16)
+        y = torch.empty_like(x)
+        e_in = torch.zeros(args.batch, dtype=torch.int32, device=dev)
+        e_out = torch.empty_like(e_in)
+        plan = B.bfpfft_plan_create(n, args.batch, B.F16_ADAPTIVE, B.FORWARD)
+        for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.bfpfft_exec_adaptive(plan, x, e_in, y, e_out, stream)
+            e1.record(stream)
+            times.append((e0, e1))
+        bytes_per_rep = args.batch * n * 8
+    elif args.case == "rda16":
+        geo = synth.radar_geometry(1024)
+        sc = synth.point_target_scene(n, n)
+        raw = torch.from_numpy(sc.raw.astype("complex64")).to(dev)
+        hr = torch.empty(n, dtype=torch.complex64, device=dev)
+        B.sar_make_filter(torch.from_numpy(sc.ref_range.astype("complex64")).to(dev), n, False, hr, stream)
+        img = torch.empty((n, n, 2), dtype=torch.float16, device=dev)
+        g5 = (geo.range_cell_m, geo.prf_hz, geo.wavelength_m, geo.speed_mps, geo.centre_range_m)
+        flags = B.RDA_RCMC | B.RDA_RANGE_DEPENDENT | B.RDA_PEAK_NORMALISE
+        for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.sar_rda_image(raw, B.F32, img, B.F16_BFP, hr, n, n, g5, 1024, flags, stream)
+            e1.record(stream)
+            times.append((e0, e1))
+        bytes_per_rep = n * n * 20
     elif args.case in ("range16", "image16"):
         n_az = 1024 if args.case == "range16" else n
         sc = synth.point_target_scene(n_az, n)
@@ -111,7 +147,7 @@ def main():
         import os
         import statistics
         ms = statistics.median(a.elapsed_time(b) for a, b in times[1:] or times)
-        print(f"{args.case} variant={os.environ.get('BFPFFT_ROWS', 'default')} ms={ms:.5f} "
+        print(f"{args.case} arith={args.arith} variant={os.environ.get('BFPFFT_ROWS', 'default')} ms={ms:.5f} "
               f"alg_GBps={bytes_per_rep / (ms * 1e-3) / 1e9:.1f}")
     status = B.bfpfft_device_status()
     if status != B.OK:

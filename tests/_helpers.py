@@ -18,6 +18,10 @@ def to_device(x: np.ndarray, dtype: int, device="cuda:0"):
     pair = np.stack([x.real, x.imag], axis=-1)
     if dtype in (B.F16_BFP, B.F16_NAIVE):
         return torch.from_numpy(np.ascontiguousarray(pair.astype(np.float16))).to(device)
+    if dtype == B.BF16:
+        t = torch.from_numpy(np.ascontiguousarray(pair.astype(np.float32))).to(torch.bfloat16)
+        assert np.array_equal(t.float().numpy(), pair.astype(np.float32)), "BF16 input not exactly representable"
+        return t.to(device)
     f8 = torch.float8_e4m3fn if dtype == B.E4M3_BFP else torch.float8_e5m2
     t = torch.from_numpy(np.ascontiguousarray(pair.astype(np.float32))).to(f8)
     back = t.to(torch.float32).numpy()
@@ -32,6 +36,8 @@ def from_device(t, dtype: int) -> np.ndarray:
         return t.numpy().astype(np.complex128)
     if dtype in (B.F16_BFP, B.F16_NAIVE):
         a = t.numpy().astype(np.float64)
+    elif dtype == B.BF16:
+        a = t.float().numpy().astype(np.float64)
     else:
         f8 = torch.float8_e4m3fn if dtype == B.E4M3_BFP else torch.float8_e5m2
         a = t.view(f8).to(torch.float32).numpy().astype(np.float64)
@@ -44,6 +50,8 @@ def empty_like_storage(shape_pts, dtype: int, device="cuda:0"):
         return torch.empty(shape_pts, dtype=torch.complex64, device=device)
     if dtype in (B.F16_BFP, B.F16_NAIVE):
         return torch.empty(tuple(shape_pts) + (2,), dtype=torch.float16, device=device)
+    if dtype == B.BF16:
+        return torch.empty(tuple(shape_pts) + (2,), dtype=torch.bfloat16, device=device)
     return torch.empty(tuple(shape_pts) + (2,), dtype=torch.uint8, device=device)
 
 
@@ -54,6 +62,8 @@ def storage_round(x: np.ndarray, dtype: int) -> np.ndarray:
         return quant.round_binary32(x)
     if dtype in (B.F16_BFP, B.F16_NAIVE):
         return quant.round_binary16(x)
+    if dtype == B.BF16:
+        return quant.round_bfloat16(x)
     return quant.round_fp8(x, "e4m3" if dtype == B.E4M3_BFP else "e5m2")
 
 

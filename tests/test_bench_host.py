@@ -44,3 +44,10 @@ def test_peak_source(tmp_path, monkeypatch):
     assert bench._peaks() == (bench.FALLBACK_HBM_GBS, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6701.5}))
     assert bench._peaks() == (6701.5, "measured")
+
+
+def test_cpu_baseline_one_core_and_all_cores():
+    cb = bench._cpu_baseline(seconds=1.0)
+    assert cb["kind"] == "oracle" and cb["unit"] == "GFLOPS" and cb["value"] > 0
+    assert cb["single_core_value"] > 0 and cb["cores"] >= 1 and cb["cpu_model"]
+    assert str(bench.ORACLE_LINES) in cb["sample"]

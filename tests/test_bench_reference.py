@@ -22,7 +22,7 @@ def _run(*extra):
 
 
 def test_reference_line_keeps_the_contract():
-    rec = _run("--steps", "1", "--warmup", "3", "--ref-lines", "8")
+    rec = _run("--steps", "1", "--warmup", "3")
     assert rec["impl"] == "reference"
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
@@ -31,9 +31,12 @@ def test_reference_line_keeps_the_contract():
     assert rec["steps"] == 1 and rec["warmup"] == 3 and rec["n_gpus"] == 1
     assert rec["higher_is_better"] is True and rec["vs_baseline"] is None
     assert rec["dtype"] == "f64"
-    assert "workload" in rec["config"]
+    import bench
+    assert rec["config"] == bench._config(bench.BATCH, 1)      # the same config as the GPU arm
+    assert rec["sample"] and str(bench.ORACLE_LINES) in rec["sample"]
     cb = rec["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == (os.cpu_count() or 1) and cb["sample"] == rec["sample"]
+    assert cb["cpu_model"]
     assert cb["value"] == rec["value"] and cb["unit"] == rec["unit"]
     e2e = rec["e2e"]
     assert e2e["value"] == rec["value"] and e2e["unit"] == rec["unit"]
@@ -41,5 +44,5 @@ def test_reference_line_keeps_the_contract():
 
 
 def test_reference_warmup_is_raised_to_three():
-    rec = _run("--steps", "1", "--warmup", "0", "--ref-lines", "4")
+    rec = _run("--steps", "1", "--warmup", "0")
     assert rec["warmup"] == 3

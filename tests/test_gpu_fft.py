@@ -58,7 +58,7 @@ def test_f32_forward_and_inverse(n, batch, rows_variant):
 
 
 ROW_VARIANTS = ["tma", "plain", "pp", "h16", "h16pp", "tma_pp", "tma_h16", "tma_h16pp", "tc", "plain4", "plain_l2",
-                "plain4_l2", "h16_l2", "h16_4_l2"]
+                "plain4_l2", "h16_l2", "h16_4_l2", "h16s_4_l2"]
 
 
 @pytest.fixture(params=ROW_VARIANTS)

@@ -1,0 +1,151 @@
+"""Precision modes on the GPU (Section VI's mode list, Table I's pure FP16,
+Section IV-C's bfloat16) against the oracle's rounding schedules.
+
+- Pure FP16 and bfloat16 (bfpfft_plan_set_arith): every operation of the
+  kernel rounds in the order of oracle.emulate.fft_radix16_rounded, so on
+  lengths that are powers of 16 the GPU output equals the emulator's value
+  by value (allowed: 1 ulp on 1 in 1000 components, where the emulator's
+  FP64 evaluation of a fused multiply-add rounds twice), and the SQNR
+  against FP64 equals the emulator's within 0.1 dB -- within the +-1.5 dB
+  band of the prediction (60.4 dB pure FP16 at N = 4096).  Other lengths:
+  SQNR against FP64 above the mode's floor.
+- FP16 operands / FP32 accumulation (the tensor-core DFT blocks): against
+  oracle.emulate.fft_radix16_mma, which the GPU matches far more closely
+  (>= 6 dB) than either matches the exact DFT.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import emulate as E
+from oracle import fft as F
+from oracle import metrics
+from oracle import quant as Q
+from paper_2605_28451_gb300 import bfpfft as B
+from paper_2605_28451_gb300 import build, synth
+
+from _helpers import from_device, storage_round, to_device
+
+pytestmark = pytest.mark.gpu
+
+ROUND = {B.F16_BFP: Q.round_binary16, B.BF16: Q.round_bfloat16}
+ULP_BITS = {B.F16_BFP: 10, B.BF16: 7}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(cuda_ready):
+    build.build()
+    B.lib()
+
+
+def gpu_run(x, n, dtype, direction, arith):
+    import torch
+    p = B.bfpfft_plan_create(n, x.shape[0], dtype, direction)
+    B.bfpfft_plan_set_arith(p, arith)
+    xin = to_device(x, dtype)
+    out = torch.empty_like(xin)
+    B.bfpfft_exec(p, xin, out)
+    torch.cuda.synchronize()
+    assert B.bfpfft_plan_status(p) == B.OK
+    return from_device(out, dtype)
+
+
+def emulate_rounded(x, dtype, direction):
+    """The kernel's schedule: forward, or conj(forward(rn(conj(z) / N))) for the inverse."""
+    op = ROUND[dtype]
+    if direction == B.FORWARD:
+        return E.fft_radix16_rounded(x, op)
+    n = x.shape[-1]
+    return np.conj(E.fft_radix16_rounded(op(np.conj(x) / n), op))
+
+
+def assert_same_values(got, emu, fraction_bits, min_equal=0.999):
+    for g, e in ((got.real, emu.real), (got.imag, emu.imag)):
+        diff = g != e
+        assert diff.mean() <= 1.0 - min_equal, diff.mean()
+        ulp = np.exp2(np.floor(np.log2(np.maximum(np.abs(e[diff]), 2.0 ** -14))) - fraction_bits)
+        assert np.all(np.abs(g[diff] - e[diff]) <= ulp), np.max(np.abs(g[diff] - e[diff]) / ulp)
+
+
+@pytest.mark.parametrize("dtype,arith", [(B.F16_BFP, B.ARITH_F16), (B.BF16, B.ARITH_BF16)])
+@pytest.mark.parametrize("n", [256, 4096])
+@pytest.mark.parametrize("direction", [B.FORWARD, B.INVERSE])
+def test_16bit_arithmetic_equals_the_rounded_schedule(dtype, arith, n, direction):
+    batch = 64 if n == 4096 else 256
+    x = storage_round(synth.complex_gaussian(batch, n, seed=0), dtype)
+    if direction == B.INVERSE:
+        x = storage_round(F.fft(x), dtype)            # a spectrum of the right scale
+    got = gpu_run(x, n, dtype, direction, arith)
+    emu = emulate_rounded(x, dtype, direction)
+    assert_same_values(got, emu, ULP_BITS[dtype])
+    exact = F.fft(x) if direction == B.FORWARD else F.ifft(x)
+    s_gpu, s_emu = metrics.sqnr_db(exact, got), metrics.sqnr_db(exact, emu)
+    assert abs(s_gpu - s_emu) <= 0.1, (s_gpu, s_emu)
+    if dtype == B.F16_BFP and n == 4096 and direction == B.FORWARD:
+        assert abs(s_gpu - 60.4) <= 1.5        # the emulator's prediction for pure FP16 at 4096
+        assert s_gpu >= 55.0
+
+
+@pytest.mark.parametrize("n", [16, 32, 64, 128, 512, 1024, 2048, 8192, 16384])
+@pytest.mark.parametrize("dtype,arith,floor_db", [(B.F16_BFP, B.ARITH_F16, 55.0), (B.BF16, B.ARITH_BF16, 35.0)])
+def test_16bit_arithmetic_other_lengths(n, dtype, arith, floor_db):
+    batch = max(2, (1 << 18) // n)
+    x = storage_round(synth.complex_gaussian(batch, n, seed=1), dtype)
+    fwd = gpu_run(x, n, dtype, B.FORWARD, arith)
+    assert metrics.sqnr_db(F.fft(x), fwd) >= floor_db
+    spec = storage_round(F.fft(x), dtype)
+    inv = gpu_run(spec, n, dtype, B.INVERSE, arith)
+    assert metrics.sqnr_db(F.ifft(spec), inv) >= floor_db
+
+
+@pytest.mark.parametrize("direction", [B.FORWARD, B.INVERSE])
+def test_fp16_operands_fp32_accumulation_follow_the_mma_schedule(direction):
+    n, batch = 4096, 64
+    x = storage_round(synth.complex_gaussian(batch, n, seed=2), B.F16_BFP)
+    if direction == B.INVERSE:
+        x = storage_round(F.fft(x), B.F16_BFP)
+    got = gpu_run(x, n, B.F16_BFP, direction, B.ARITH_F16_MUL_F32_ACC)
+    if direction == B.FORWARD:
+        emu = E.fft_radix16_mma(x)
+        exact = F.fft(x)
+    else:
+        emu = np.conj(E.fft_radix16_mma(np.conj(x) / n))
+        exact = F.ifft(x)
+    s_emu = metrics.sqnr_db(exact, emu)
+    assert metrics.sqnr_db(emu, got) >= s_emu + 6.0
+    assert abs(metrics.sqnr_db(exact, got) - s_emu) <= 0.5
+    assert metrics.sqnr_db(exact, got) >= 55.0
+
+
+def test_pure_fp16_naive_inverse_overflows_and_the_shift_does_not():
+    n, batch = 4096, 4
+    spec = np.full((batch, n), 100.0 + 0.0j)
+    naive = gpu_run(spec, n, B.F16_NAIVE, B.INVERSE, B.ARITH_F16)
+    assert not np.all(np.isfinite(naive))
+    bfp = gpu_run(spec, n, B.F16_BFP, B.INVERSE, B.ARITH_F16)
+    assert np.all(np.isfinite(bfp))
+    assert metrics.sqnr_db(F.ifft(spec), bfp) >= 50.0
+
+
+def test_set_arith_combinations():
+    def status(n, dtype, arith, direction=B.FORWARD):
+        p = B.bfpfft_plan_create(n, 2, dtype, direction)
+        try:
+            B.bfpfft_plan_set_arith(p, arith)
+        except B.BfpfftError as e:
+            return e.status
+        return B.OK
+    assert status(4096, B.F16_BFP, B.ARITH_F16) == B.OK
+    assert status(16384, B.F16_NAIVE, B.ARITH_F16) == B.OK
+    assert status(32768, B.F16_BFP, B.ARITH_F16) == B.ERR_UNSUPPORTED
+    assert status(4096, B.F32, B.ARITH_F16) == B.ERR_UNSUPPORTED
+    assert status(4096, B.E4M3_BFP, B.ARITH_F16) == B.ERR_UNSUPPORTED
+    assert status(4096, B.F16_BFP, B.ARITH_F16_MUL_F32_ACC) == B.OK
+    assert status(8192, B.F16_BFP, B.ARITH_F16_MUL_F32_ACC) == B.ERR_UNSUPPORTED
+    assert status(4096, B.BF16, B.ARITH_F32) == B.ERR_UNSUPPORTED
+    assert status(4096, B.F16_BFP, B.ARITH_BF16) == B.ERR_UNSUPPORTED
+    assert status(4096, B.F16_BFP, 9) == B.ERR_INVALID_ARG
+    u = B.bfpfft_plan_create_many([256, 4096], [0, 256], B.F16_BFP, B.FORWARD)
+    with pytest.raises(B.BfpfftError) as e:
+        B.bfpfft_plan_set_arith(u, B.ARITH_F16)
+    assert e.value.status == B.ERR_UNSUPPORTED

@@ -257,3 +257,59 @@ def test_table_5_pin_catches_a_wrong_storage_schedule(plant):
         got = E.fft_rounded(x, store=Q.round_binary16, store_input=False)
     s = metrics.sqnr_db(F.fft(x), got)
     assert abs(s - want) > 0.3, s
+
+
+@pytest.mark.parametrize("n", [16, 256, 4096])
+def test_mma_schedule_unrounded_is_the_dft(n):
+    x = np.random.default_rng(n).standard_normal((3, n)) + 1j * np.random.default_rng(n + 1).standard_normal((3, n))
+    got = E.fft_radix16_mma(x, operand=None, coeff=None, acc=None, store=None)
+    ref = F.dft_bruteforce(x) if n <= 256 else F.fft(x)
+    assert metrics.rel_l2(ref, got) <= 1e-13
+
+
+
+@pytest.fixture(scope="module")
+def mma_case():
+    x = Q.round_binary16(np.random.default_rng(5).standard_normal((64, 4096))
+                         + 1j * np.random.default_rng(6).standard_normal((64, 4096)))
+    return x, F.fft(x)
+
+
+def test_mma_schedule_operand_roundings_follow_the_error_model(mma_case):
+    """FP16 operands of N = 4096 (input already FP16): passes 2 and 3 round their
+    inputs, so two storage points; with the FP16 output store, three.  Each
+    must match the rounding error model's prediction."""
+    x, ref = mma_case
+    ops = E.fft_radix16_mma(x, coeff=None, acc=None, store=None)
+    ops_store = E.fft_radix16_mma(x, coeff=None, acc=None)
+    assert metrics.sqnr_db(ref, ops) == pytest.approx(E.predict_sqnr_db(2, 10, 0.0451), abs=0.3)
+    assert metrics.sqnr_db(ref, ops_store) == pytest.approx(E.predict_sqnr_db(3, 10, 0.0451), abs=0.3)
+
+
+def test_mma_schedule_fp32_accumulation_is_fp32_class(mma_case):
+    x, ref = mma_case
+    assert metrics.sqnr_db(ref, E.fft_radix16_mma(x, operand=None, coeff=None, store=None)) >= 135.0
+
+
+def test_mma_schedule_coefficient_rounding_is_a_fixed_perturbation(mma_case):
+    """Rounding the DFT-16 matrix to FP16 perturbs a pass by E = W~ - W.  On one
+    pass of white data (N = 16) its relative noise power is mean |E_qr|^2
+    (|W_qr| = 1), unaligned.  At N = 4096 the operand / store noise is
+    independent of that perturbation, so the full mode's noise power is the
+    sum of the two measured separately."""
+    x16 = np.random.default_rng(7).standard_normal((20000, 16)) + 1j * np.random.default_rng(8).standard_normal((20000, 16))
+    qr = np.outer(np.arange(16), np.arange(16)) % 16
+    w = np.exp(-2j * np.pi * qr / 16)
+    e2 = np.mean(np.abs(Q.round_binary16(w.real) + 1j * Q.round_binary16(w.imag) - w) ** 2)
+    one_pass = metrics.sqnr_db(F.fft(x16), E.fft_radix16_mma(x16, operand=None, acc=None, store=None), align=False)
+    assert one_pass == pytest.approx(-10 * np.log10(e2), abs=0.2)
+    x, ref = mma_case
+    parts = [metrics.sqnr_db(ref, E.fft_radix16_mma(x, coeff=None, acc=None), align=False),
+             metrics.sqnr_db(ref, E.fft_radix16_mma(x, operand=None, acc=None, store=None), align=False)]
+    combined = -10 * np.log10(sum(10 ** (-p / 10) for p in parts))
+    assert metrics.sqnr_db(ref, E.fft_radix16_mma(x), align=False) == pytest.approx(combined, abs=0.3)
+
+
+def test_mma_schedule_rejects_other_lengths():
+    with pytest.raises(ValueError):
+        E.fft_radix16_mma(np.ones((1, 1024), complex))
