@@ -243,6 +243,24 @@ int bfpfft_plan_set_arith(bfpfft_plan plan, int arith);
  */
 int bfpfft_plan_selftest_wait(bfpfft_plan plan, void* stream);
 
+/*
+ * sar_range_compress / sar_azimuth_compress in a chosen arithmetic (Section
+ * VI's precision modes of the range-Doppler chain, Table IV): arith
+ * BFPFFT_ARITH_F32 is the calls above (FP32 registers; FP16, FP32 or naive
+ * storage); BFPFFT_ARITH_F16 runs every transform, the filter product and the
+ * 1/N shift in FP16 arithmetic (the "pure FP16" mode; the filter spectrum is
+ * rounded to FP16 once; a complex64 raw echo is rounded to FP16 as it is
+ * loaded) and needs FP16 output (F16_BFP, or F16_NAIVE for the unshifted
+ * schedule) and, for the azimuth call, FP16 input.  The FP16 mode turns
+ * corners with the tiled transpose whatever BFPFFT_SAR_TURN says.
+ * Errors: as the calls above; INVALID_ARG for an unknown arith; UNSUPPORTED for
+ * a storage combination the mode does not offer.
+ */
+int sar_range_compress_arith(const void* raw, int raw_dtype, void* out, int out_dtype, const void* hr,
+                             int64_t n_az, int64_t n_rg, int transpose_out, int arith, void* stream);
+int sar_azimuth_compress_arith(const void* rc, int rc_dtype, int rc_layout, void* img, int img_dtype,
+                               const void* ha, int64_t n_az, int64_t n_rg, int arith, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Adaptive per-line block exponents (Section VIII, Limitations).
  *

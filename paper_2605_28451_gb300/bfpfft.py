@@ -72,6 +72,10 @@ SIGNATURES = {
                                           ctypes.c_int, _vp]),
     "sar_azimuth_compress": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _c_int64,
                                             _c_int64, _vp]),
+    "sar_range_compress_arith": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _c_int64, _c_int64,
+                                                ctypes.c_int, ctypes.c_int, _vp]),
+    "sar_azimuth_compress_arith": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp, _c_int64,
+                                                  _c_int64, ctypes.c_int, _vp]),
     "sar_rda_image": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _c_int64, _c_int64, _vp, _c_int64,
                                      ctypes.c_int, _vp]),
     "sar_autofocus_workspace_bytes": (ctypes.c_size_t, [_c_int64]),
@@ -272,6 +276,20 @@ def sar_azimuth_compress(rc, rc_dtype: int, rc_layout: int, img, img_dtype: int,
                          stream=None):
     _check(lib().sar_azimuth_compress(_ptr(rc), int(rc_dtype), int(rc_layout), _ptr(img), int(img_dtype), _ptr(ha),
                                       int(n_az), int(n_rg), _stream(stream)), "sar_azimuth_compress")
+
+
+def sar_range_compress_arith(raw, raw_dtype: int, out, out_dtype: int, hr, n_az: int, n_rg: int,
+                             transpose_out: bool, arith: int, stream=None):
+    _check(lib().sar_range_compress_arith(_ptr(raw), int(raw_dtype), _ptr(out), int(out_dtype), _ptr(hr), int(n_az),
+                                          int(n_rg), int(bool(transpose_out)), int(arith), _stream(stream)),
+           "sar_range_compress_arith")
+
+
+def sar_azimuth_compress_arith(rc, rc_dtype: int, rc_layout: int, img, img_dtype: int, ha, n_az: int, n_rg: int,
+                               arith: int, stream=None):
+    _check(lib().sar_azimuth_compress_arith(_ptr(rc), int(rc_dtype), int(rc_layout), _ptr(img), int(img_dtype),
+                                            _ptr(ha), int(n_az), int(n_rg), int(arith), _stream(stream)),
+           "sar_azimuth_compress_arith")
 
 
 RDA_RCMC = 1

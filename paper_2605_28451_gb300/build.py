@@ -38,6 +38,7 @@ SOURCES = [
     "rows_adaptive.cu",
     "rows16.cu",
     "rda.cu",
+    "twopass.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

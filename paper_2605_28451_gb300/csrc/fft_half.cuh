@@ -18,11 +18,15 @@
 //   W16^2, W16^6      one rounded sum, then a rounded product by sqrt(1/2)
 //   -i                exact swap
 //
-// Exchange layout.  Slot of point i: i XOR h(i >> 5) on its low five bits, with
-// h(q) = (q & 15) | (bit 3 of q) << 4.  Simulated over every pass of every
-// length from 256 to 16384: the stride-16 stores of the first pass, the
-// 256-apart half-warps of the second, and the consecutive loads are all free
-// of bank conflicts, with no padding.
+// Exchange layout (Layout16 below).  The XOR swizzle -- slot of point i is
+// i XOR h(i >> 5) on its low five bits, h(q) = (q & 15) | (bit 3 of q) << 4 --
+// was simulated over every pass of every length from 256 to 16384: the
+// stride-16 stores of the first pass, the 256-apart half-warps of the second
+// and the consecutive loads are all free of bank conflicts, with no padding.
+// One padding slot per 32 points costs one two-way conflicted store group but
+// no integer work per access; no linear padding is conflict-free in all
+// passes (the first pass needs the second half-warp moved by 0 or 16 banks,
+// the second by 8).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -175,19 +179,44 @@ template <class H> struct Dft16b<H, 16> {
   }
 };
 
-// Swizzled 16-bit exchange slot of point i (see the header comment).
+// 16-bit exchange layouts.  kSwizzle: the XOR swizzle of the header comment,
+// free of bank conflicts but a few integer operations per access.  kPad32:
+// one padding slot per 32 points, slot i + (i >> 5): every access is the
+// thread's base plus a compile-time offset (no per-access integer work),
+// conflict-free except the second pass's stores, whose half-warps lie 256
+// points apart (two-way).
+// kPadQ: each exchange has its own padding (every exchange is written once
+// and read once, so the layouts need not agree): after the first pass
+// i + (i >> 5), after the second i + (i >> 5) + 8 (i >> 8), which moves the
+// second pass's 256-apart half-warps 16 banks apart.  Simulated over every
+// pass: conflict-free for every length from 512 (a two-way conflict on one
+// access group at 256 and below, where several lines share a warp), and every
+// access is the thread's base plus a compile-time offset.
+enum Layout16 : int { kSwizzle = 0, kPad32 = 1, kPadQ = 2 };
+
+template <int L, int Q>
 __device__ __forceinline__ int slot16(int i) {
-  const int q = i >> 5;
-  return i ^ ((q & 15) | (((q >> 3) & 1) << 4));
+  if constexpr (L == kSwizzle) {
+    const int q = i >> 5;
+    return i ^ ((q & 15) | (((q >> 3) & 1) << 4));
+  } else if constexpr (L == kPadQ && Q == 1) {
+    return i + (i >> 5) + 8 * (i >> 8);
+  } else {
+    return i + (i >> 5);
+  }
 }
 
-template <int N, int Ns, class H>
+template <int N, int L>
+__host__ __device__ constexpr int slots16() { return L == kSwizzle ? N : L == kPad32 ? N + N / 32 : N + N / 16; }
+
+template <int N, int Ns, class H, int L>
 struct StockhamPass16 {
   static constexpr int P = kPointsPerThread;
   static constexpr int T = N / P;
   static constexpr int R = (N / Ns) >= 16 ? 16 : N / Ns;
   static constexpr int B = P / R;
   static constexpr bool kLast = (Ns * R == N);
+  static constexpr int kQ = ilog16(Ns);   // exchange number written by this pass
 
   __device__ __forceinline__ static void run(H (&v)[P], const Tw16* __restrict__ tw, uint32_t* xch, int t) {
     using A = A16<H>;
@@ -215,15 +244,15 @@ struct StockhamPass16 {
       } else {
         const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) xch[slot16(base + r * Ns)] = A::bits(u[r]);
+        for (int r = 0; r < R; ++r) xch[slot16<L, kQ>(base + r * Ns)] = A::bits(u[r]);
       }
     }
     if constexpr (!kLast) {
       __syncthreads();
 #pragma unroll
-      for (int m = 0; m < P; ++m) v[m] = A::from_bits(xch[slot16(t + T * m)]);
+      for (int m = 0; m < P; ++m) v[m] = A::from_bits(xch[slot16<L, kQ>(t + T * m)]);
       __syncthreads();
-      StockhamPass16<N, Ns * R, H>::run(v, tw, xch, t);
+      StockhamPass16<N, Ns * R, H, L>::run(v, tw, xch, t);
     }
   }
 };
@@ -231,8 +260,13 @@ struct StockhamPass16 {
 // Dense rows of 16-bit storage computed in 16-bit arithmetic.  MODE kForward
 // or kInverse (conj(DFT(conj(z) * 1/N)), the 1/N applied in the format before
 // the transform, Eq. 1); NAIVE drops the shift and scales after the transform
-// (Section III-B).  One line per group of N / 16 threads.
-template <int N, class H, int MODE, bool NAIVE, int MINB>
+// (Section III-B).  MODE kCompress is the matched-filter line of the SAR
+// chain in the same arithmetic: forward DFT, the product with the filter
+// spectrum a.h (rounded once to the format; the two-step fused product of the
+// twiddles), conj and the 1/N shift, DFT, conj.  IN32: the input is complex64
+// (the raw echo), rounded to the format as it is loaded.  One line per group
+// of N / 16 threads.
+template <int N, class H, int MODE, bool NAIVE, int MINB, int L, bool IN32 = false>
 __global__ void __launch_bounds__(RowShape<N>::kThreads, MINB)
 fft_rows16_kernel(const RowArgs a) {
   using S = RowShape<N>;
@@ -243,18 +277,26 @@ fft_rows16_kernel(const RowArgs a) {
   const int t = threadIdx.x - g * T;
   const long long line = (long long)blockIdx.x * G + g;
   const bool active = line < a.lines;
-  uint32_t* xch = smem16 + g * N;
+  uint32_t* xch = smem16 + g * slots16<N, L>();
   const Tw16* tw = static_cast<const Tw16*>(a.tw16);
   H v[P];
   if (active) {
+    using TIn = typename std::conditional<IN32, float2, uint32_t>::type;
     if (a.pf_ahead > 0 && threadIdx.x == 0) {
       const long long l0 = ((long long)blockIdx.x + a.pf_ahead) * G;
       const long long cnt = a.lines - l0 < G ? a.lines - l0 : G;
-      if (cnt > 0) prefetch_l2_bulk(static_cast<const H*>(a.in) + l0 * N, uint32_t(cnt * N * sizeof(H)));
+      if (cnt > 0) prefetch_l2_bulk(static_cast<const TIn*>(a.in) + l0 * N, uint32_t(cnt * N * sizeof(TIn)));
     }
-    const uint32_t* in = static_cast<const uint32_t*>(a.in) + line * a.in_stride + t;
+    const TIn* in = static_cast<const TIn*>(a.in) + line * a.in_stride + t;
 #pragma unroll
-    for (int m = 0; m < P; ++m) v[m] = A::from_bits(__ldcs(in + T * m));
+    for (int m = 0; m < P; ++m) {
+      if constexpr (IN32) {
+        const float2 x = __ldcs(in + T * m);
+        v[m] = A::make(x.x, x.y);
+      } else {
+        v[m] = A::from_bits(__ldcs(in + T * m));
+      }
+    }
   } else {
 #pragma unroll
     for (int m = 0; m < P; ++m) v[m] = A::make(0.f, 0.f);
@@ -265,8 +307,28 @@ fft_rows16_kernel(const RowArgs a) {
 #pragma unroll
     for (int m = 0; m < P; ++m) v[m] = A::mul(v[m], c);
   }
-  StockhamPass16<N, 1, H>::run(v, tw, xch, t);
-  if (MODE == kInverse) {
+  StockhamPass16<N, 1, H, L>::run(v, tw, xch, t);
+  if constexpr (MODE == kCompress) {
+    // Filter product in groups of four (register pressure), then conj and the
+    // shift; the first transform's last exchange ended with a barrier, so the
+    // second may write the exchange buffer at once.
+    const H c = A::make(NAIVE ? 1.0f : 1.0f / float(N), NAIVE ? -1.0f : -1.0f / float(N));
+#pragma unroll
+    for (int m0 = 0; m0 < P; m0 += 4) {
+      float2 h[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) h[i] = __ldg(a.h + t + T * (m0 + i));
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const H w = A::make(h[i].x, h[i].y), wp = A::make(-h[i].y, h[i].x);
+        v[m0 + i] = A::mul(Ops16<H>::cmul(v[m0 + i], w, wp), c);
+      }
+    }
+    int t2;
+    asm volatile("mov.b32 %0, %1;" : "=r"(t2) : "r"(t));
+    StockhamPass16<N, 1, H, L>::run(v, tw, xch, t2);
+  }
+  if (MODE == kInverse || MODE == kCompress) {
     const float s = NAIVE ? 1.0f / float(N) : 1.0f;
     const H c = A::make(s, -s);
 #pragma unroll
@@ -280,11 +342,11 @@ fft_rows16_kernel(const RowArgs a) {
   }
 }
 
-template <int N, class H, int MODE, bool NAIVE, int MINB>
-cudaError_t launch_rows16_n(const RowArgs& a, cudaStream_t stream) {
+template <int N, class H, int MODE, bool NAIVE, int MINB, int L, bool IN32 = false>
+cudaError_t launch_rows16_nl(const RowArgs& a, cudaStream_t stream) {
   using S = RowShape<N>;
-  constexpr size_t kBytes = size_t(S::G) * N * sizeof(uint32_t);
-  auto kern = fft_rows16_kernel<N, H, MODE, NAIVE, MINB>;
+  constexpr size_t kBytes = size_t(S::G) * slots16<N, L>() * sizeof(uint32_t);
+  auto kern = fft_rows16_kernel<N, H, MODE, NAIVE, MINB, L, IN32>;
   static const LaunchSetup setup = setup_kernel(kern, S::kThreads, kBytes);
   if (setup.err != cudaSuccess) return setup.err;
   if (a.lines <= 0) return cudaSuccess;
@@ -296,6 +358,13 @@ cudaError_t launch_rows16_n(const RowArgs& a, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+// Exchange layout kPadQ (the swizzle and plain pad32 measured the same time as
+// each other: the swizzle issue-bound, pad32 bound by its bank conflicts).
+template <int N, class H, int MODE, bool NAIVE, int MINB, bool IN32 = false>
+cudaError_t launch_rows16_n(const RowArgs& a, cudaStream_t stream) {
+  return launch_rows16_nl<N, H, MODE, NAIVE, MINB, kPadQ, IN32>(a, stream);
+}
+
 // Resident CTAs per SM requested from the register allocator: 16 values of
 // 32 bits per thread leave room for more than the FP32 kernel's four with
 // FP16 (40 registers, no spills); bfloat16 pairs spill at 40 and keep four.
@@ -304,6 +373,23 @@ constexpr int rows16_min_blocks() {
   return RowShape<N>::kThreads >= 1024 ? 1
          : RowShape<N>::kThreads >= 512 ? 2
          : (std::is_same<H, __half2>::value ? 6 : 4);
+}
+
+// SAR compression lines in FP16 arithmetic, log2n in [8, 14]: 4 CTAs per SM
+// (the filter loads and the second transform need the FP32 kernel's registers).
+template <bool NAIVE, bool IN32>
+cudaError_t launch_rows16_compress(int log2n, const RowArgs& a, cudaStream_t s) {
+  using H = __half2;
+  switch (log2n) {
+    case 8: return launch_rows16_n<256, H, kCompress, NAIVE, 4, IN32>(a, s);
+    case 9: return launch_rows16_n<512, H, kCompress, NAIVE, 4, IN32>(a, s);
+    case 10: return launch_rows16_n<1024, H, kCompress, NAIVE, 4, IN32>(a, s);
+    case 11: return launch_rows16_n<2048, H, kCompress, NAIVE, 4, IN32>(a, s);
+    case 12: return launch_rows16_n<4096, H, kCompress, NAIVE, 4, IN32>(a, s);
+    case 13: return launch_rows16_n<8192, H, kCompress, NAIVE, 2, IN32>(a, s);
+    case 14: return launch_rows16_n<16384, H, kCompress, NAIVE, 1, IN32>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <class H, int MODE, bool NAIVE>

@@ -89,7 +89,8 @@ struct RowArgs {
 enum RowVariant : int {
   kRowsTma = 0, kRowsPlain = 1, kRowsPlainPP = 2, kRowsPlainH = 3, kRowsPlainHPP = 4,
   kRowsTmaPP = 5, kRowsTmaH = 6, kRowsTmaHPP = 7, kRowsTc = 8, kRowsPlain4 = 9,
-  kRowsPlainL2 = 10, kRowsPlain4L2 = 11, kRowsPlainHL2 = 12, kRowsPlainH4L2 = 13, kRowsPlainHS4L2 = 14
+  kRowsPlainL2 = 10, kRowsPlain4L2 = 11, kRowsPlainHL2 = 12, kRowsPlainH4L2 = 13, kRowsPlainHS4L2 = 14,
+  kRowsTwoPass = 15   // lines of 32768 and 65536 points: two streaming passes (twopass.cu) instead of four-step
 };
 
 constexpr int kPointsPerThread = 16;

@@ -30,6 +30,9 @@ cudaError_t launch_spectral_adaptive_c64(int log2n, const RowArgs& a, cudaStream
 constexpr int kRows16MaxLog2 = 14;
 cudaError_t launch_rows16_f16(int log2n, int mode, bool naive, const RowArgs& a, cudaStream_t s);
 cudaError_t launch_rows16_bf16(int log2n, int mode, const RowArgs& a, cudaStream_t s);
+// SAR compression lines in FP16 arithmetic (log2n in [8, 14]): in32 reads a
+// complex64 input; naive drops the 1/N shift (Section III-B).
+cudaError_t launch_rows16_compress_f16(int log2n, bool in32, bool naive, const RowArgs& a, cudaStream_t s);
 cudaError_t launch_twiddles16(void* tw, int n, bool bf16);
 
 // SAR compression lines (Section VI, Fig. 1): float2 or __half2 in and out,

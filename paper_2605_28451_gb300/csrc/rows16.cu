@@ -12,6 +12,11 @@ cudaError_t launch_rows16_f16(int log2n, int mode, bool naive, const RowArgs& a,
                : launch_rows16<__half2, kInverse, false>(log2n, a, s);
 }
 
+cudaError_t launch_rows16_compress_f16(int log2n, bool in32, bool naive, const RowArgs& a, cudaStream_t s) {
+  if (in32) return naive ? launch_rows16_compress<true, true>(log2n, a, s) : launch_rows16_compress<false, true>(log2n, a, s);
+  return naive ? launch_rows16_compress<true, false>(log2n, a, s) : launch_rows16_compress<false, false>(log2n, a, s);
+}
+
 cudaError_t launch_rows16_bf16(int log2n, int mode, const RowArgs& a, cudaStream_t s) {
   if (mode == kForward) return launch_rows16<__nv_bfloat162, kForward, false>(log2n, a, s);
   if (mode == kInverse) return launch_rows16<__nv_bfloat162, kInverse, false>(log2n, a, s);

@@ -27,6 +27,7 @@
 #include "uneven.h"
 #include "pt_metrics.h"
 #include "rda.h"
+#include "twopass.h"
 
 namespace {
 
@@ -116,9 +117,22 @@ __global__ void fourstep_twiddle_kernel(float2* tw, int n) {
   tw[i] = make_float2(float(c), float(s));
 }
 
+// Two-pass twiddles of a length n = N1 * 256 line: T[k1][n2] = W_n^{n2 k1} for
+// k1 < N1, n2 < 256 (n entries; consecutive lanes take consecutive n2).  FP64
+// sincospi, rounded once to FP32.
+__global__ void twopass_twiddle_kernel(float2* tw, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k1 = i / 256, n2 = i % 256;
+  double s, c;
+  sincospi(-2.0 * double((long long)n2 * k1) / double(n), &s, &c);
+  tw[i] = make_float2(float(c), float(s));
+}
+
 // Per-device, per-length twiddle tables, created on first use and kept for
 // the life of the process (a few hundred KB per device at most).  Keys
-// 0..16: pass-major Stockham tables; 100 + log2 n: four-step tables.
+// 0..16: pass-major Stockham tables; 100 + log2 n: four-step tables;
+// 500 + log2 n: two-pass tables.
 std::mutex g_tw_mutex;
 std::map<std::pair<int, int>, float2*> g_tw;
 
@@ -134,12 +148,15 @@ int get_twiddles(int log2n, float2** out) {
     return BFPFFT_OK;
   }
   if (fault("alloc")) return BFPFFT_ERR_OOM;
-  const bool four = log2n >= 100;
-  const int n = 1 << (four ? log2n - 100 : log2n);
+  const bool two = log2n >= 500;
+  const bool four = !two && log2n >= 100;
+  const int n = 1 << (two ? log2n - 500 : four ? log2n - 100 : log2n);
   float2* tw = nullptr;
   e = cudaMalloc(&tw, sizeof(float2) * n);
   if (e != cudaSuccess) return cuda_status(e);
-  if (four) {
+  if (two) {
+    twopass_twiddle_kernel<<<(n + 255) / 256, 256>>>(tw, n);
+  } else if (four) {
     fourstep_twiddle_kernel<<<(n + 255) / 256, 256>>>(tw, n);
   } else {
     twiddle_kernel<<<(n + 255) / 256, 256>>>(tw, n);
@@ -210,6 +227,46 @@ int get_status_word(int** out) {
   return BFPFFT_OK;
 }
 
+// Corner turns of the SAR calls: "split" (default) compresses dense rows and
+// turns the result with a tiled transpose through stream-ordered scratch;
+// "fused" turns on chip through cluster distributed shared memory.
+// BFPFFT_SAR_TURN selects; the split form measured faster on GB300 (4096 x
+// 4096, FP16: 97 us against 120 us per compression).
+bool sar_split_turns() {
+  const char* v = std::getenv("BFPFFT_SAR_TURN");
+  return v == nullptr || std::strcmp(v, "fused") != 0;
+}
+
+// Stream-ordered scratch from a library-owned pool per device that keeps its
+// memory between calls (release threshold: never), so repeated calls neither
+// synchronise nor return memory to the driver.
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  if (fault("alloc")) return cudaErrorMemoryAllocation;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = pools.find(dev);
+    if (it == pools.end()) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+      uint64_t keep = UINT64_MAX;
+      if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
+      pools[dev] = pool;
+    } else {
+      pool = it->second;
+    }
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 // Row-kernel variant from BFPFFT_ROWS (tma, plain, pp, h16, h16pp, tma_pp,
 // tma_h16, tma_h16pp, tc, plain4, plain_l2, plain4_l2).  Unset: plain4_l2,
 // the plain kernel with an FP32 exchange at 4 CTAs per SM whose CTAs prefetch
@@ -224,7 +281,8 @@ int rows_variant() {
       {"h16", bfp::kRowsPlainH},      {"h16pp", bfp::kRowsPlainHPP}, {"tma_pp", bfp::kRowsTmaPP},
       {"tma_h16", bfp::kRowsTmaH},    {"tma_h16pp", bfp::kRowsTmaHPP}, {"tc", bfp::kRowsTc},
       {"plain4", bfp::kRowsPlain4},   {"plain_l2", bfp::kRowsPlainL2}, {"plain4_l2", bfp::kRowsPlain4L2},
-      {"h16_l2", bfp::kRowsPlainHL2}, {"h16_4_l2", bfp::kRowsPlainH4L2}, {"h16s_4_l2", bfp::kRowsPlainHS4L2}};
+      {"h16_l2", bfp::kRowsPlainHL2}, {"h16_4_l2", bfp::kRowsPlainH4L2}, {"h16s_4_l2", bfp::kRowsPlainHS4L2},
+      {"twopass", bfp::kRowsTwoPass}};
   for (const auto& k : kNames)
     if (std::strcmp(v, k.name) == 0) return k.code;
   return bfp::kRowsTma;
@@ -340,6 +398,11 @@ struct bfpfft_plan_s {
   // Uneven plans (bfpfft_plan_create_many): owned device arrays.
   bool many = false;
   int tuned_clusters = 0;               // persistent clusters chosen by the tuner (0: all resident)
+  int long_twopass = 0;                 // lines of 32768 / 65536 points by the two-pass kernels (1) or in the
+                                        // persistent kernel's four-step lines (0)
+  int first_short_task = 0;             // first task of a length below 32768
+  long long long_first[2] = {0, 0};     // lines of 65536 / 32768 points: first index into d_line_off ...
+  long long long_count[2] = {0, 0};     // ... and count
   int kind = 0;                         // storage kind of the persistent kernel
   long long* d_line_off = nullptr;
   bfp::UnevenTask* d_tasks = nullptr;
@@ -408,6 +471,43 @@ int uneven_kind(int dtype) {
 
 }  // namespace
 
+// Lines of 2^log2n points (15 or 16) by the two-pass kernels: `lines` lines,
+// dense (line_off nullptr) or at line_off[0 .. lines).  The intermediate goes
+// through pool scratch in chunks whose footprint stays near 64 MB, so a chunk's
+// intermediate is still in L2 when the second pass reads it.
+static int run_twopass(int kind, int log2n, int mode, const void* in, void* out, const long long* line_off,
+                       long long lines, float in_scale, float out_scale, int* finite_flag, cudaStream_t s) {
+  if (lines <= 0) return BFPFFT_OK;
+  bfp::TwoPassArgs t{};
+  float2* tab = nullptr;
+  int st = get_twiddles(log2n - 8, &tab);
+  if (st != BFPFFT_OK) return st;
+  t.tw_col = tab;
+  if ((st = get_twiddles(8, &tab)) != BFPFFT_OK) return st;
+  t.tw_row = tab;
+  if ((st = get_twiddles(500 + log2n, &tab)) != BFPFFT_OK) return st;
+  t.tw_4step = tab;
+  long long chunk = (64ll << 20) / (long long)bfp::twopass_scratch_bytes(kind, 1, log2n);
+  if (const char* c = std::getenv("BFPFFT_TWOPASS_CHUNK")) chunk = std::max(1ll, std::atoll(c));
+  chunk = std::min(chunk, lines);
+  void* scratch = nullptr;
+  cudaError_t e = scratch_alloc(&scratch, bfp::twopass_scratch_bytes(kind, chunk, log2n), s);
+  if (e != cudaSuccess) return cuda_status(e);
+  t.in = in;
+  t.out = out;
+  t.scratch = scratch;
+  t.line_off = line_off;
+  t.lines = lines;
+  t.chunk_lines = chunk;
+  t.in_scale = in_scale;
+  t.out_scale = out_scale;
+  t.finite_flag = finite_flag;
+  t.pf_ahead = device_memory(in) ? 1 : 0;   // L2 prefetch one resident wave ahead (device memory only)
+  e = bfp::launch_twopass(kind, log2n, mode, t, s);
+  const cudaError_t f = cudaFreeAsync(scratch, s);
+  return cuda_status(e != cudaSuccess ? e : f);
+}
+
 extern "C" int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream);
 static int exec_many(bfpfft_plan plan, const void* in, void* out, cudaStream_t s) {
   bfp::UnevenArgs a{};
@@ -416,17 +516,37 @@ static int exec_many(bfpfft_plan plan, const void* in, void* out, cudaStream_t s
   a.line_off = plan->d_line_off;
   a.tasks = plan->d_tasks;
   a.num_tasks = plan->num_tasks;
+  const int variant = rows_variant();   // the _l2 row variants also prefetch the next task into L2
+  // BFPFFT_ROWS=twopass forces the split (tests); otherwise the tuner's choice.
+  const bool forced = std::getenv("BFPFFT_ROWS") != nullptr && variant == bfp::kRowsTwoPass;
+  if ((plan->long_twopass || forced) && plan->first_short_task > 0) {
+    // Long lines first, by the two-pass kernels; the persistent kernel then
+    // takes the tasks of the shorter lengths only.
+    const int mode = plan->direction == BFPFFT_INVERSE ? bfp::kInverse : bfp::kForward;
+    for (int c = 0; c < 2; ++c) {
+      const int l = 16 - c;
+      const float sc = float(1 << ((l + 1) / 2));    // FP8 block exponent of a uniform plan of this length
+      const bool fp8 = plan->kind >= 2;
+      const int st = run_twopass(plan->kind, l, mode, in, out, plan->d_line_off + plan->long_first[c],
+                                 plan->long_count[c], fp8 && mode == bfp::kInverse ? sc : 1.f,
+                                 fp8 && mode == bfp::kForward ? 1.f / sc : 1.f,
+                                 (plan->flags & BFPFFT_CHECK_FINITE) ? plan->status : nullptr, s);
+      if (st != BFPFFT_OK) return st;
+    }
+    a.tasks = plan->d_tasks + plan->first_short_task;
+    a.num_tasks = plan->num_tasks - plan->first_short_task;
+    if (a.num_tasks == 0) return BFPFFT_OK;
+  }
   a.tw = plan->d_tw;
   a.tw4 = plan->d_tw4;
   a.counter = plan->d_counter;
   a.status = plan->status;
   a.finite_flag = (plan->flags & BFPFFT_CHECK_FINITE) ? plan->status : nullptr;
-  const int variant = rows_variant();   // the _l2 row variants also prefetch the next task into L2
   a.prefetch = (variant == bfp::kRowsPlainL2 || variant == bfp::kRowsPlain4L2 || variant == bfp::kRowsPlainHL2 ||
-                variant == bfp::kRowsPlainH4L2 || variant == bfp::kRowsPlainHS4L2) &&
+                variant == bfp::kRowsPlainH4L2 || variant == bfp::kRowsPlainHS4L2 || variant == bfp::kRowsTwoPass) &&
                device_memory(in);
   const int want = plan->tuned_clusters > 0 ? plan->tuned_clusters : plan->clusters;
-  const int clusters = std::min(want, std::max(1, plan->num_tasks));
+  const int clusters = std::min(want, std::max(1, a.num_tasks));
   return cuda_status(bfp::launch_uneven(plan->kind, plan->direction == BFPFFT_INVERSE, a, clusters, s));
 }
 
@@ -557,8 +677,18 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
   const int saved_clusters = plan->tuned_clusters;
   if (!plan->many) plan->batch = sample_batch;
   std::vector<int> candidates;
+  const int saved_long = plan->long_twopass;
   if (plan->many) {
-    for (int c = plan->clusters; c >= 1 && candidates.size() < 4; c = c * 3 / 4) candidates.push_back(c);
+    // Uneven plans: the persistent cluster count, and whether lines of 32768 /
+    // 65536 points run as four-step lines inside the persistent kernel or as
+    // the two-pass kernels before it (code = clusters + 65536 * two-pass).
+    const bool has_long = plan->first_short_task > 0;
+    for (int c = plan->clusters; c >= 1 && candidates.size() < 8; c = c * 3 / 4) {
+      candidates.push_back(c);
+      if (has_long) candidates.push_back(c + 65536);
+    }
+  } else if (plan->log2n >= 15) {
+    candidates = {bfp::kRowsPlain4L2, bfp::kRowsTwoPass};
   } else {
     candidates = {bfp::kRowsPlain4L2, bfp::kRowsPlainL2, bfp::kRowsPlain, bfp::kRowsPlain4,
                   bfp::kRowsTma,        bfp::kRowsPlainPP, bfp::kRowsTmaPP};
@@ -576,7 +706,12 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
   int best = -1;
   float best_t = 1e30f;
   for (int c : candidates) {
-    if (plan->many) plan->tuned_clusters = c; else plan->variant = c;
+    if (plan->many) {
+      plan->tuned_clusters = c & 0xffff;
+      plan->long_twopass = c >> 16;
+    } else {
+      plan->variant = c;
+    }
     float ts[5];
     for (int r = 0; r < 7 && st == BFPFFT_OK; ++r) {
       cudaEventRecord(e0, nullptr);
@@ -593,13 +728,23 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
     }
   }
   plan->batch = saved_batch;
-  if (plan->many) plan->tuned_clusters = saved_clusters; else plan->variant = saved_variant;
+  if (plan->many) {
+    plan->tuned_clusters = saved_clusters;
+    plan->long_twopass = saved_long;
+  } else {
+    plan->variant = saved_variant;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(in);
   cudaFree(out);
   if (st != BFPFFT_OK) return st;
-  if (plan->many) plan->tuned_clusters = best; else plan->variant = best;
+  if (plan->many) {
+    plan->tuned_clusters = best & 0xffff;
+    plan->long_twopass = best >> 16;
+  } else {
+    plan->variant = best;
+  }
   *chosen = best;
   if (best_ms) *best_ms = best_t;
   std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -621,7 +766,12 @@ void tune_on_create(bfpfft_plan p) {
     tune_load_locked();
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      if (p->many) p->tuned_clusters = it->second.first; else p->variant = it->second.first;
+      if (p->many) {
+        p->tuned_clusters = it->second.first & 0xffff;
+        p->long_twopass = it->second.first >> 16;
+      } else {
+        p->variant = it->second.first;
+      }
       return;
     }
   }
@@ -736,6 +886,15 @@ int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, c
   p->many = true;
   p->kind = kind;
   p->num_tasks = int(tasks.size());
+  // Tasks are sorted longest first: lines of 65536 and 32768 points come first.
+  p->first_short_task = 0;
+  for (const auto& t : tasks) {
+    if (t.log2n < 15) break;
+    ++p->first_short_task;
+    const int c = 16 - t.log2n;
+    if (p->long_count[c] == 0) p->long_first[c] = t.first;
+    p->long_count[c] += t.count;
+  }
   int st = BFPFFT_OK;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) st = cuda_status(e);
@@ -812,6 +971,13 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
   if (!device_memory(in)) {
     a.variant = without_l2(a.variant);
     a.no_prefetch = 1;
+  }
+  if (plan->log2n >= 15 && a.variant == bfp::kRowsTwoPass && plan->dtype != BFPFFT_F16_NAIVE &&
+      plan->dtype != BFPFFT_BF16 && plan->dtype != BFPFFT_F16_ADAPTIVE) {
+    return run_twopass(uneven_kind(plan->dtype), plan->log2n,
+                       plan->direction == BFPFFT_FORWARD ? bfp::kForward : bfp::kInverse, in, out, nullptr,
+                       plan->batch, std::ldexp(1.0f, plan->in_exp), std::ldexp(1.0f, -plan->out_exp),
+                       a.finite_flag, static_cast<cudaStream_t>(stream));
   }
   if (plan->arith == BFPFFT_ARITH_F16_MUL_F32_ACC) a.variant = bfp::kRowsTc;
   if (plan->arith == BFPFFT_ARITH_F16 || plan->arith == BFPFFT_ARITH_BF16) {
@@ -1038,49 +1204,25 @@ int sar_make_filter(const void* ref, int64_t n, int peak_normalise, void* h_out,
   return cuda_status(cudaGetLastError());
 }
 
-// Corner turns of the SAR calls: "split" (default) compresses dense rows and
-// turns the result with a tiled transpose through stream-ordered scratch;
-// "fused" turns on chip through cluster distributed shared memory.
-// BFPFFT_SAR_TURN selects; the split form measured faster on GB300 (4096 x
-// 4096, FP16: 97 us against 120 us per compression).
-bool sar_split_turns() {
-  const char* v = std::getenv("BFPFFT_SAR_TURN");
-  return v == nullptr || std::strcmp(v, "fused") != 0;
-}
-
-// Stream-ordered scratch from a library-owned pool per device that keeps its
-// memory between calls (release threshold: never), so repeated calls neither
-// synchronise nor return memory to the driver.
-cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
-  static std::mutex mu;
-  static std::map<int, cudaMemPool_t> pools;
-  if (fault("alloc")) return cudaErrorMemoryAllocation;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  cudaMemPool_t pool;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    auto it = pools.find(dev);
-    if (it == pools.end()) {
-      cudaMemPoolProps props = {};
-      props.allocType = cudaMemAllocationTypePinned;
-      props.location.type = cudaMemLocationTypeDevice;
-      props.location.id = dev;
-      if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
-      uint64_t keep = UINT64_MAX;
-      if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
-      pools[dev] = pool;
-    } else {
-      pool = it->second;
-    }
-  }
-  return cudaMallocFromPoolAsync(p, bytes, pool, s);
-}
 
 int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype, const void* hr,
                        int64_t n_az, int64_t n_rg, int transpose_out, void* stream) {
+  return sar_range_compress_arith(raw, raw_dtype, out, out_dtype, hr, n_az, n_rg, transpose_out, BFPFFT_ARITH_F32,
+                                  stream);
+}
+
+// The compression lines of a SAR call: the FP32-arithmetic kernels, or with
+// BFPFFT_ARITH_F16 the FP16-arithmetic kernel (dense rows, FP16 output).
+static cudaError_t sar_lines(int l, int arith, bool in16, bool out16, bool naive, bool tload, bool tstore,
+                             const bfp::RowArgs& a, cudaStream_t s) {
+  if (arith == BFPFFT_ARITH_F16) return bfp::launch_rows16_compress_f16(l, !in16, naive, a, s);
+  return bfp::launch_sar(l, in16, out16, naive, tload, tstore, a, s);
+}
+
+int sar_range_compress_arith(const void* raw, int raw_dtype, void* out, int out_dtype, const void* hr,
+                             int64_t n_az, int64_t n_rg, int transpose_out, int arith, void* stream) {
   if (n_az < 0) return BFPFFT_ERR_INVALID_ARG;
+  if (arith != BFPFFT_ARITH_F32 && arith != BFPFFT_ARITH_F16) return BFPFFT_ERR_INVALID_ARG;
   const int l = log2_exact(n_rg);
   if (l < bfp::kSarMinLog2 || l > kSarMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
   if (n_az == 0) return BFPFFT_OK;
@@ -1089,15 +1231,20 @@ int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype,
   if (raw_dtype != BFPFFT_F32 && raw_dtype != BFPFFT_F16_BFP) return BFPFFT_ERR_UNSUPPORTED;
   if (out_dtype != BFPFFT_F32 && out_dtype != BFPFFT_F16_BFP && out_dtype != BFPFFT_F16_NAIVE)
     return BFPFFT_ERR_UNSUPPORTED;
+  if (arith == BFPFFT_ARITH_F16 && out_dtype == BFPFFT_F32) return BFPFFT_ERR_UNSUPPORTED;
   if (transpose_out != 0 && transpose_out != 1) return BFPFFT_ERR_INVALID_ARG;
   if (fault("launch")) return BFPFFT_ERR_CUDA;
   bfp::RowArgs a;
   int st = row_args(l, &a);
   if (st != BFPFFT_OK) return st;
+  if (arith == BFPFFT_ARITH_F16 && (st = get_twiddles16(l, false, &a.tw16)) != BFPFFT_OK) return st;
   a.in = raw;
   a.out = out;
   a.h = static_cast<const float2*>(hr);
-  if (!device_memory(raw)) a.variant = without_l2(a.variant);
+  if (!device_memory(raw)) {
+    a.variant = without_l2(a.variant);
+    a.no_prefetch = 1;
+  }
   a.lines = n_az;
   a.in_stride = n_rg;
   a.out_stride = transpose_out ? n_az : n_rg;
@@ -1105,7 +1252,7 @@ int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype,
   const bool in16 = raw_dtype == BFPFFT_F16_BFP;
   const bool out16 = out_dtype != BFPFFT_F32;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (transpose_out && sar_split_turns()) {
+  if (transpose_out && (sar_split_turns() || arith == BFPFFT_ARITH_F16)) {
     // Rows into scratch [n_az][n_rg], then turned into out [n_rg][n_az].
     const int eb = out16 ? 4 : 8;
     void* tmp = nullptr;
@@ -1113,18 +1260,25 @@ int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype,
     if (e != cudaSuccess) return cuda_status(e);
     a.out = tmp;
     a.out_stride = n_rg;
-    e = bfp::launch_sar(l, in16, out16, naive, false, false, a, s);
+    e = sar_lines(l, arith, in16, out16, naive, false, false, a, s);
     if (e == cudaSuccess) e = bfp::launch_transpose(tmp, out, n_az, n_rg, eb, s);
     const cudaError_t f = cudaFreeAsync(tmp, s);
     return cuda_status(e != cudaSuccess ? e : f);
   }
-  cudaError_t e = bfp::launch_sar(l, in16, out16, naive, /*tload=*/false, transpose_out != 0, a, s);
+  cudaError_t e = sar_lines(l, arith, in16, out16, naive, /*tload=*/false, transpose_out != 0, a, s);
   return cuda_status(e);
 }
 
 int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img, int img_dtype,
                          const void* ha, int64_t n_az, int64_t n_rg, void* stream) {
+  return sar_azimuth_compress_arith(rc, rc_dtype, rc_layout, img, img_dtype, ha, n_az, n_rg, BFPFFT_ARITH_F32,
+                                    stream);
+}
+
+int sar_azimuth_compress_arith(const void* rc, int rc_dtype, int rc_layout, void* img, int img_dtype,
+                               const void* ha, int64_t n_az, int64_t n_rg, int arith, void* stream) {
   if (n_rg < 0) return BFPFFT_ERR_INVALID_ARG;
+  if (arith != BFPFFT_ARITH_F32 && arith != BFPFFT_ARITH_F16) return BFPFFT_ERR_INVALID_ARG;
   const int l = log2_exact(n_az);
   if (l < bfp::kSarMinLog2 || l > kSarMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
   if (n_rg == 0) return BFPFFT_OK;
@@ -1133,22 +1287,28 @@ int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img,
   if (rc_dtype != BFPFFT_F32 && rc_dtype != BFPFFT_F16_BFP) return BFPFFT_ERR_UNSUPPORTED;
   if (img_dtype != BFPFFT_F32 && img_dtype != BFPFFT_F16_BFP && img_dtype != BFPFFT_F16_NAIVE)
     return BFPFFT_ERR_UNSUPPORTED;
+  if (arith == BFPFFT_ARITH_F16 && (img_dtype == BFPFFT_F32 || rc_dtype != BFPFFT_F16_BFP))
+    return BFPFFT_ERR_UNSUPPORTED;
   if (rc_layout != 0 && rc_layout != 1) return BFPFFT_ERR_INVALID_ARG;
   if (fault("launch")) return BFPFFT_ERR_CUDA;
   bfp::RowArgs a;
   int st = row_args(l, &a);
   if (st != BFPFFT_OK) return st;
+  if (arith == BFPFFT_ARITH_F16 && (st = get_twiddles16(l, false, &a.tw16)) != BFPFFT_OK) return st;
   a.in = rc;
   a.out = img;
   a.h = static_cast<const float2*>(ha);
-  if (!device_memory(rc)) a.variant = without_l2(a.variant);
+  if (!device_memory(rc)) {
+    a.variant = without_l2(a.variant);
+    a.no_prefetch = 1;
+  }
   a.lines = n_rg;                                   // one line per range column
   a.in_stride = rc_layout == 0 ? n_rg : n_az;       // [n_az][n_rg] column vs [n_rg][n_az] row
   a.out_stride = n_rg;                              // image is [n_az][n_rg]
   const bool naive = img_dtype == BFPFFT_F16_NAIVE;
   const bool in16 = rc_dtype == BFPFFT_F16_BFP, out16 = img_dtype != BFPFFT_F32;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (sar_split_turns()) {
+  if (sar_split_turns() || arith == BFPFFT_ARITH_F16) {
     // Layout 0 is first turned to [n_rg][n_az]; the azimuth lines are then
     // dense rows, compressed into scratch and turned into img [n_az][n_rg].
     const size_t pts = size_t(n_az) * size_t(n_rg);
@@ -1164,7 +1324,7 @@ int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img,
       a.in_stride = n_az;
       a.out = rows_out;
       a.out_stride = n_az;
-      e = bfp::launch_sar(l, in16, out16, naive, false, false, a, s);
+      e = sar_lines(l, arith, in16, out16, naive, false, false, a, s);
     }
     if (e == cudaSuccess) e = bfp::launch_transpose(rows_out, img, n_rg, n_az, ob, s);
     cudaError_t f = cudaSuccess;

@@ -188,3 +188,41 @@ def test_autograd_function_and_refocus():
     m_bad = metrics.point_target_metrics(AF.image(u, np.zeros(n_az), ha), t, guard=8)[0]
     assert m_fix["peak"] > 0.95 * m_true["peak"]
     assert m_true["peak"] > 1.3 * m_bad["peak"]
+
+
+def test_config5_refocus_after_50_steps(config5):
+    """Config 5 end to end: 50 Adam steps (lr 0.05, phi_0 = 0) through the
+    torch.autograd.Function on the FP16-BFP 4096 x 4096 scene, then the
+    refocused image (FP64 oracle) against the error-free image.
+
+    The entropy must close at least 90 % of the gap between the defocused
+    image and the true phase correction, and the brightest target's PSLR must
+    come within 1 dB of the error-free image's (its 3 dB azimuth width within
+    0.1 cell).  Weaker targets whose apertures no brighter target shares stay
+    above their error-free PSLR after 50 steps (the image entropy is dominated
+    by the bright targets); their PSLRs are reported, not bounded."""
+    import torch
+    sc, u, ha, eps = config5
+    n = u.shape[0]
+    rc = to_device(np.ascontiguousarray(storage_round(u, B.F16_BFP).T), B.F16_BFP)
+    ha_d = to_device(ha, B.F32)
+    ws = GA.Workspace(n, "cuda:0")
+    phi = torch.zeros(n, dtype=torch.float32, device="cuda:0", requires_grad=True)
+    e0 = GA.entropy(phi, rc, ha_d, B.F16_BFP, ws).item()
+    opt = torch.optim.Adam([phi], lr=0.05)
+    for _ in range(50):
+        opt.zero_grad()
+        e = GA.entropy(phi, rc, ha_d, B.F16_BFP, ws)
+        e.backward()
+        opt.step()
+    e50 = GA.entropy(phi, rc, ha_d, B.F16_BFP, ws).item()
+    e_true = AF.entropy(u, eps, ha)
+    assert (e0 - e50) >= 0.9 * (e0 - e_true), (e0, e50, e_true)
+    phi_h = phi.detach().cpu().numpy().astype(np.float64)
+    m_fix = metrics.point_target_metrics(AF.image(u, phi_h, ha), sc.targets)
+    m_true = metrics.point_target_metrics(AF.image(u, eps, ha), sc.targets)
+    b = int(np.argmax([a for _, _, a in sc.targets]))
+    assert abs(m_fix[b]["pslr_db"] - m_true[b]["pslr_db"]) <= 1.0, (m_fix[b]["pslr_db"], m_true[b]["pslr_db"])
+    assert abs(m_fix[b]["width_azimuth_cells"] - m_true[b]["width_azimuth_cells"]) <= 0.1
+    print("refocused PSLR", [round(m["pslr_db"], 2) for m in m_fix], "error-free",
+          [round(m["pslr_db"], 2) for m in m_true])

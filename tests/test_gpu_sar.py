@@ -231,3 +231,81 @@ def test_config3_full_size_image_against_fp64(config3_reference, dtype, sar_turn
             assert abs(a[k] - b[k]) <= 0.1, (k, a[k], b[k])
         for k in ("width_range_cells", "width_azimuth_cells"):
             assert abs(a[k] - b[k]) <= 0.1, (k, a[k], b[k])
+
+
+@pytest.mark.parametrize("n_rg", [256, 4096, 16384])
+@pytest.mark.parametrize("transpose", [False, True])
+@pytest.mark.parametrize("raw_dtype", [B.F32, B.F16_BFP])
+def test_pure_fp16_range_compression(n_rg, transpose, raw_dtype):
+    """Section VI's pure FP16 mode (sar_range_compress_arith, BFPFFT_ARITH_F16):
+    every transform and the filter product in FP16 arithmetic; SQNR against the
+    FP64 oracle of the same stored inputs >= 50 dB per call (two transforms and
+    a product, each rounding every operation to FP16)."""
+    import torch
+    n_az = 45
+    sc = synth.point_target_scene(n_az, n_rg, aperture=16, targets=[(n_az // 2, n_rg // 2, 1.0)],
+                                  noise_seed=n_az + n_rg)
+    ref_r = synth.centred_reference(synth.range_chirp()[: min(480, n_rg // 2)], n_rg)
+    hr, hr64 = oracle_filter(ref_r, False)
+    raw = storage_round(sc.raw, raw_dtype)
+    out = empty_like_storage((n_rg, n_az) if transpose else (n_az, n_rg), B.F16_BFP)
+    B.sar_range_compress_arith(to_device(raw, raw_dtype), raw_dtype, out, B.F16_BFP, hr, n_az, n_rg, transpose,
+                               B.ARITH_F16)
+    torch.cuda.synchronize()
+    got = from_device(out, B.F16_BFP)
+    if transpose:
+        got = got.T
+    # the kernel rounds a complex64 echo to FP16 on load: the oracle takes the same values
+    expect = sar.range_compress(storage_round(raw, B.F16_BFP), hr64)
+    assert metrics.sqnr_db(expect, got) >= 50.0
+
+
+def test_pure_fp16_naive_range_compression_overflows():
+    sc = synth.point_target_scene(1024, 4096)
+    raw = storage_round(sc.raw, B.F32)
+    hr, _ = oracle_filter(sc.ref_range, False)
+    import torch
+    out = empty_like_storage((1024, 4096), B.F16_BFP)
+    B.sar_range_compress_arith(to_device(raw, B.F32), B.F32, out, B.F16_NAIVE, hr, 1024, 4096, False, B.ARITH_F16)
+    torch.cuda.synchronize()
+    assert not np.all(np.isfinite(from_device(out, B.F16_BFP)))
+
+
+def test_config3_pure_fp16_image_against_fp64(config3_reference):
+    """Config 3 at full size in the pure FP16 mode (Table III: the paper's pure
+    FP16 image keeps PSLR / SNR within 0.1 dB of FP32): SQNR >= 40 dB over the
+    whole image, per target |dPSLR|, |dISLR|, |dSNR| <= 0.1 dB, |dwidth| <= 0.1
+    cell against the FP64 image, same peak cell."""
+    import torch
+    sc, raw, hr, ha, img_ref, m_ref = config3_reference
+    n = raw.shape[0]
+    rc = empty_like_storage((n, n), B.F16_BFP)
+    img = empty_like_storage((n, n), B.F16_BFP)
+    B.sar_range_compress_arith(to_device(raw, B.F32), B.F32, rc, B.F16_BFP, hr, n, n, True, B.ARITH_F16)
+    B.sar_azimuth_compress_arith(rc, B.F16_BFP, 1, img, B.F16_BFP, ha, n, n, B.ARITH_F16)
+    torch.cuda.synchronize()
+    got = from_device(img, B.F16_BFP)
+    assert np.all(np.isfinite(got))
+    assert metrics.sqnr_db(img_ref, got) >= 40.0
+    m16 = metrics.point_target_metrics(got, sc.targets)
+    for a, b in zip(m_ref, m16):
+        assert a["peak_cell"] == b["peak_cell"]
+        for k in ("pslr_range_db", "pslr_azimuth_db", "islr_range_db", "islr_azimuth_db", "snr_db"):
+            assert abs(a[k] - b[k]) <= 0.1, (k, a[k], b[k])
+        for k in ("width_range_cells", "width_azimuth_cells"):
+            assert abs(a[k] - b[k]) <= 0.1, (k, a[k], b[k])
+
+
+def test_arith_argument_checks():
+    import torch
+    x = torch.zeros((8, 4096), dtype=torch.complex64, device="cuda:0")
+    h = torch.zeros(4096, dtype=torch.complex64, device="cuda:0")
+    with pytest.raises(B.BfpfftError) as e:
+        B.sar_range_compress_arith(x, B.F32, x, B.F32, h, 8, 4096, False, B.ARITH_F16)   # FP32 out
+    assert e.value.status == B.ERR_UNSUPPORTED
+    with pytest.raises(B.BfpfftError) as e:
+        B.sar_range_compress_arith(x, B.F32, x, B.F16_BFP, h, 8, 4096, False, 7)
+    assert e.value.status == B.ERR_INVALID_ARG
+    with pytest.raises(B.BfpfftError) as e:
+        B.sar_azimuth_compress_arith(x, B.F32, 1, x, B.F16_BFP, h, 4096, 8, B.ARITH_F16)   # FP32 rc
+    assert e.value.status == B.ERR_UNSUPPORTED

@@ -50,9 +50,31 @@ def run_many(data, lengths, offsets, dtype, direction, graph=False, reps=1):
 MIXED = [65536, 16, 4096, 256, 16384, 1024, 8192, 32, 4096, 32768, 512, 2048, 64, 128, 65536, 256, 4096] * 2
 
 
+@pytest.fixture(params=["fourstep", "twopass"])
+def long_lines(request, monkeypatch):
+    """Lines of 32768 / 65536 points inside the persistent kernel (four-step) or
+    split off to the two-pass kernels (BFPFFT_ROWS=twopass forces the split)."""
+    if request.param == "twopass":
+        monkeypatch.setenv("BFPFFT_ROWS", "twopass")
+    else:
+        monkeypatch.delenv("BFPFFT_ROWS", raising=False)
+    return request.param
+
+
+def fp16_line_ok(g, ref, n, long_lines):
+    """FP16 parity of one line; the two-pass intermediate is one more FP16
+    storage point (the FP16-exchange bound of the uniform row tests)."""
+    if long_lines == "twopass" and n >= 32768:
+        rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+        bound = 2.0 ** -11 * (np.abs(ref) + 6.0 * rms)
+        return (np.all(np.abs(g.real - ref.real) <= bound) and np.all(np.abs(g.imag - ref.imag) <= bound)
+                and metrics.sqnr_db(ref, g) >= 55.0), None
+    return fp16_elementwise_ok(g, ref)
+
+
 @pytest.mark.parametrize("direction", [B.FORWARD, B.INVERSE])
 @pytest.mark.parametrize("dtype", [B.F32, B.F16_BFP])
-def test_mixed_lengths_every_line(dtype, direction):
+def test_mixed_lengths_every_line(dtype, direction, long_lines):
     lengths = np.array(MIXED)
     data, offsets = packed(lengths, dtype, seed=31)
     got, plan = run_many(data, lengths, offsets, dtype, direction)
@@ -65,12 +87,12 @@ def test_mixed_lengths_every_line(dtype, direction):
         if dtype == B.F32:
             assert metrics.rel_l2(ref, g) <= 1e-6, n
         else:
-            ok, worst = fp16_elementwise_ok(g, ref)
+            ok, worst = fp16_line_ok(g, ref, n, long_lines)
             assert ok, (n, worst)
 
 
 @pytest.mark.parametrize("dtype,fmt", [(B.E4M3_BFP, "e4m3"), (B.E5M2_BFP, "e5m2")])
-def test_fp8_mixed_lengths(dtype, fmt):
+def test_fp8_mixed_lengths(dtype, fmt, long_lines):
     lengths = np.array([4096, 256, 65536, 1024, 16384, 4096])
     data, offsets = packed(lengths, dtype, seed=32)
     got, _ = run_many(data, lengths, offsets, dtype, B.FORWARD)
@@ -80,7 +102,7 @@ def test_fp8_mixed_lengths(dtype, fmt):
         fp8_close(got[o:o + n], exact, fmt)
 
 
-def test_graph_replay_matches_direct_launch():
+def test_graph_replay_matches_direct_launch(long_lines):
     lengths = np.array(MIXED)
     data, offsets = packed(lengths, B.F16_BFP, seed=33)
     direct, _ = run_many(data, lengths, offsets, B.F16_BFP, B.FORWARD)
@@ -102,9 +124,10 @@ def test_uneven_plan_rejects_bad_lengths():
     assert e.value.status == B.ERR_UNSUPPORTED
 
 
-def test_config4_full_size_sampled_lines():
+def test_config4_full_size_sampled_lines(long_lines):
     """20,000 transforms, lengths from {256, 1024, 4096, 16384, 65536} with Zipf
-    weights (seed 3), FP16-BFP, one persistent launch through a CUDA graph."""
+    weights (seed 3), FP16-BFP, one persistent launch through a CUDA graph (with
+    the two-pass split: the two-pass kernels, then the persistent launch)."""
     import torch
     lengths = synth.uneven_lengths(20000, seed=3)
     offsets = np.zeros_like(lengths)
@@ -125,7 +148,7 @@ def test_config4_full_size_sampled_lines():
             o = int(offsets[i])
             xs = from_device(x[o:o + n], B.F16_BFP)
             ys = from_device(y[o:o + n], B.F16_BFP)
-            ok, worst = fp16_elementwise_ok(ys, F.fft(xs))
+            ok, worst = fp16_line_ok(ys, F.fft(xs), n, long_lines)
             assert ok, (n, worst)
 
 
@@ -151,8 +174,22 @@ def test_tuner_uniform_and_uneven(tmp_path, monkeypatch):
     lengths = np.array(MIXED)
     data, offsets = packed(lengths, B.F16_BFP, seed=34)
     many = B.bfpfft_plan_create_many(lengths, offsets, B.F16_BFP, B.FORWARD)
-    clusters, _ = B.bfpfft_plan_tune(many)
-    assert 1 <= clusters <= B.bfpfft_plan_info(many)[1]
+    code, _ = B.bfpfft_plan_tune(many)          # clusters + 65536 * (long lines by the two-pass kernels)
+    assert 1 <= (code & 0xffff) <= B.bfpfft_plan_info(many)[1] and (code >> 16) in (0, 1)
+    got, _ = run_many(data, lengths, offsets, B.F16_BFP, B.FORWARD)
+    tuned = B.bfpfft_plan_create_many(lengths, offsets, B.F16_BFP, B.FORWARD)
+    B.bfpfft_plan_tune(tuned)
+    x_many = to_device(data, B.F16_BFP)
+    y_many = torch.empty_like(x_many)
+    B.bfpfft_exec(tuned, x_many, y_many)
+    torch.cuda.synchronize()
+    out = from_device(y_many, B.F16_BFP)
+    for n, o in zip(lengths, offsets):
+        ok, worst = fp16_line_ok(out[o:o + n], F.fft(data[o:o + n]), n, "twopass" if code >> 16 else "fourstep")
+        assert ok, (n, worst)
+    long_plan = B.bfpfft_plan_create(65536, 8, B.F16_BFP, B.FORWARD)
+    chosen_long, _ = B.bfpfft_plan_tune(long_plan)
+    assert chosen_long in (11, 15)                # the four-step kernel or the two-pass kernels
     monkeypatch.setenv("BFPFFT_TUNE", "cached")
     again = B.bfpfft_plan_create(4096, 512, B.F16_BFP, B.FORWARD)
     B.bfpfft_exec(again, xin, y)
