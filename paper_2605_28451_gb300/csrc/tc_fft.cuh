@@ -21,9 +21,11 @@
 // storage point, so the inverse relies on the 1/N shift (Eq. 1) like the
 // paper's half2 kernel.
 //
-// Rows: butterfly j of pass p sits in A/D row rho_p(j); thread tau (TMEM lane
-// tau % 128 of tile tau / 128) handles the butterfly in row tau.  rho_p keep
-// every shared-memory store of the producer free of bank conflicts (below).
+// Rows: butterfly j of pass p sits in A/D row rho_p(j); thread tau < 128
+// (TMEM lane tau) handles the butterflies in rows tau and 128 + tau, one per
+// M tile.  rho_p keep every shared-memory store of the producer free of bank
+// conflicts (below).  Eight 128-thread CTAs share an SM, so that while one
+// waits for its MMAs the others load, twiddle and store.
 //
 // Waits are bounded; on expiry the CTA records a timeout, waits (bounded) for
 // its last commit, frees its tensor memory and returns.
@@ -40,12 +42,21 @@ namespace tc {
 
 constexpr int kN = 4096;
 constexpr int kB = 256;              // butterflies per pass
+constexpr int kThreads = 128;        // one per TMEM lane; each owns the lane in both M tiles
 constexpr int kLbo = 128;            // bytes between K-adjacent core matrices
 constexpr int kSbo = 512;            // bytes between 8-row groups (4 core matrices of K = 32)
 constexpr int kABytes = kB * 64;     // 256 rows x 32 FP16
 constexpr int kBBytes = 32 * 64;     // 32 rows x 32 FP16
-constexpr int kSmemBytes = kABytes + kBBytes + 16;
+constexpr int kLineBytes = kN * 4;   // one FP16 line
 constexpr uint32_t kTmemCols = 64;   // two 128 x 32 FP32 accumulators
+constexpr int kCtasPerSm = 8;        // 64 registers, 64 TMEM columns, 26 KB of shared memory each
+constexpr int kTwPitch = 18;         // twiddle rows in shared memory: 18 entries (144 B) apart
+constexpr int kTwBytes = 2 * 16 * kTwPitch * 8;
+// Shared memory: A | 3 B matrices | twiddle rows | mbarrier | TMEM slot.
+constexpr int kBOff = kABytes;
+constexpr int kTwOff = kBOff + 3 * kBBytes;
+constexpr int kBarOff = (kTwOff + kTwBytes + 15) / 16 * 16;
+constexpr int kSmemBytes = kBarOff + 16;
 
 // K-major canonical layout without swizzle: byte offset of element (row, k).
 __host__ __device__ constexpr int kmaj(int row, int k) {
@@ -59,7 +70,7 @@ __host__ __device__ constexpr int kmaj(int row, int k) {
 //   P = 0: row bits = j bits (0, 1, 2, 4, 5, 3, 6, 7)
 //   P = 1: row bits = (j4, j5, j6 ^ j0, j1, j2, j3, j6, j7)
 //   P = 2: identity (the last pass stores X[j + 256 q] coalesced)
-// and the pass-0 loads visit the k-pairs in a lane-rotated order.
+// The pass-0 inputs go in as 16-byte stores, four k-pairs of one row each.
 __device__ __forceinline__ int bit(int x, int b) { return (x >> b) & 1; }
 
 template <int P>
@@ -85,6 +96,14 @@ __device__ __forceinline__ int butterfly_of(int r) {
   } else {
     return r;
   }
+}
+
+// A line's input read once: no L1 allocation (volatile keeps it ordered with
+// the in-place stores).
+__device__ __forceinline__ uint32_t ld_once_b32(const void* p) {
+  uint32_t r;
+  asm volatile("ld.global.L1::no_allocate.b32 %0, [%1];" : "=r"(r) : "l"(p));
+  return r;
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
@@ -129,19 +148,21 @@ __device__ __forceinline__ void ld32(uint32_t taddr, uint32_t (&r)[32]) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void store_pair(unsigned char* sA, int row, int r, float2 v) {
-  *reinterpret_cast<__half2*>(sA + kmaj(row, 2 * r)) = __float22half2_rn(v);
-}
-
 }  // namespace tc
 
 // One radix-16 pass: MMA on the current A tile, then the D rows go either
-// (P < 2) twiddled into the next A tile or (P == 2) to HBM.  Returns false
+// (P < 2) twiddled into the next A tile or (P == 2) to HBM.  Each thread owns
+// TMEM lane tid of both M tiles (A/D rows tid and 128 + tid).  Returns false
 // when the completion wait expired (all threads agree).
-template <int P, class TS, int MODE>
+//
+// Store addresses are a per-thread base plus a compile-time offset per q
+// (t = j mod 16, rn = j / 16 for butterfly j; the pass-1 row map splits into
+// the thread's bits and q's bits except row bit 2 = t2 ^ q0, hence the two
+// bases for even and odd q).
+template <int P, int MODE>
 __device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsigned char* sA, uint64_t* bar,
-                                        uint32_t tmem, uint32_t my_tmem, uint32_t a_base, uint32_t b_base,
-                                        uint32_t& phase) {
+                                        uint32_t tmem, uint32_t lane_tmem, uint32_t a_base, uint32_t b_base,
+                                        uint32_t& phase, const float2* s_tw) {
   using namespace tc;
   const int tid = threadIdx.x;
   fence_proxy_async_shared();
@@ -161,50 +182,107 @@ __device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsign
   if (__syncthreads_or(!arrived)) return false;
   phase ^= 1;
   fence_after();
-  uint32_t d[32];
-  tc::ld32(my_tmem, d);
-  const int j = tc::butterfly_of<P>(tid);
-  if constexpr (P < 2) {
-    constexpr int kLogNs = 4 * P;                      // sub-length 16^P of this pass
-    constexpr int kNs2 = 16 << kLogNs;                 // sub-length of the next pass
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int i = ((j >> kLogNs) << (kLogNs + 4)) + (j & ((1 << kLogNs) - 1)) + (q << kLogNs);
-      const int jn = i & 255, rn = i >> 8;
-      float2 y = make_float2(__uint_as_float(d[2 * q]), __uint_as_float(d[2 * q + 1]));
-      if (rn > 0) y = cmul(y, __ldg(a.tw + (kNs2 - 16) + (rn - 1) * kNs2 + (jn & (kNs2 - 1))));
-      tc::store_pair(sA, tc::row_of<P + 1>(jn), rn, y);
-    }
-  } else {
-    TS* out = static_cast<TS*>(a.out) + line * a.out_stride + j;
+  for (int h = 0; h < 2; ++h) {
+    uint32_t d[32];
+    tc::ld32(lane_tmem + uint32_t(32 * h), d);
+    const int rho = tid + 128 * h;
+    const int j = tc::butterfly_of<P>(rho);
+    if constexpr (P < 2) {
+      const int t = j & 15, rn = j >> 4;
+      const int rn_off = (rn >> 2) * kLbo + (rn & 3) * 4;
+      int base_even, base_odd;
+      const float2* tw_row = s_tw + rn * kTwPitch;       // W_256^{rn q}, q < 16 (rn = 0: ones)
+      if constexpr (P == 0) {
+        // Twiddles W_256^{rn q} from the shared-memory table: rows 144 B
+        // apart put the four rn of a warp in four different 16-byte bank
+        // groups; one 16-byte load fetches q and q + 1.
+        const int t2 = (t >> 2) & 1;
+        base_even = 16 * (t & 3) + 4160 * t2 + 8192 * (t >> 3) + rn_off;
+        base_odd = base_even + 64 - 128 * t2;
+        const float4* tw2 = reinterpret_cast<const float4*>(tw_row);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      float2 y = make_float2(__uint_as_float(d[2 * q]), __uint_as_float(d[2 * q + 1]));
-      if (MODE == kInverse) y = cconj(y);
-      Storage<TS>::store(out + 256 * q, y);
+        for (int q2 = 0; q2 < 8; ++q2) {
+          const float4 wp = tw2[q2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int q = 2 * q2 + e;
+            const float2 w = e ? make_float2(wp.z, wp.w) : make_float2(wp.x, wp.y);
+            const float2 y = cmul(make_float2(__uint_as_float(d[2 * q]), __uint_as_float(d[2 * q + 1])), w);
+            *reinterpret_cast<__half2*>(sA + (q & 1 ? base_odd : base_even) + 512 * (q >> 1)) =
+                __float22half2_rn(y);
+          }
+        }
+      } else {
+        // Twiddles W_4096^{rn (t + 16 q)}: the geometric sequence from
+        // W_4096^{rn t} with ratio W_256^{rn}, both read once (the sequence's
+        // FP32 rounding, about 1e-6 after 15 steps, is far below the FP16
+        // rounding of the operands it scales).
+        base_even = 512 * (t >> 3) + 16 * (t & 7) + rn_off;
+        float2 w = s_tw[(16 + rn) * kTwPitch + t];
+        const float2 ratio = tw_row[1];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float2 y = cmul(make_float2(__uint_as_float(d[2 * q]), __uint_as_float(d[2 * q + 1])), w);
+          *reinterpret_cast<__half2*>(sA + base_even + 1024 * q) = __float22half2_rn(y);
+          if (q < 15) w = cmul(w, ratio);
+        }
+      }
+    } else {
+      // The inverse's final conjugation is folded into the last pass's matrix.
+      __half2* out = static_cast<__half2*>(a.out) + line * a.out_stride + rho;
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        out[256 * q] = __float22half2_rn(make_float2(__uint_as_float(d[2 * q]), __uint_as_float(d[2 * q + 1])));
+      check_finite<Storage<__half2>, 16>(a.finite_flag, [&](int m) {
+        return make_float2(__uint_as_float(d[2 * m]), __uint_as_float(d[2 * m + 1]));
+      });
     }
-    check_finite<Storage<TS>, 16>(a.finite_flag, [&](int m) {
-      return make_float2(__uint_as_float(d[2 * m]), __uint_as_float(d[2 * m + 1]));
-    });
   }
   fence_before();
   return true;
 }
 
-template <class TS, int MODE>
-__global__ void __launch_bounds__(256, 3) fft_tc_kernel(const RowArgs a) {
+// 128 threads per CTA, eight CTAs per SM: eight lines in flight per SM (the
+// TMEM limit at 64 columns a line) while each CTA's passes run one after
+// another.  Persistent: CTA b takes lines b, b + grid, ...; thread 0 bulk-
+// prefetches the CTA's next line into L2.
+template <int MODE>
+__global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(const RowArgs a) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* sA = smem_tc;
-  unsigned char* sB = smem_tc + kABytes;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_tc + kABytes + kBBytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_tc + kABytes + kBBytes + 8);
+  unsigned char* sB = smem_tc + kBOff;
+  float2* s_tw = reinterpret_cast<float2*>(smem_tc + kTwOff);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_tc + kBarOff);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_tc + kBarOff + 8);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const float inv_n = 1.0f / float(kN);
+  const __half2* in_lines = static_cast<const __half2*>(a.in);
 
-  // DFT-16 matrix in real form (prepared on the host in FP16, [n][k]).
+  // DFT-16 matrix in real form (prepared on the host in FP16, [n][k]) and two
+  // derived copies for the inverse (Eq. 1 as conj(DFT(conj(x) / N))):
+  //   B_last  = B with the imaginary output rows n = 2 q + 1 negated (the
+  //             final conjugation);
+  //   B_first = B / N with the imaginary input columns k = 2 r + 1 negated
+  //             (the conjugated, 1/N-shifted input; N = 2^12 keeps every
+  //             coefficient normal in FP16, so the scaling is exact).
   const __half* b_src = static_cast<const __half*>(a.tc_b);
-  for (int i = tid; i < 32 * 32; i += 256) *reinterpret_cast<__half*>(sB + kmaj(i / 32, i % 32)) = b_src[i];
+  for (int i = tid; i < 32 * 32; i += kThreads) {
+    const int n = i / 32, k = i % 32;
+    const __half v = b_src[i];
+    *reinterpret_cast<__half*>(sB + kmaj(n, k)) = v;
+    *reinterpret_cast<__half*>(sB + kBBytes + kmaj(n, k)) = (n & 1) ? __hneg(v) : v;
+    const __half vs = __float2half_rn(__half2float(v) * (1.0f / float(kN)));
+    *reinterpret_cast<__half*>(sB + 2 * kBBytes + kmaj(n, k)) = (k & 1) ? __hneg(vs) : vs;
+  }
+  // Twiddle rows from the pass-major table: [rn][q] = W_256^{rn q} (entry
+  // 16 (rn - 1) + q) and [16 + rn][t] = W_4096^{rn t} (entry
+  // 240 + 256 (rn - 1) + t), rn = 1..15, q, t < 16; the rows rn = 0 are ones.
+  for (int i = tid; i < 2 * 256; i += kThreads) {
+    const int tab = i / 256, rn = (i % 256) / 16, c = i % 16;
+    s_tw[(16 * tab + rn) * kTwPitch + c] =
+        rn == 0 ? make_float2(1.0f, 0.0f) : a.tw[tab == 0 ? 16 * (rn - 1) + c : 240 + 256 * (rn - 1) + c];
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
                  "r"(kTmemCols));
@@ -217,28 +295,36 @@ __global__ void __launch_bounds__(256, 3) fft_tc_kernel(const RowArgs a) {
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t my_tmem = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(32 * (warp >> 2));
+  const uint32_t lane_tmem = tmem + (uint32_t(32 * warp) << 16);
   const uint32_t a_base = smem_addr(sA), b_base = smem_addr(sB);
+  const uint32_t b_first = MODE == kInverse ? b_base + 2 * kBBytes : b_base;
+  const uint32_t b_last = MODE == kInverse ? b_base + kBBytes : b_base;
   uint32_t phase = 0;
   bool ok = true;
 
   for (long long line = blockIdx.x; ok && line < a.lines; line += gridDim.x) {
-    if (a.pf_ahead > 0 && tid == 0 && line + gridDim.x < a.lines)   // next iteration's line, into L2
-      prefetch_l2_bulk(static_cast<const TS*>(a.in) + (line + gridDim.x) * a.in_stride, uint32_t(kN * sizeof(TS)));
-    // Pass-0 inputs: butterfly j = tid takes x[j + 256 r]; coalesced loads.
-    const TS* in = static_cast<const TS*>(a.in) + line * a.in_stride + tid;
-    const int row = tc::row_of<0>(tid);
-    const int rot = (tid >> 3) & 3;                     // lane-rotated k-pair order
+    const long long next = line + gridDim.x;
+    if (a.pf_ahead > 0 && tid == 0 && next < a.lines)   // next iteration's line, into L2
+      prefetch_l2_bulk(in_lines + next * a.in_stride, uint32_t(kLineBytes));
+    // Pass-0 inputs: butterfly j takes x[j + 256 r]; its row of A is four
+    // 16-byte core-matrix rows, one st.shared.v4 per four points (the eight
+    // lanes of a quarter-warp have distinct row % 8).
+    const __half2* in = in_lines + line * a.in_stride + tid;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int r = (m + rot) & 15;
-      float2 x = Storage<TS>::load(in + 256 * r);
-      if (MODE == kInverse) x = cscale(cconj(x), inv_n);
-      tc::store_pair(sA, row, r, x);
+    for (int h = 0; h < 2; ++h) {
+      const int j = tid + 128 * h;
+      uint32_t x[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) x[r] = ld_once_b32(in + 128 * h + 256 * r);
+      const int row = tc::row_of<0>(j);
+      unsigned char* dst = sA + (row >> 3) * kSbo + (row & 7) * 16;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        *reinterpret_cast<uint4*>(dst + c * kLbo) = make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
     }
-    ok = tc_pass<0, TS, MODE>(a, line, sA, bar, tmem, my_tmem, a_base, b_base, phase) &&
-         tc_pass<1, TS, MODE>(a, line, sA, bar, tmem, my_tmem, a_base, b_base, phase) &&
-         tc_pass<2, TS, MODE>(a, line, sA, bar, tmem, my_tmem, a_base, b_base, phase);
+    ok = tc_pass<0, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_first, phase, s_tw) &&
+         tc_pass<1, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_base, phase, s_tw) &&
+         tc_pass<2, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_last, phase, s_tw);
   }
   // A wait that expired leaves `phase` at the commit it was waiting for:
   // give that commit one more bounded wait before the tensor memory goes.
@@ -252,27 +338,27 @@ __global__ void __launch_bounds__(256, 3) fft_tc_kernel(const RowArgs a) {
 
 template <class TS, int MODE>
 cudaError_t launch_tc_n(const RowArgs& a, cudaStream_t stream) {
-  auto kern = fft_tc_kernel<TS, MODE>;
-  // Three CTAs per SM: the register limit of __launch_bounds__(256, 3);
-  // tensor memory would allow eight (64 of 512 columns each), so the
-  // persistent CTAs never wait on each other's allocation.  Computed once,
+  static_assert(sizeof(TS) == sizeof(__half2), "the tensor-core rows take FP16 storage");
+  auto kern = fft_tc_kernel<MODE>;
+  // kCtasPerSm CTAs per SM: the register limit of __launch_bounds__; tensor
+  // memory holds exactly that many 64-column allocations, so the persistent
+  // CTAs never wait on each other's allocation.  Computed once,
   // thread-safely (function-local static).
   static const LaunchSetup setup = []() -> LaunchSetup {
     LaunchSetup r{cudaSuccess, 0};
     int dev = 0, sms = 0;
     if ((r.err = cudaGetDevice(&dev)) != cudaSuccess) return r;
     if ((r.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return r;
-    r.resident = 3 * sms;
+    r.resident = tc::kCtasPerSm * sms;
     return r;
   }();
   if (setup.err != cudaSuccess) return setup.err;
-  const int grid_cap = setup.resident;
   (void)kern;
   if (a.lines <= 0) return cudaSuccess;
-  const int grid = int(a.lines < grid_cap ? a.lines : grid_cap);
+  const int grid = int(a.lines < setup.resident ? a.lines : setup.resident);
   RowArgs b = a;
   b.pf_ahead = a.no_prefetch ? 0 : 1;       // dense rows in device memory: prefetch the next line
-  kern<<<grid, 256, tc::kSmemBytes, stream>>>(b);
+  kern<<<grid, tc::kThreads, tc::kSmemBytes, stream>>>(b);
   return cudaGetLastError();
 }
 
