@@ -186,8 +186,8 @@ def run_ours(args):
     x16 = torch.randn((batch, N, 2), device=dev, generator=g).to(torch.float16)
     y16 = torch.empty_like(x16)
     z16 = torch.empty_like(x16)
-    fwd16 = B.bfpfft_plan_create(N, batch, B.F16_BFP, B.FORWARD)
-    inv16 = B.bfpfft_plan_create(N, batch, B.F16_BFP, B.INVERSE)
+    fwd16 = _tc_plan(B, batch, B.FORWARD)
+    inv16 = _tc_plan(B, batch, B.INVERSE)
 
     def step16(evs=None):
         if evs is not None:
@@ -275,8 +275,8 @@ def run_ours(args):
     small_x = x16[:256].contiguous()
     small_y = torch.empty_like(small_x)
     small_z = torch.empty_like(small_x)
-    pf = B.bfpfft_plan_create(N, 256, B.F16_BFP, B.FORWARD)
-    pi = B.bfpfft_plan_create(N, 256, B.F16_BFP, B.INVERSE)
+    pf = _tc_plan(B, 256, B.FORWARD)
+    pi = _tc_plan(B, 256, B.INVERSE)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     small = []
@@ -317,7 +317,7 @@ def run_ours(args):
     fwd_avg = sum(fwd_ms) / len(fwd_ms)
     inv_avg = sum(inv_ms) / len(inv_ms)
     achieved = alg_bytes / (fwd_avg * 1e-3) / 1e9
-    traffic = _profiled_traffic("fft_rows_f16_fwd_4096")
+    traffic = _profiled_traffic("fft_tc_f16_fwd_4096")
 
     if rank == 0:
         cpu = _cpu_baseline(seconds=args.cpu_seconds) if world == 1 else None
@@ -332,14 +332,14 @@ def run_ours(args):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f16 storage, f32 arithmetic",
+            "dtype": "f16 storage; f16 operands, f32 accumulation (tcgen05 DFT-16 blocks)",
             "data": "synthetic (re, im ~ N(0,1), seeded)",
             "config": _config(batch, world),
             "roofline": {
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "fft_rows_kernel<4096, half2, half2, forward> (plain4_l2: FP32 exchange, 4 CTAs/SM, "
-                          "L2 prefetch one wave ahead)",
+                "kernel": "fft_tc_kernel<forward> (radix-16 passes as tcgen05.mma kind::f16, FP32 accumulators "
+                          "in TMEM, 8 persistent CTAs/SM, L2 prefetch of each CTA's next line)",
                 "kernel_source_hash": _kernel_source_hash(),
                 "bytes_per_launch": alg_bytes, "launch_ms": round(fwd_avg, 5), "peak_source": peak_kind,
                 "frac_of_8tbs_nominal": round(achieved / 8000.0, 4),
@@ -367,6 +367,14 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _tc_plan(B, batch: int, direction: int):
+    """The headline plan: N = 4096 FP16-BFP storage with FP16 operands and
+    FP32 accumulation, the radix-16 DFT blocks on the tensor cores."""
+    p = B.bfpfft_plan_create(N, batch, B.F16_BFP, direction)
+    B.bfpfft_plan_set_arith(p, B.ARITH_F16_MUL_F32_ACC)
+    return p
+
+
 def _bench_batch_sweep(B, torch, dev, stream, batches=(256, 4096, 32768, 131072), steps: int = 30):
     """FP16-BFP forward + shifted inverse at N = 4096 for several batches:
     median of `steps` steps after 5 warm-ups, L2 flushed between steps when
@@ -379,8 +387,8 @@ def _bench_batch_sweep(B, torch, dev, stream, batches=(256, 4096, 32768, 131072)
         g = torch.Generator(device=dev).manual_seed(batch)
         x = torch.randn((batch, N, 2), device=dev, generator=g).to(torch.float16)
         y, z = torch.empty_like(x), torch.empty_like(x)
-        pf = B.bfpfft_plan_create(N, batch, B.F16_BFP, B.FORWARD)
-        pi = B.bfpfft_plan_create(N, batch, B.F16_BFP, B.INVERSE)
+        pf = _tc_plan(B, batch, B.FORWARD)
+        pi = _tc_plan(B, batch, B.INVERSE)
         small = x.numel() * x.element_size() < 512 * 1024 * 1024
         fw, tot = [], []
         for i in range(steps + 5):
@@ -415,9 +423,10 @@ def _sqnr_vs(B, torch, ref_c64, test, test_dtype, count, stream):
 
 
 def _bench_precision_modes(B, torch, dev, stream, x16, flops_step, steps):
-    """The paper's precision modes on the headline workload (N = 4096, batch of
-    x16, forward + shifted inverse): pure FP16 arithmetic, FP16 operands with
-    FP32 accumulation (tensor-core DFT blocks), bfloat16, and FP16 with
+    """The paper's other precision modes on the headline workload (N = 4096,
+    batch of x16, forward + shifted inverse; the headline itself is FP16
+    operands with FP32 accumulation on the tensor cores): FP16 storage with
+    FP32 arithmetic throughout, pure FP16 arithmetic, bfloat16, and FP16 with
     adaptive per-line exponents.  Each: GFLOPS, the forward launch's GB/s and
     fraction of the measured HBM copy bandwidth, and the forward output's
     SQNR against the FP32-storage path on the first 256 lines."""
@@ -445,8 +454,8 @@ def _bench_precision_modes(B, torch, dev, stream, x16, flops_step, steps):
             tot.append(e[0].elapsed_time(e[2]))
         return statistics.median(fw), statistics.median(tot)
 
-    cases = (("pure_fp16", B.F16_BFP, B.ARITH_F16, x16),
-             ("fp16_operands_fp32_accumulate_tensor_cores", B.F16_BFP, B.ARITH_F16_MUL_F32_ACC, x16),
+    cases = (("fp16_storage_fp32_arithmetic", B.F16_BFP, B.ARITH_F32, x16),
+             ("pure_fp16", B.F16_BFP, B.ARITH_F16, x16),
              ("bf16", B.BF16, B.ARITH_BF16, None))
     for name, dtype, arith, xin in cases:
         if xin is None:
@@ -539,7 +548,8 @@ def _bench_sar(B, torch, dev, stream):
 
 def _image_quality(B, torch, dev, stream, raw, hr, ha, img16, targets, n_az, n_rg):
     """FP16-BFP image vs the FP32 image of the same scene, both on the GPU:
-    end-to-end SQNR (FP64 reduction) and the point-target metrics (FP64 kernel)."""
+    end-to-end SQNR (FP64 reduction) and the point-target metrics (FP64 kernel);
+    and the FP16 image's metrics against the FP64 oracle's stored values."""
     rc32 = torch.empty((n_rg, n_az), dtype=torch.complex64, device=dev)
     img32 = torch.empty((n_az, n_rg), dtype=torch.complex64, device=dev)
     B.sar_range_compress(raw, B.F32, rc32, B.F32, hr, n_az, n_rg, True, stream)
@@ -562,13 +572,35 @@ def _image_quality(B, torch, dev, stream, raw, hr, ha, img16, targets, n_az, n_r
     torch.cuda.synchronize()
     a, b = m16.cpu().numpy(), m32.cpu().numpy()
     d = abs(a - b)
-    return {"sqnr_fp16_vs_fp32_db": round(sq["aligned_db"], 2), "nonfinite": sq["nonfinite"],
-            "max_abs_delta_db": {"pslr": float(d[:, 0:2].max()), "islr": float(d[:, 2:4].max()),
-                                 "snr": float(d[:, 7].max())},
-            "max_abs_delta_width_cells": float(d[:, 4:6].max()),
-            "pslr_db_fp16": [round(float(x), 2) for x in a[:, 0:2].max(axis=1)],
-            "snr_db_fp16": [round(float(x), 2) for x in a[:, 7]],
-            "metrics_kernel_ms": round(e0.elapsed_time(e1), 3)}
+    out = {"sqnr_fp16_vs_fp32_db": round(sq["aligned_db"], 2), "nonfinite": sq["nonfinite"],
+           "max_abs_delta_db": {"pslr": float(d[:, 0:2].max()), "islr": float(d[:, 2:4].max()),
+                                "snr": float(d[:, 7].max())},
+           "max_abs_delta_width_cells": float(d[:, 4:6].max()),
+           "pslr_db_fp16": [round(float(x), 2) for x in a[:, 0:2].max(axis=1)],
+           "snr_db_fp16": [round(float(x), 2) for x in a[:, 7]],
+           "metrics_kernel_ms": round(e0.elapsed_time(e1), 3)}
+    out["fp16_vs_fp64_oracle"] = _golden_deltas(a, targets, n_az, n_rg)
+    return out
+
+
+def _golden_deltas(m16, targets, n_az, n_rg):
+    """The FP16 image's point-target metrics against the FP64 oracle's, stored
+    for the 4096 x 4096 scene in tests/golden (written by an oracle-only
+    script); None for other scenes."""
+    p = os.path.join(ROOT, "tests", "golden", "sar_4096_image_metrics.json")
+    if not os.path.exists(p):
+        return None
+    gold = json.load(open(p))
+    if (n_az, n_rg) != (4096, 4096) or gold["targets"] != [[int(e), int(r)] for e, r, _ in targets]:
+        return None
+    keys = ("pslr_range_db", "pslr_azimuth_db", "islr_range_db", "islr_azimuth_db", "width_range_cells",
+            "width_azimuth_cells", "peak", "snr_db")
+    ref = [[g[k] for k in keys] for g in gold["metrics"]]
+    dd = [[abs(float(m16[i][c]) - ref[i][c]) for c in range(8)] for i in range(len(ref))]
+    return {"max_abs_delta_db": {"pslr": max(max(r[0:2]) for r in dd), "islr": max(max(r[2:4]) for r in dd),
+                                 "snr": max(r[7] for r in dd)},
+            "max_abs_delta_width_cells": max(max(r[4:6]) for r in dd),
+            "bar": "0.1 dB, 0.1 cell", "source": "tests/golden/sar_4096_image_metrics.json"}
 
 
 def _bench_autofocus(B, torch, dev, stream):
@@ -686,8 +718,8 @@ def _bench_e2e(B, torch, dev, stream, x16, fwd, inv, flops_step, args, chunks: i
     d_in = torch.empty_like(x16)
     d_mid = torch.empty_like(x16)
     d_out = torch.empty_like(x16)
-    fwd_c = B.bfpfft_plan_create(N, per, B.F16_BFP, B.FORWARD)
-    inv_c = B.bfpfft_plan_create(N, per, B.F16_BFP, B.INVERSE)
+    fwd_c = _tc_plan(B, per, B.FORWARD)
+    inv_c = _tc_plan(B, per, B.INVERSE)
     s_in, s_fft, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     ev_in = [torch.cuda.Event() for _ in range(chunks)]
     ev_fft = [torch.cuda.Event() for _ in range(chunks)]

@@ -51,3 +51,23 @@ def test_cpu_baseline_one_core_and_all_cores():
     assert cb["kind"] == "oracle" and cb["unit"] == "GFLOPS" and cb["value"] > 0
     assert cb["single_core_value"] > 0 and cb["cores"] >= 1 and cb["cpu_model"]
     assert str(bench.ORACLE_LINES) in cb["sample"]
+
+
+def test_sar_image_deltas_against_the_stored_fp64_metrics():
+    """The bench's config-3 deltas read the oracle's stored metrics: the stored
+    values themselves give zero deltas, a shifted PSLR shows up in the PSLR
+    column only, and another scene gets no comparison."""
+    import os
+    gold = json.load(open(os.path.join(bench.ROOT, "tests", "golden", "sar_4096_image_metrics.json")))
+    keys = ("pslr_range_db", "pslr_azimuth_db", "islr_range_db", "islr_azimuth_db", "width_range_cells",
+            "width_azimuth_cells", "peak", "snr_db")
+    m = [[g[k] for k in keys] + [0.0] * 4 for g in gold["metrics"]]
+    targets = [(e, r, 1.0) for e, r in gold["targets"]]
+    d = bench._golden_deltas(m, targets, 4096, 4096)
+    assert d["max_abs_delta_db"] == {"pslr": 0.0, "islr": 0.0, "snr": 0.0}
+    assert d["max_abs_delta_width_cells"] == 0.0
+    m[1][1] += 0.05
+    d = bench._golden_deltas(m, targets, 4096, 4096)
+    assert abs(d["max_abs_delta_db"]["pslr"] - 0.05) < 1e-12 and d["max_abs_delta_db"]["islr"] == 0.0
+    assert bench._golden_deltas(m, targets, 2048, 4096) is None
+    assert bench._golden_deltas(m, targets[:-1], 4096, 4096) is None

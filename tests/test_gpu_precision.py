@@ -149,3 +149,72 @@ def test_set_arith_combinations():
     with pytest.raises(B.BfpfftError) as e:
         B.bfpfft_plan_set_arith(u, B.ARITH_F16)
     assert e.value.status == B.ERR_UNSUPPORTED
+
+
+def _tc_plan(n, batch, direction):
+    p = B.bfpfft_plan_create(n, batch, B.F16_BFP, direction)
+    B.bfpfft_plan_set_arith(p, B.ARITH_F16_MUL_F32_ACC)
+    return p
+
+
+def _mma_inverse(x):
+    return np.conj(E.fft_radix16_mma(np.conj(x) / x.shape[-1]))
+
+
+@pytest.mark.parametrize("batch,rows", [
+    (65536, [0, 1, 1215, 1216, 2431, 30001, 65534, 65535]),   # the benchmark's launch: 53-54 lines per CTA
+    (2 * 1216 + 7, [0, 6, 7, 1215, 1216, 1222, 2431, 2438]),  # ragged: CTAs take 2 or 3 lines
+])
+def test_tensor_core_rows_at_the_benchmark_configuration(batch, rows):
+    """The benchmark's timed step (N = 4096, FP16 operands, FP32 accumulation
+    on the tensor cores, persistent CTAs walking many lines): sampled lines of
+    the forward output and of the shifted inverse of that output against the
+    FP64 oracle (SQNR >= 55 dB) and against oracle.emulate.fft_radix16_mma,
+    which the GPU matches far more closely than either matches the exact
+    transform."""
+    import torch
+    n = 4096
+    g = torch.Generator(device="cuda:0").manual_seed(7)
+    xin = torch.randn((batch, n, 2), device="cuda:0", generator=g).to(torch.float16)
+    y = torch.empty_like(xin)
+    z = torch.empty_like(xin)
+    fwd, inv = _tc_plan(n, batch, B.FORWARD), _tc_plan(n, batch, B.INVERSE)
+    B.bfpfft_exec(fwd, xin, y)
+    B.bfpfft_exec(inv, y, z)
+    torch.cuda.synchronize()
+    assert B.bfpfft_plan_status(fwd) == B.OK and B.bfpfft_plan_status(inv) == B.OK
+    x = from_device(xin[rows], B.F16_BFP)
+    got_f = from_device(y[rows], B.F16_BFP)
+    got_i = from_device(z[rows], B.F16_BFP)
+    for got, exact, emu in ((got_f, F.fft(x), E.fft_radix16_mma(x)),
+                            (got_i, F.ifft(got_f), _mma_inverse(got_f))):
+        s_emu = metrics.sqnr_db(exact, emu)
+        assert metrics.sqnr_db(exact, got) >= 55.0
+        assert abs(metrics.sqnr_db(exact, got) - s_emu) <= 0.5
+        assert metrics.sqnr_db(emu, got) >= s_emu + 6.0
+        for line in range(len(rows)):            # no line left behind by the persistent loop
+            assert metrics.sqnr_db(exact[line], got[line]) >= 55.0, rows[line]
+
+
+def test_tensor_core_rows_host_buffers_and_in_place():
+    """Pinned host input (no L2 prefetch of host memory) and in-place calls
+    give the same bits as device buffers out of place."""
+    import torch
+    n, batch = 4096, 1300
+    x = storage_round(synth.complex_gaussian(batch, n, seed=11), B.F16_BFP)
+    dev_in = to_device(x, B.F16_BFP)
+    host_in = torch.empty(dev_in.shape, dtype=dev_in.dtype, pin_memory=True)
+    host_in.copy_(dev_in)
+    fwd, inv = _tc_plan(n, batch, B.FORWARD), _tc_plan(n, batch, B.INVERSE)
+    ref_y, ref_z = torch.empty_like(dev_in), torch.empty_like(dev_in)
+    B.bfpfft_exec(fwd, dev_in, ref_y)
+    B.bfpfft_exec(inv, ref_y, ref_z)
+    host_y = torch.empty_like(dev_in)
+    B.bfpfft_exec(fwd, host_in, host_y)
+    inplace = dev_in.clone()
+    B.bfpfft_exec(fwd, inplace, inplace)
+    B.bfpfft_exec(inv, inplace, inplace)
+    torch.cuda.synchronize()
+    assert B.bfpfft_plan_status(fwd) == B.OK and B.bfpfft_plan_status(inv) == B.OK
+    assert torch.equal(host_y, ref_y)
+    assert torch.equal(inplace, ref_z)
