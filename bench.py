@@ -537,12 +537,63 @@ def _bench_sar(B, torch, dev, stream):
                      "naive_has_nonfinite": None}
         if full:
             out[name].update(_image_quality(B, torch, dev, stream, raw, hr, ha, img, sc.targets, n_az, n_rg))
+            out["table4_modes_4096x4096"] = _bench_sar_modes(B, torch, dev, stream, raw, hr, ha, sc.targets,
+                                                             n_az, n_rg, flush)
         if not full:
             naive = torch.empty((n_az, n_rg, 2), dtype=torch.float16, device=dev)
             B.sar_range_compress(raw, B.F32, naive, B.F16_NAIVE, hr, n_az, n_rg, False, stream)
             torch.cuda.synchronize()
             out[name]["naive_has_nonfinite"] = bool((~torch.isfinite(naive)).any().item())
         del raw, rc, img, flush
+    return out
+
+
+def _bench_sar_modes(B, torch, dev, stream, raw, hr, ha, targets, n_az, n_rg, flush):
+    """Table IV's four precision modes of the range-Doppler image on the same
+    scene: time (median of 20, L2 flushed), SQNR against the GPU FP32 image and
+    point-target deltas against the FP64 oracle's stored metrics."""
+    modes = (("fp32", B.F32, B.ARITH_F32), ("fp16_mul_fp32_acc_tensor_cores", B.F16_BFP, B.ARITH_F16_MUL_F32_ACC),
+             ("fp16_storage_fp32_compute", B.F16_BFP, B.ARITH_F32), ("pure_fp16", B.F16_BFP, B.ARITH_F16))
+    imgs, out = {}, {}
+    for name, dt, arith in modes:
+        shape = (n_rg, n_az) if dt == B.F32 else (n_rg, n_az, 2)
+        tdt = torch.complex64 if dt == B.F32 else torch.float16
+        rc = torch.empty(shape, dtype=tdt, device=dev)
+        img = torch.empty((n_az, n_rg) if dt == B.F32 else (n_az, n_rg, 2), dtype=tdt, device=dev)
+
+        def step():
+            B.sar_range_compress_arith(raw, B.F32, rc, dt, hr, n_az, n_rg, True, arith, stream)
+            B.sar_azimuth_compress_arith(rc, dt, 1, img, dt, ha, n_az, n_rg, arith, stream)
+
+        for _ in range(3):
+            step()
+        ts = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for i in range(20):
+            flush.fill_(i & 0xFF)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        imgs[name] = (img, dt)
+        out[name] = {"ms_median_l2_flushed": round(statistics.median(ts), 4)}
+        del rc
+    ref = imgs["fp32"][0]
+    ws_bytes = B.bfp_sqnr_workspace_bytes()
+    ws = torch.empty(ws_bytes // 8, dtype=torch.float64, device=dev)
+    sums = torch.empty(8, dtype=torch.float64, device=dev)
+    t = torch.tensor([[e, r] for e, r, _ in targets], dtype=torch.int32, device=dev)
+    pw = B.sar_point_target_workspace_bytes(n_az, n_rg)
+    pws = torch.empty(pw, dtype=torch.uint8, device=dev)
+    m = torch.empty((len(targets), 12), dtype=torch.float64, device=dev)
+    for name, (img, dt) in imgs.items():
+        if name != "fp32":
+            B.bfp_sqnr_sums(ref, B.F32, img, dt, n_az * n_rg, sums, ws, ws_bytes, stream)
+            out[name]["sqnr_vs_fp32_db"] = round(B.sqnr_from_sums(sums[:5].cpu().tolist())["aligned_db"], 2)
+        B.sar_point_target_metrics(img, dt, n_az, n_rg, t, len(targets), 96, m, pws, pw, stream)
+        torch.cuda.synchronize()
+        out[name]["vs_fp64_oracle"] = _golden_deltas(m.cpu().numpy(), targets, n_az, n_rg)
     return out
 
 

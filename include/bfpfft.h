@@ -251,10 +251,16 @@ int bfpfft_plan_selftest_wait(bfpfft_plan plan, void* stream);
  * 1/N shift in FP16 arithmetic (the "pure FP16" mode; the filter spectrum is
  * rounded to FP16 once; a complex64 raw echo is rounded to FP16 as it is
  * loaded) and needs FP16 output (F16_BFP, or F16_NAIVE for the unshifted
- * schedule) and, for the azimuth call, FP16 input.  The FP16 mode turns
- * corners with the tiled transpose whatever BFPFFT_SAR_TURN says.
+ * schedule) and, for the azimuth call, FP16 input.
+ * BFPFFT_ARITH_F16_MUL_F32_ACC (the "FP16 multiply, FP32 accumulate" mode) runs
+ * both transforms of a line on the tensor cores (the tensor-core rows of
+ * bfpfft_plan_set_arith: FP16 operands at every pass, FP32 accumulation) and
+ * the filter product and 1/N shift in FP32 between them; lines of 4096 points
+ * only, FP16-BFP output, FP32 or FP16 input (rounded to FP16 operands as it is
+ * loaded).  Both 16-bit modes turn corners with the tiled transpose whatever
+ * BFPFFT_SAR_TURN says.
  * Errors: as the calls above; INVALID_ARG for an unknown arith; UNSUPPORTED for
- * a storage combination the mode does not offer.
+ * a length or storage combination the mode does not offer.
  */
 int sar_range_compress_arith(const void* raw, int raw_dtype, void* out, int out_dtype, const void* hr,
                              int64_t n_az, int64_t n_rg, int transpose_out, int arith, void* stream);

@@ -34,6 +34,10 @@ cudaError_t launch_rows16_bf16(int log2n, int mode, const RowArgs& a, cudaStream
 // complex64 input; naive drops the 1/N shift (Section III-B).
 cudaError_t launch_rows16_compress_f16(int log2n, bool in32, bool naive, const RowArgs& a, cudaStream_t s);
 cudaError_t launch_twiddles16(void* tw, int n, bool bf16);
+// SAR compression lines of 4096 points on the tensor cores (tc_fft.cuh): FP16
+// operands, FP32 accumulation; in32 reads a complex64 input; FP16 output rows.
+// a.tc_b holds the DFT-16 matrix, a.h the filter spectrum.
+cudaError_t launch_tc_compress(bool in32, const RowArgs& a, cudaStream_t s);
 
 // SAR compression lines (Section VI, Fig. 1): float2 or __half2 in and out,
 // optional naive FP16 output, optional cluster corner turn on load / store.

@@ -27,4 +27,9 @@ cudaError_t launch_compress_c64_to_f16(int log2n, bool naive, const RowArgs& a, 
   return launch_rows<float2, __half2, kCompress, false, false>(log2n, a, s);
 }
 
+cudaError_t launch_tc_compress(bool in32, const RowArgs& a, cudaStream_t s) {
+  if (a.tc_b == nullptr || a.h == nullptr) return cudaErrorInvalidValue;
+  return in32 ? launch_tc_kernel<kCompress, float2>(a, s) : launch_tc_kernel<kCompress, __half2>(a, s);
+}
+
 }  // namespace bfp

@@ -1211,18 +1211,34 @@ int sar_range_compress(const void* raw, int raw_dtype, void* out, int out_dtype,
                                   stream);
 }
 
-// The compression lines of a SAR call: the FP32-arithmetic kernels, or with
-// BFPFFT_ARITH_F16 the FP16-arithmetic kernel (dense rows, FP16 output).
+// The compression lines of a SAR call: the FP32-arithmetic kernels; with
+// BFPFFT_ARITH_F16 the FP16-arithmetic kernel; with
+// BFPFFT_ARITH_F16_MUL_F32_ACC the tensor-core kernel (N = 4096).  The last
+// two write dense FP16 rows.
 static cudaError_t sar_lines(int l, int arith, bool in16, bool out16, bool naive, bool tload, bool tstore,
                              const bfp::RowArgs& a, cudaStream_t s) {
   if (arith == BFPFFT_ARITH_F16) return bfp::launch_rows16_compress_f16(l, !in16, naive, a, s);
+  if (arith == BFPFFT_ARITH_F16_MUL_F32_ACC) return bfp::launch_tc_compress(!in16, a, s);
   return bfp::launch_sar(l, in16, out16, naive, tload, tstore, a, s);
+}
+
+// Arguments a SAR call's arithmetic mode accepts: FP16 arithmetic writes FP16
+// (BFP or naive); the tensor-core lines take N = 4096 and write FP16-BFP.
+static int sar_arith_check(int arith, int l, int in_dtype, int out_dtype, bool azimuth) {
+  if (arith != BFPFFT_ARITH_F32 && arith != BFPFFT_ARITH_F16 && arith != BFPFFT_ARITH_F16_MUL_F32_ACC)
+    return BFPFFT_ERR_INVALID_ARG;
+  if (arith == BFPFFT_ARITH_F16 && (out_dtype == BFPFFT_F32 || (azimuth && in_dtype != BFPFFT_F16_BFP)))
+    return BFPFFT_ERR_UNSUPPORTED;
+  if (arith == BFPFFT_ARITH_F16_MUL_F32_ACC && (l != 12 || out_dtype != BFPFFT_F16_BFP))
+    return BFPFFT_ERR_UNSUPPORTED;
+  return BFPFFT_OK;
 }
 
 int sar_range_compress_arith(const void* raw, int raw_dtype, void* out, int out_dtype, const void* hr,
                              int64_t n_az, int64_t n_rg, int transpose_out, int arith, void* stream) {
   if (n_az < 0) return BFPFFT_ERR_INVALID_ARG;
-  if (arith != BFPFFT_ARITH_F32 && arith != BFPFFT_ARITH_F16) return BFPFFT_ERR_INVALID_ARG;
+  if (arith != BFPFFT_ARITH_F32 && arith != BFPFFT_ARITH_F16 && arith != BFPFFT_ARITH_F16_MUL_F32_ACC)
+    return BFPFFT_ERR_INVALID_ARG;
   const int l = log2_exact(n_rg);
   if (l < bfp::kSarMinLog2 || l > kSarMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
   if (n_az == 0) return BFPFFT_OK;
@@ -1231,13 +1247,15 @@ int sar_range_compress_arith(const void* raw, int raw_dtype, void* out, int out_
   if (raw_dtype != BFPFFT_F32 && raw_dtype != BFPFFT_F16_BFP) return BFPFFT_ERR_UNSUPPORTED;
   if (out_dtype != BFPFFT_F32 && out_dtype != BFPFFT_F16_BFP && out_dtype != BFPFFT_F16_NAIVE)
     return BFPFFT_ERR_UNSUPPORTED;
-  if (arith == BFPFFT_ARITH_F16 && out_dtype == BFPFFT_F32) return BFPFFT_ERR_UNSUPPORTED;
+  if (const int ac = sar_arith_check(arith, l, raw_dtype, out_dtype, false); ac != BFPFFT_OK) return ac;
   if (transpose_out != 0 && transpose_out != 1) return BFPFFT_ERR_INVALID_ARG;
   if (fault("launch")) return BFPFFT_ERR_CUDA;
   bfp::RowArgs a;
   int st = row_args(l, &a);
   if (st != BFPFFT_OK) return st;
   if (arith == BFPFFT_ARITH_F16 && (st = get_twiddles16(l, false, &a.tw16)) != BFPFFT_OK) return st;
+  if (arith == BFPFFT_ARITH_F16_MUL_F32_ACC && (st = get_tc_matrix(const_cast<void**>(&a.tc_b))) != BFPFFT_OK)
+    return st;
   a.in = raw;
   a.out = out;
   a.h = static_cast<const float2*>(hr);
@@ -1252,7 +1270,7 @@ int sar_range_compress_arith(const void* raw, int raw_dtype, void* out, int out_
   const bool in16 = raw_dtype == BFPFFT_F16_BFP;
   const bool out16 = out_dtype != BFPFFT_F32;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (transpose_out && (sar_split_turns() || arith == BFPFFT_ARITH_F16)) {
+  if (transpose_out && (sar_split_turns() || arith != BFPFFT_ARITH_F32)) {
     // Rows into scratch [n_az][n_rg], then turned into out [n_rg][n_az].
     const int eb = out16 ? 4 : 8;
     void* tmp = nullptr;
@@ -1278,7 +1296,8 @@ int sar_azimuth_compress(const void* rc, int rc_dtype, int rc_layout, void* img,
 int sar_azimuth_compress_arith(const void* rc, int rc_dtype, int rc_layout, void* img, int img_dtype,
                                const void* ha, int64_t n_az, int64_t n_rg, int arith, void* stream) {
   if (n_rg < 0) return BFPFFT_ERR_INVALID_ARG;
-  if (arith != BFPFFT_ARITH_F32 && arith != BFPFFT_ARITH_F16) return BFPFFT_ERR_INVALID_ARG;
+  if (arith != BFPFFT_ARITH_F32 && arith != BFPFFT_ARITH_F16 && arith != BFPFFT_ARITH_F16_MUL_F32_ACC)
+    return BFPFFT_ERR_INVALID_ARG;
   const int l = log2_exact(n_az);
   if (l < bfp::kSarMinLog2 || l > kSarMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
   if (n_rg == 0) return BFPFFT_OK;
@@ -1287,14 +1306,15 @@ int sar_azimuth_compress_arith(const void* rc, int rc_dtype, int rc_layout, void
   if (rc_dtype != BFPFFT_F32 && rc_dtype != BFPFFT_F16_BFP) return BFPFFT_ERR_UNSUPPORTED;
   if (img_dtype != BFPFFT_F32 && img_dtype != BFPFFT_F16_BFP && img_dtype != BFPFFT_F16_NAIVE)
     return BFPFFT_ERR_UNSUPPORTED;
-  if (arith == BFPFFT_ARITH_F16 && (img_dtype == BFPFFT_F32 || rc_dtype != BFPFFT_F16_BFP))
-    return BFPFFT_ERR_UNSUPPORTED;
+  if (const int ac = sar_arith_check(arith, l, rc_dtype, img_dtype, true); ac != BFPFFT_OK) return ac;
   if (rc_layout != 0 && rc_layout != 1) return BFPFFT_ERR_INVALID_ARG;
   if (fault("launch")) return BFPFFT_ERR_CUDA;
   bfp::RowArgs a;
   int st = row_args(l, &a);
   if (st != BFPFFT_OK) return st;
   if (arith == BFPFFT_ARITH_F16 && (st = get_twiddles16(l, false, &a.tw16)) != BFPFFT_OK) return st;
+  if (arith == BFPFFT_ARITH_F16_MUL_F32_ACC && (st = get_tc_matrix(const_cast<void**>(&a.tc_b))) != BFPFFT_OK)
+    return st;
   a.in = rc;
   a.out = img;
   a.h = static_cast<const float2*>(ha);
@@ -1308,7 +1328,7 @@ int sar_azimuth_compress_arith(const void* rc, int rc_dtype, int rc_layout, void
   const bool naive = img_dtype == BFPFFT_F16_NAIVE;
   const bool in16 = rc_dtype == BFPFFT_F16_BFP, out16 = img_dtype != BFPFFT_F32;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (sar_split_turns() || arith == BFPFFT_ARITH_F16) {
+  if (sar_split_turns() || arith != BFPFFT_ARITH_F32) {
     // Layout 0 is first turned to [n_rg][n_az]; the azimuth lines are then
     // dense rows, compressed into scratch and turned into img [n_az][n_rg].
     const size_t pts = size_t(n_az) * size_t(n_rg);

@@ -105,6 +105,11 @@ __device__ __forceinline__ uint32_t ld_once_b32(const void* p) {
   asm volatile("ld.global.L1::no_allocate.b32 %0, [%1];" : "=r"(r) : "l"(p));
   return r;
 }
+__device__ __forceinline__ float2 ld_once_f2(const void* p) {
+  float2 r;
+  asm volatile("ld.global.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
+  return r;
+}
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = uint64_t((addr >> 4) & 0x3FFF);
@@ -159,7 +164,14 @@ __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::aft
 // (t = j mod 16, rn = j / 16 for butterfly j; the pass-1 row map splits into
 // the thread's bits and q's bits except row bit 2 = t2 ^ q0, hence the two
 // bases for even and odd q).
-template <int P, int MODE>
+//
+// FILTER (last pass of a compression line's forward transform): instead of
+// going to HBM, output q of butterfly j -- spectrum bin k = j + 256 q -- is
+// multiplied by the filter H[k] in FP32, conjugated and shifted by 1/N
+// (Eq. 1), and written as the inverse transform's pass-0 input: butterfly j
+// of the inverse takes bins j + 256 r, so the 16 results form row rho_0(j)
+// of A, four 16-byte stores.
+template <int P, int MODE, bool FILTER = false>
 __device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsigned char* sA, uint64_t* bar,
                                         uint32_t tmem, uint32_t lane_tmem, uint32_t a_base, uint32_t b_base,
                                         uint32_t& phase, const float2* s_tw) {
@@ -228,6 +240,24 @@ __device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsign
           if (q < 15) w = cmul(w, ratio);
         }
       }
+    } else if constexpr (FILTER) {
+      const float2* hk = a.h + rho;
+      const float inv_n = 1.0f / float(kN);
+      const int row = tc::row_of<0>(rho);
+      unsigned char* dst = sA + (row >> 3) * kSbo + (row & 7) * 16;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint32_t x[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int q = 4 * c + e;
+          const float2 y = cmul(make_float2(__uint_as_float(d[2 * q]), __uint_as_float(d[2 * q + 1])),
+                                __ldg(hk + 256 * q));
+          const __half2 v = __floats2half2_rn(y.x * inv_n, -y.y * inv_n);
+          x[e] = *reinterpret_cast<const uint32_t*>(&v);
+        }
+        *reinterpret_cast<uint4*>(dst + c * kLbo) = make_uint4(x[0], x[1], x[2], x[3]);
+      }
     } else {
       // The inverse's final conjugation is folded into the last pass's matrix.
       __half2* out = static_cast<__half2*>(a.out) + line * a.out_stride + rho;
@@ -247,7 +277,7 @@ __device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsign
 // TMEM limit at 64 columns a line) while each CTA's passes run one after
 // another.  Persistent: CTA b takes lines b, b + grid, ...; thread 0 bulk-
 // prefetches the CTA's next line into L2.
-template <int MODE>
+template <int MODE, class TIn>
 __global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(const RowArgs a) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
@@ -257,7 +287,7 @@ __global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(co
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_tc + kBarOff);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_tc + kBarOff + 8);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const __half2* in_lines = static_cast<const __half2*>(a.in);
+  const TIn* in_lines = static_cast<const TIn*>(a.in);
 
   // DFT-16 matrix in real form (prepared on the host in FP16, [n][k]) and two
   // derived copies for the inverse (Eq. 1 as conj(DFT(conj(x) / N))):
@@ -298,33 +328,52 @@ __global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(co
   const uint32_t lane_tmem = tmem + (uint32_t(32 * warp) << 16);
   const uint32_t a_base = smem_addr(sA), b_base = smem_addr(sB);
   const uint32_t b_first = MODE == kInverse ? b_base + 2 * kBBytes : b_base;
-  const uint32_t b_last = MODE == kInverse ? b_base + kBBytes : b_base;
+  const uint32_t b_last = MODE != kForward ? b_base + kBBytes : b_base;
   uint32_t phase = 0;
   bool ok = true;
 
   for (long long line = blockIdx.x; ok && line < a.lines; line += gridDim.x) {
     const long long next = line + gridDim.x;
     if (a.pf_ahead > 0 && tid == 0 && next < a.lines)   // next iteration's line, into L2
-      prefetch_l2_bulk(in_lines + next * a.in_stride, uint32_t(kLineBytes));
+      prefetch_l2_bulk(in_lines + next * a.in_stride, uint32_t(kN * sizeof(TIn)));
     // Pass-0 inputs: butterfly j takes x[j + 256 r]; its row of A is four
     // 16-byte core-matrix rows, one st.shared.v4 per four points (the eight
-    // lanes of a quarter-warp have distinct row % 8).
-    const __half2* in = in_lines + line * a.in_stride + tid;
+    // lanes of a quarter-warp have distinct row % 8).  Complex64 inputs are
+    // rounded to FP16 operands here.
+    const TIn* in = in_lines + line * a.in_stride + tid;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int j = tid + 128 * h;
       uint32_t x[16];
 #pragma unroll
-      for (int r = 0; r < 16; ++r) x[r] = ld_once_b32(in + 128 * h + 256 * r);
+      for (int r = 0; r < 16; ++r) {
+        if constexpr (sizeof(TIn) == 4) {
+          x[r] = ld_once_b32(in + 128 * h + 256 * r);
+        } else {
+          const __half2 v = __float22half2_rn(ld_once_f2(in + 128 * h + 256 * r));
+          x[r] = *reinterpret_cast<const uint32_t*>(&v);
+        }
+      }
       const int row = tc::row_of<0>(j);
       unsigned char* dst = sA + (row >> 3) * kSbo + (row & 7) * 16;
 #pragma unroll
       for (int c = 0; c < 4; ++c)
         *reinterpret_cast<uint4*>(dst + c * kLbo) = make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
     }
-    ok = tc_pass<0, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_first, phase, s_tw) &&
-         tc_pass<1, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_base, phase, s_tw) &&
-         tc_pass<2, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_last, phase, s_tw);
+    if constexpr (MODE == kCompress) {
+      // Forward, filter (into A, conjugated and shifted), inverse: the inverse's
+      // input is already conj(Y) / N, so its first pass takes plain B.
+      ok = tc_pass<0, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_base, phase, s_tw) &&
+           tc_pass<1, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_base, phase, s_tw) &&
+           tc_pass<2, MODE, true>(a, line, sA, bar, tmem, lane_tmem, a_base, b_base, phase, s_tw) &&
+           tc_pass<0, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_base, phase, s_tw) &&
+           tc_pass<1, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_base, phase, s_tw) &&
+           tc_pass<2, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_last, phase, s_tw);
+    } else {
+      ok = tc_pass<0, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_first, phase, s_tw) &&
+           tc_pass<1, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_base, phase, s_tw) &&
+           tc_pass<2, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_last, phase, s_tw);
+    }
   }
   // A wait that expired leaves `phase` at the commit it was waiting for:
   // give that commit one more bounded wait before the tensor memory goes.
@@ -336,10 +385,9 @@ __global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(co
   }
 }
 
-template <class TS, int MODE>
-cudaError_t launch_tc_n(const RowArgs& a, cudaStream_t stream) {
-  static_assert(sizeof(TS) == sizeof(__half2), "the tensor-core rows take FP16 storage");
-  auto kern = fft_tc_kernel<MODE>;
+template <int MODE, class TIn>
+cudaError_t launch_tc_kernel(const RowArgs& a, cudaStream_t stream) {
+  auto kern = fft_tc_kernel<MODE, TIn>;
   // kCtasPerSm CTAs per SM: the register limit of __launch_bounds__; tensor
   // memory holds exactly that many 64-column allocations, so the persistent
   // CTAs never wait on each other's allocation.  Computed once,
@@ -360,6 +408,12 @@ cudaError_t launch_tc_n(const RowArgs& a, cudaStream_t stream) {
   b.pf_ahead = a.no_prefetch ? 0 : 1;       // dense rows in device memory: prefetch the next line
   kern<<<grid, tc::kThreads, tc::kSmemBytes, stream>>>(b);
   return cudaGetLastError();
+}
+
+template <class TS, int MODE>
+cudaError_t launch_tc_n(const RowArgs& a, cudaStream_t stream) {
+  static_assert(sizeof(TS) == sizeof(__half2), "the tensor-core rows take FP16 storage");
+  return launch_tc_kernel<MODE, __half2>(a, stream);
 }
 
 }  // namespace bfp
