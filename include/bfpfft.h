@@ -313,6 +313,31 @@ int bfpfft_exec_adaptive(bfpfft_plan plan, const void* in, const int32_t* in_exp
 int bfp_spectral_adaptive(const void* x, int x_dtype, const int32_t* x_exp, const void* h, void* out,
                           int32_t* out_exp, int64_t n, int64_t lines, void* stream);
 
+/*
+ * Batched forward-multiply-inverse, y = IDFT(DFT(x) . H) per line, with the
+ * fixed 1/N shift of Eq. 1 (Section VIII, Generality: FFT convolution and
+ * correlation, and the spectral layers of Fourier neural operators, reuse the
+ * schedule).  The kernels are those of the SAR compression calls below; the
+ * line is held on chip from load to store.
+ *   x         [lines][n], x_dtype BFPFFT_F32 or BFPFFT_F16_BFP (16-byte aligned)
+ *   h         float2 filter spectra: h_stride = 0 applies h[n] to every line
+ *             (convolution with DFT(g), correlation with conj(DFT(g)));
+ *             h_stride = n gives line l its own h[l n .. l n + n) (a spectral
+ *             layer's per-channel weights; zeros above a cut-off truncate the
+ *             modes).  Other strides: INVALID_ARG.
+ *   out       [lines][n], out_dtype BFPFFT_F32, BFPFFT_F16_BFP or BFPFFT_F16_NAIVE
+ *             (no shift: overflows as Section III-B predicts)
+ *   n         a power of two in [256, 16384]
+ *   arith     BFPFFT_ARITH_F32, BFPFFT_ARITH_F16 or BFPFFT_ARITH_F16_MUL_F32_ACC,
+ *             with the storage combinations and lengths of
+ *             sar_range_compress_arith
+ * lines = 0 is a no-op.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, UNSUPPORTED (n, dtype or arith combination), MISALIGNED,
+ * CUDA.
+ */
+int bfp_spectral_filter(const void* x, int x_dtype, const void* h, int64_t h_stride, void* out, int out_dtype,
+                        int64_t n, int64_t lines, int arith, void* stream);
+
 /* ---------------------------------------------------------------------------
  * SAR range-Doppler compression (Section VI, Fig. 1).
  *

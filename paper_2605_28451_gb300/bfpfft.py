@@ -67,6 +67,8 @@ SIGNATURES = {
     "bfpfft_plan_set_arith": (ctypes.c_int, [_vp, ctypes.c_int]),
     "bfpfft_exec_adaptive": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "bfp_spectral_adaptive": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _c_int64, _c_int64, _vp]),
+    "bfp_spectral_filter": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _c_int64, _vp, ctypes.c_int, _c_int64, _c_int64,
+                                           ctypes.c_int, _vp]),
     "sar_make_filter": (ctypes.c_int, [_vp, _c_int64, ctypes.c_int, _vp, _vp]),
     "sar_range_compress": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _c_int64, _c_int64,
                                           ctypes.c_int, _vp]),
@@ -254,6 +256,12 @@ def bfpfft_exec_adaptive(plan: Plan, inp, in_exp, out, out_exp, stream=None):
     """FP16 mantissas + int32 per-line exponents in and out (in_exp may be None)."""
     _check(lib().bfpfft_exec_adaptive(plan.handle, _ptr(inp), _ptr(in_exp), _ptr(out), _ptr(out_exp),
                                       _stream(stream)), "bfpfft_exec_adaptive")
+
+
+def bfp_spectral_filter(x, x_dtype: int, h, h_stride: int, out, out_dtype: int, n: int, lines: int,
+                        arith: int = ARITH_F32, stream=None):
+    _check(lib().bfp_spectral_filter(_ptr(x), int(x_dtype), _ptr(h), int(h_stride), _ptr(out), int(out_dtype), int(n),
+                                     int(lines), int(arith), _stream(stream)), "bfp_spectral_filter")
 
 
 def bfp_spectral_adaptive(x, x_dtype: int, x_exp, h, out, out_exp, n: int, lines: int, stream=None):

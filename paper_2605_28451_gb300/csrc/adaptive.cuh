@@ -86,7 +86,7 @@ fft_rows_adaptive_kernel(const RowArgs a) {
 #pragma unroll
     for (int m = 0; m < P; ++m) v[m] = make_float2(0.f, 0.f);
   }
-  row_compute<N, MODE, false, false>(v, a, sm, t);
+  row_compute<N, MODE, false, false>(v, a, sm, t, line);
 
   // Block maximum of |Re|, |Im| over the line.  Non-negative floats order like
   // their bit patterns, so the reduction runs on unsigned integers.

@@ -317,7 +317,7 @@ fft_rows16_kernel(const RowArgs a) {
     for (int m0 = 0; m0 < P; m0 += 4) {
       float2 h[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) h[i] = __ldg(a.h + t + T * (m0 + i));
+      for (int i = 0; i < 4; ++i) h[i] = __ldg(a.h + (active ? line : 0) * a.h_stride + t + T * (m0 + i));
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const H w = A::make(h[i].x, h[i].y), wp = A::make(-h[i].y, h[i].x);

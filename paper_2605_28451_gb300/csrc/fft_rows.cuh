@@ -60,6 +60,7 @@ struct RowArgs {
   void* out;
   const float2* tw;        // W_N^i for i in [0, N), FP32
   const float2* h;         // filter spectrum [N] (compress only)
+  long long h_stride;      // compress: points between the filters of consecutive lines (0: one filter for all)
   long long lines;         // number of lines
   long long in_stride;     // points between consecutive input lines
   long long out_stride;    // points between consecutive output lines
@@ -295,15 +296,18 @@ __device__ __forceinline__ void line_dft(float2 (&v)[kPointsPerThread], const fl
 // conj * 1/N (Eq. 1), the transform(s), the filter multiply of compress mode,
 // the final conjugate, and the naive FP16 rounding of Section III-B.
 template <int N, int MODE, bool NAIVE, bool SCALED, class X = LocalXch>
-__device__ __forceinline__ void row_compute_x(float2 (&v)[kPointsPerThread], const RowArgs& a, const X& xch, int t);
+__device__ __forceinline__ void row_compute_x(float2 (&v)[kPointsPerThread], const RowArgs& a, const X& xch, int t,
+                                              long long line = 0);
 
 template <int N, int MODE, bool NAIVE, bool SCALED>
-__device__ __forceinline__ void row_compute(float2 (&v)[kPointsPerThread], const RowArgs& a, float2* sm, int t) {
-  row_compute_x<N, MODE, NAIVE, SCALED>(v, a, LocalXch{sm}, t);
+__device__ __forceinline__ void row_compute(float2 (&v)[kPointsPerThread], const RowArgs& a, float2* sm, int t,
+                                            long long line = 0) {
+  row_compute_x<N, MODE, NAIVE, SCALED>(v, a, LocalXch{sm}, t, line);
 }
 
 template <int N, int MODE, bool NAIVE, bool SCALED, class X>
-__device__ __forceinline__ void row_compute_x(float2 (&v)[kPointsPerThread], const RowArgs& a, const X& xch, int t) {
+__device__ __forceinline__ void row_compute_x(float2 (&v)[kPointsPerThread], const RowArgs& a, const X& xch, int t,
+                                              long long line) {
   constexpr int P = kPointsPerThread, T = N / P;
   const float inv_n = 1.0f / float(N);
   if (SCALED) {
@@ -318,13 +322,15 @@ __device__ __forceinline__ void row_compute_x(float2 (&v)[kPointsPerThread], con
   line_dft<N>(v, a.tw, xch, t);
 
   if (MODE == kCompress) {
+    // This line's filter (idle groups past the last line read line 0's).
+    const float2* hl = a.h + (line < a.lines ? line : 0) * a.h_stride;
     // Filter loads in groups of four: keeps the compiler from hoisting all
     // sixteen next to the line (register pressure at 3 CTAs / SM).
 #pragma unroll
     for (int m0 = 0; m0 < P; m0 += 4) {
       float2 h[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) h[i] = __ldg(a.h + t + T * (m0 + i));
+      for (int i = 0; i < 4; ++i) h[i] = __ldg(hl + t + T * (m0 + i));
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const float2 p = cmul(v[m0 + i], h[i]);
@@ -526,10 +532,10 @@ fft_rows_kernel(const RowArgs a) {
     for (int m = 0; m < P; ++m) v[m] = make_float2(0.f, 0.f);
   }
   if constexpr (XV == kXchF32) {
-    row_compute<N, MODE, NAIVE, SCALED>(v, a, sm, t);
+    row_compute<N, MODE, NAIVE, SCALED>(v, a, sm, t, line);
   } else {
     unsigned char* base = reinterpret_cast<unsigned char*>(smem_rows) + g * XchSel<N, XV>::kLineBytes;
-    row_compute_x<N, MODE, NAIVE, SCALED>(v, a, XchSel<N, XV>::make(base), t);
+    row_compute_x<N, MODE, NAIVE, SCALED>(v, a, XchSel<N, XV>::make(base), t, line);
   }
 
   if constexpr (TSTORE && S::kLinesPerCluster == 8 && std::is_same<TOut, __half2>::value) {
@@ -729,8 +735,8 @@ fft_rows_tma_kernel(const RowArgs a) {
     }
     int ti;   // opaque per iteration: no address arithmetic carried across the loop
     asm volatile("mov.b32 %0, %1;" : "=r"(ti) : "r"(t));
-    row_compute_x<N, MODE, NAIVE, SCALED>(v, a, XchSel<N, XV>::make(xg), ti);
     const long long line = grp * G + g;
+    row_compute_x<N, MODE, NAIVE, SCALED>(v, a, XchSel<N, XV>::make(xg), ti, line);
     if (line < a.lines) {
       TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;
 #pragma unroll
@@ -1081,7 +1087,7 @@ fft_cluster_kernel(const RowArgs a) {
   for (int m = 0; m < P; ++m) v[m] = Storage<TIn>::load(in + T * m);
   // Every CTA of the cluster must be running before its slab is written.
   cluster.sync();
-  row_compute_x<N, MODE, NAIVE, SCALED>(v, a, xch, t);
+  row_compute_x<N, MODE, NAIVE, SCALED>(v, a, xch, t, line);
   // The last exchange ended with a cluster barrier after its reads: no CTA
   // touches another's slab from here on.
   TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;

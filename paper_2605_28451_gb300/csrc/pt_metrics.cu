@@ -30,7 +30,8 @@ namespace {
 constexpr int kW = 64;            // window
 constexpr int kF = 16;            // interpolation factor
 constexpr int kFine = kW * kF;    // 1024 fine samples per axis
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;           // noise reduction
+constexpr int kTargetThreads = 512;     // one CTA per target: 16 warps for its FP64 sums
 
 template <class T> __device__ __forceinline__ double2 pixel(const T* img, long long i);
 template <> __device__ __forceinline__ double2 pixel<float2>(const float2* img, long long i) {
@@ -54,6 +55,18 @@ __device__ __forceinline__ double2 expi(int sign, long long m, int n) {
   sincospi(2.0 * double(sign) * double(m % n) / double(n), &s, &c);
   return make_double2(c, s);
 }
+
+// Every phase the kernel needs is a multiple of 2 pi / 64 (the window DFT,
+// sign -1) or 2 pi / 1024 (the x16 interpolation, sign +1): two tables in
+// shared memory, filled once per CTA with expi, replace the per-term
+// sincospi of the sums (the sums themselves are unchanged).  n is a power of
+// two, so m mod n is m & (n - 1) for negative m too.
+struct PhaseTables {
+  const double2* fwd64;     // exp(-2 pi i m / 64)
+  const double2* inv1024;   // exp(+2 pi i m / 1024)
+  __device__ __forceinline__ double2 w64(long long m) const { return fwd64[m & (kW - 1)]; }
+  __device__ __forceinline__ double2 w1024(long long m) const { return inv1024[m & (kFine - 1)]; }
+};
 
 __device__ __forceinline__ int freq(int k) { return k < kW / 2 ? k : k - kW; }
 
@@ -104,24 +117,29 @@ __device__ CutResult cut_metrics(const double* mag) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) target_kernel(const T* __restrict__ img, long long n_az, long long n_rg,
+__global__ void __launch_bounds__(kTargetThreads) target_kernel(const T* __restrict__ img, long long n_az, long long n_rg,
                                                           const int* __restrict__ targets, double* __restrict__ out) {
   extern __shared__ double2 sh[];
   double2* spec = sh;                                   // [64][64] window spectrum S[ka][kr]
   double2* tmp = sh + kW * kW;                          // [64][64] scratch
-  double* cut = reinterpret_cast<double*>(tmp + kW * kW);  // [2][1024] magnitudes
-  __shared__ double red_v[kThreads];
-  __shared__ int red_i[kThreads];
+  double2* tab64 = tmp + kW * kW;                       // [64] phase table
+  double2* tab1024 = tab64 + kW;                        // [1024] phase table
+  double* cut = reinterpret_cast<double*>(tab1024 + kFine);  // [2][1024] magnitudes
+  __shared__ double red_v[kTargetThreads];
+  __shared__ int red_i[kTargetThreads];
   __shared__ int peak_cell[2];
   __shared__ int fine_peak[2];
   const int t = threadIdx.x;
   const int eta = targets[2 * blockIdx.x], rr = targets[2 * blockIdx.x + 1];
+  for (int i = t; i < kW; i += kTargetThreads) tab64[i] = expi(-1, i, kW);
+  for (int i = t; i < kFine; i += kTargetThreads) tab1024[i] = expi(+1, i, kFine);
+  const PhaseTables ph{tab64, tab1024};
 
   // 1. peak cell within +-4 cells
   {
     double best = -1.0;
     int bi = 0;
-    for (int i = t; i < 81; i += kThreads) {
+    for (int i = t; i < 81; i += kTargetThreads) {
       const long long a = ((eta + i / 9 - 4) % n_az + n_az) % n_az;
       const long long r = ((rr + i % 9 - 4) % n_rg + n_rg) % n_rg;
       const double m = mag2(pixel(img, a * n_rg + r));
@@ -135,7 +153,7 @@ __global__ void __launch_bounds__(kThreads) target_kernel(const T* __restrict__ 
     __syncthreads();
     if (t == 0) {
       int b = 0;
-      for (int i = 1; i < kThreads; ++i)
+      for (int i = 1; i < kTargetThreads; ++i)
         if (red_v[i] > red_v[b] || (red_v[i] == red_v[b] && red_i[i] < red_i[b])) b = i;
       peak_cell[0] = int(((eta + red_i[b] / 9 - 4) % n_az + n_az) % n_az);
       peak_cell[1] = int(((rr + red_i[b] % 9 - 4) % n_rg + n_rg) % n_rg);
@@ -145,24 +163,24 @@ __global__ void __launch_bounds__(kThreads) target_kernel(const T* __restrict__ 
   const int pa = peak_cell[0], pr = peak_cell[1];
 
   // 2. window and its 2-D DFT: tmp[a][kr] = sum_r w[a][r] e^{-2 pi i r kr / 64}; spec[ka][kr] = sum_a ...
-  for (int i = t; i < kW * kW; i += kThreads) {
+  for (int i = t; i < kW * kW; i += kTargetThreads) {
     const int a = i / kW, r = i % kW;
     const long long ga = ((pa - kW / 2 + a) % n_az + n_az) % n_az;
     const long long gr = ((pr - kW / 2 + r) % n_rg + n_rg) % n_rg;
     spec[i] = pixel(img, ga * n_rg + gr);             // window, temporarily
   }
   __syncthreads();
-  for (int i = t; i < kW * kW; i += kThreads) {
+  for (int i = t; i < kW * kW; i += kTargetThreads) {
     const int a = i / kW, kr = i % kW;
     double2 acc = make_double2(0.0, 0.0);
-    for (int r = 0; r < kW; ++r) acc = caddd(acc, cmuld(spec[a * kW + r], expi(-1, (long long)r * kr, kW)));
+    for (int r = 0; r < kW; ++r) acc = caddd(acc, cmuld(spec[a * kW + r], ph.w64((long long)r * kr)));
     tmp[i] = acc;
   }
   __syncthreads();
-  for (int i = t; i < kW * kW; i += kThreads) {
+  for (int i = t; i < kW * kW; i += kTargetThreads) {
     const int ka = i / kW, kr = i % kW;
     double2 acc = make_double2(0.0, 0.0);
-    for (int a = 0; a < kW; ++a) acc = caddd(acc, cmuld(tmp[a * kW + kr], expi(-1, (long long)a * ka, kW)));
+    for (int a = 0; a < kW; ++a) acc = caddd(acc, cmuld(tmp[a * kW + kr], ph.w64((long long)a * ka)));
     spec[i] = acc;
   }
   __syncthreads();
@@ -172,22 +190,22 @@ __global__ void __launch_bounds__(kThreads) target_kernel(const T* __restrict__ 
   //    U[ua][ur] = (1 / kW^2) sum_ka sum_kr S[ka][kr] e^{2 pi i (f(ka) ua + f(kr) ur) / kFine}
   constexpr int kLo = (kW / 2 - 1) * kF, kSpan = 2 * kF + 1;
   // tmp[ua_local][kr] = sum_ka S[ka][kr] e^{2 pi i f(ka) ua / kFine}, ua = kLo + ua_local
-  for (int i = t; i < kSpan * kW; i += kThreads) {
+  for (int i = t; i < kSpan * kW; i += kTargetThreads) {
     const int ul = i / kW, kr = i % kW;
     double2 acc = make_double2(0.0, 0.0);
     for (int ka = 0; ka < kW; ++ka)
-      acc = caddd(acc, cmuld(spec[ka * kW + kr], expi(+1, (long long)freq(ka) * (kLo + ul), kFine)));
+      acc = caddd(acc, cmuld(spec[ka * kW + kr], ph.w1024((long long)freq(ka) * (kLo + ul))));
     tmp[i] = acc;
   }
   __syncthreads();
   {
     double best = -1.0;
     int bi = 0;
-    for (int i = t; i < kSpan * kSpan; i += kThreads) {
+    for (int i = t; i < kSpan * kSpan; i += kTargetThreads) {
       const int ul = i / kSpan, vl = i % kSpan;
       double2 acc = make_double2(0.0, 0.0);
       for (int kr = 0; kr < kW; ++kr)
-        acc = caddd(acc, cmuld(tmp[ul * kW + kr], expi(+1, (long long)freq(kr) * (kLo + vl), kFine)));
+        acc = caddd(acc, cmuld(tmp[ul * kW + kr], ph.w1024((long long)freq(kr) * (kLo + vl))));
       const double m = mag2(acc);
       if (m > best) {
         best = m;
@@ -199,7 +217,7 @@ __global__ void __launch_bounds__(kThreads) target_kernel(const T* __restrict__ 
     __syncthreads();
     if (t == 0) {
       int b = 0;
-      for (int i = 1; i < kThreads; ++i)
+      for (int i = 1; i < kTargetThreads; ++i)
         if (red_v[i] > red_v[b] || (red_v[i] == red_v[b] && red_i[i] < red_i[b])) b = i;
       fine_peak[0] = kLo + red_i[b] / kSpan;
       fine_peak[1] = kLo + red_i[b] % kSpan;
@@ -216,21 +234,21 @@ __global__ void __launch_bounds__(kThreads) target_kernel(const T* __restrict__ 
   if (t < kW) {
     double2 acc = make_double2(0.0, 0.0);
     for (int ka = 0; ka < kW; ++ka)
-      acc = caddd(acc, cmuld(spec[ka * kW + t], expi(+1, (long long)freq(ka) * ua, kFine)));
+      acc = caddd(acc, cmuld(spec[ka * kW + t], ph.w1024((long long)freq(ka) * ua)));
     row[t] = acc;
   } else if (t < 2 * kW) {
     const int ka = t - kW;
     double2 acc = make_double2(0.0, 0.0);
     for (int kr = 0; kr < kW; ++kr)
-      acc = caddd(acc, cmuld(spec[ka * kW + kr], expi(+1, (long long)freq(kr) * ur, kFine)));
+      acc = caddd(acc, cmuld(spec[ka * kW + kr], ph.w1024((long long)freq(kr) * ur)));
     col[ka] = acc;
   }
   __syncthreads();
-  for (int i = t; i < 2 * kFine; i += kThreads) {
+  for (int i = t; i < 2 * kFine; i += kTargetThreads) {
     const int which = i / kFine, u = i % kFine;
     const double2* v = which == 0 ? row : col;
     double2 acc = make_double2(0.0, 0.0);
-    for (int k = 0; k < kW; ++k) acc = caddd(acc, cmuld(v[k], expi(+1, (long long)freq(k) * u, kFine)));
+    for (int k = 0; k < kW; ++k) acc = caddd(acc, cmuld(v[k], ph.w1024((long long)freq(k) * u)));
     cut[i] = sqrt(mag2(acc)) * norm;
   }
   __syncthreads();
@@ -324,12 +342,12 @@ __global__ void snr_kernel(const double* __restrict__ partial, int blocks, int k
 template <class T>
 cudaError_t launch_typed(const void* img, long long n_az, long long n_rg, const int* targets, int k, int guard,
                          double* out, void* ws, cudaStream_t s) {
-  const size_t smem = size_t(2 * kW * kW) * sizeof(double2) + size_t(2 * kFine) * sizeof(double);
+  const size_t smem = size_t(2 * kW * kW + kW + kFine) * sizeof(double2) + size_t(2 * kFine) * sizeof(double);
   auto kern = target_kernel<T>;
   // Set once per instantiation, thread-safely (function-local static).
   static const cudaError_t setup = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (setup != cudaSuccess) return setup;
-  kern<<<k, kThreads, smem, s>>>(static_cast<const T*>(img), n_az, n_rg, targets, out);
+  kern<<<k, kTargetThreads, smem, s>>>(static_cast<const T*>(img), n_az, n_rg, targets, out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   unsigned char* keep_a = static_cast<unsigned char*>(ws);

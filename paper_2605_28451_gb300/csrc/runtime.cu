@@ -1183,6 +1183,48 @@ int bfp_spectral_adaptive(const void* x, int x_dtype, const int32_t* x_exp, cons
   return cuda_status(e);
 }
 
+static int sar_arith_check(int arith, int l, int in_dtype, int out_dtype, bool azimuth);
+static cudaError_t sar_lines(int l, int arith, bool in16, bool out16, bool naive, bool tload, bool tstore,
+                             const bfp::RowArgs& a, cudaStream_t s);
+
+int bfp_spectral_filter(const void* x, int x_dtype, const void* h, int64_t h_stride, void* out, int out_dtype,
+                        int64_t n, int64_t lines, int arith, void* stream) {
+  if (lines < 0) return BFPFFT_ERR_INVALID_ARG;
+  if (arith != BFPFFT_ARITH_F32 && arith != BFPFFT_ARITH_F16 && arith != BFPFFT_ARITH_F16_MUL_F32_ACC)
+    return BFPFFT_ERR_INVALID_ARG;
+  if (h_stride != 0 && h_stride != n) return BFPFFT_ERR_INVALID_ARG;
+  const int l = log2_exact(n);
+  if (l < bfp::kSarMinLog2 || l > kSarMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
+  if (x_dtype != BFPFFT_F32 && x_dtype != BFPFFT_F16_BFP) return BFPFFT_ERR_UNSUPPORTED;
+  if (out_dtype != BFPFFT_F32 && out_dtype != BFPFFT_F16_BFP && out_dtype != BFPFFT_F16_NAIVE)
+    return BFPFFT_ERR_UNSUPPORTED;
+  if (const int ac = sar_arith_check(arith, l, x_dtype, out_dtype, false); ac != BFPFFT_OK) return ac;
+  if (lines == 0) return BFPFFT_OK;
+  if (x == nullptr || h == nullptr || out == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  if (!aligned16(x) || !aligned16(h) || !aligned16(out)) return BFPFFT_ERR_MISALIGNED;
+  if (fault("launch")) return BFPFFT_ERR_CUDA;
+  bfp::RowArgs a;
+  int st = row_args(l, &a);
+  if (st != BFPFFT_OK) return st;
+  if (arith == BFPFFT_ARITH_F16 && (st = get_twiddles16(l, false, &a.tw16)) != BFPFFT_OK) return st;
+  if (arith == BFPFFT_ARITH_F16_MUL_F32_ACC && (st = get_tc_matrix(const_cast<void**>(&a.tc_b))) != BFPFFT_OK)
+    return st;
+  a.in = x;
+  a.out = out;
+  a.h = static_cast<const float2*>(h);
+  a.h_stride = h_stride;
+  if (!device_memory(x)) {
+    a.variant = without_l2(a.variant);
+    a.no_prefetch = 1;
+  }
+  a.lines = lines;
+  a.in_stride = n;
+  a.out_stride = n;
+  const bool naive = out_dtype == BFPFFT_F16_NAIVE;
+  return cuda_status(sar_lines(l, arith, x_dtype == BFPFFT_F16_BFP, out_dtype != BFPFFT_F32, naive, false, false, a,
+                               static_cast<cudaStream_t>(stream)));
+}
+
 int sar_make_filter(const void* ref, int64_t n, int peak_normalise, void* h_out, void* stream) {
   if (ref == nullptr || h_out == nullptr) return BFPFFT_ERR_INVALID_ARG;
   if (!aligned16(ref) || !aligned16(h_out)) return BFPFFT_ERR_MISALIGNED;

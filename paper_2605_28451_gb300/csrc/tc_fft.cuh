@@ -241,7 +241,7 @@ __device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsign
         }
       }
     } else if constexpr (FILTER) {
-      const float2* hk = a.h + rho;
+      const float2* hk = a.h + line * a.h_stride + rho;
       const float inv_n = 1.0f / float(kN);
       const int row = tc::row_of<0>(rho);
       unsigned char* dst = sA + (row >> 3) * kSbo + (row & 7) * 16;

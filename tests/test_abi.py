@@ -130,6 +130,17 @@ def test_adaptive_argument_checks(lib):
     with pytest.raises(B.BfpfftError) as e:
         B.bfpfft_plan_create(32768, 4, B.F16_ADAPTIVE, B.FORWARD)
     assert e.value.status == B.ERR_UNSUPPORTED
+    sf = lib.bfp_spectral_filter
+    assert sf(16, B.F32, 16, 0, 16, B.F32, 4096, 0, B.ARITH_F32, None) == B.OK                 # no lines
+    assert sf(16, B.F32, 16, 0, 16, B.F32, 4096, -1, B.ARITH_F32, None) == B.ERR_INVALID_ARG
+    assert sf(16, B.F32, 16, 7, 16, B.F32, 4096, 4, B.ARITH_F32, None) == B.ERR_INVALID_ARG    # stride not 0 or n
+    assert sf(16, B.F32, 16, 4096, 16, B.F32, 4096, 4, 9, None) == B.ERR_INVALID_ARG            # unknown arith
+    assert sf(16, B.F32, 16, 0, 16, B.F32, 128, 4, B.ARITH_F32, None) == B.ERR_UNSUPPORTED      # n below 256
+    assert sf(16, B.E4M3_BFP, 16, 0, 16, B.F32, 4096, 4, B.ARITH_F32, None) == B.ERR_UNSUPPORTED
+    assert sf(16, B.F32, 16, 0, 16, B.F32, 4096, 4, B.ARITH_F16, None) == B.ERR_UNSUPPORTED     # FP16 mode, FP32 out
+    assert sf(16, B.F32, 16, 0, 16, B.F16_BFP, 2048, 4, B.ARITH_F16_MUL_F32_ACC, None) == B.ERR_UNSUPPORTED
+    assert sf(None, B.F32, 16, 0, 16, B.F32, 4096, 4, B.ARITH_F32, None) == B.ERR_INVALID_ARG
+    assert sf(17, B.F32, 16, 0, 16, B.F32, 4096, 4, B.ARITH_F32, None) == B.ERR_MISALIGNED
     assert lib.bfp_spectral_adaptive(16, B.F32, None, 16, 16, 16, 32768, 4, None) == B.ERR_UNSUPPORTED
     assert lib.bfp_spectral_adaptive(16, B.E4M3_BFP, None, 16, 16, 16, 4096, 4, None) == B.ERR_UNSUPPORTED
     assert lib.bfp_spectral_adaptive(16, B.F32, 16, 16, 16, 16, 4096, 4, None) == B.ERR_INVALID_ARG
