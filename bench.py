@@ -666,29 +666,41 @@ def _bench_autofocus(B, torch, dev, stream):
     ha = torch.empty(n, dtype=torch.complex64, device=dev)
     B.sar_make_filter(torch.from_numpy(ref.astype("complex64")).to(dev), n, True, ha, stream)
     phi = torch.from_numpy(synth.phase_error(n).astype("float32")).to(dev)
-    ws = GA.Workspace(n, dev)
     grad = torch.empty(n, dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    out = {}
+    ref_grad = None
+    for name, arith in (("fp32_arithmetic", B.ARITH_F32), ("tensor_cores", B.ARITH_F16_MUL_F32_ACC)):
+        ws = GA.Workspace(n, dev, arith)
 
-    def step():
-        B.sar_autofocus_grad(rc, B.F16_BFP, phi, ha, n, n, grad, ws.stats, ws.buf, ws.bytes, stream)
+        def step():
+            B.sar_autofocus_grad(rc, B.F16_BFP, phi, ha, n, n, grad, ws.stats, ws.buf, ws.bytes, stream, arith)
 
-    for _ in range(3):
-        step()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ts = []
-    for i in range(10):
-        flush.fill_(i & 0xFF)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    t = statistics.median(ts)
-    # entropy pass: 2 transforms per range bin; gradient pass: 4 (recomputed forward + adjoint)
-    flops = 6 * n * 5 * n * 12
-    return {"ms_median_l2_flushed": round(t, 4), "gflops": round(flops / (t * 1e-3) / 1e9, 1),
-            "alg_gbs": round(3 * 4 * n * n / (t * 1e-3) / 1e9, 1), "dtype": "FP16-BFP rc, FP32 arithmetic"}
+        for _ in range(3):
+            step()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for i in range(10):
+            flush.fill_(i & 0xFF)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        t = statistics.median(ts)
+        # entropy pass: 2 transforms per range bin; gradient pass: 4 (recomputed forward + adjoint)
+        flops = 6 * n * 5 * n * 12
+        out[name] = {"ms_median_l2_flushed": round(t, 4), "gflops": round(flops / (t * 1e-3) / 1e9, 1),
+                     "alg_gbs": round(3 * 4 * n * n / (t * 1e-3) / 1e9, 1)}
+        g = grad.double()
+        if ref_grad is None:
+            ref_grad = g.clone()
+        else:                             # the tensor-core gradient against the FP32-arithmetic one
+            out[name]["grad_rel_l2_vs_fp32_arithmetic"] = round(float((g - ref_grad).norm() / ref_grad.norm()), 6)
+    out["fp32_arithmetic"]["dtype"] = "FP16-BFP rc, FP32 arithmetic"
+    out["tensor_cores"]["dtype"] = "FP16-BFP rc, FP16 operands / FP32 accumulation"
+    out.update(out["fp32_arithmetic"])          # the step's headline figures stay at the top level
+    return out
 
 
 def _bench_uneven(B, torch, dev, stream):

@@ -476,6 +476,24 @@ int sar_autofocus_grad(const void* rc, int rc_dtype, const float* phi, const voi
                        int64_t n_rg, float* grad_out, void* stats_out, void* workspace, size_t ws_bytes,
                        void* stream);
 
+/*
+ * The same two calls in a chosen arithmetic: BFPFFT_ARITH_F32 is the calls
+ * above; BFPFFT_ARITH_F16_MUL_F32_ACC runs every transform on the tensor cores
+ * (FP16 operands at each radix-16 pass, FP32 accumulation; the filter product,
+ * |I|^2, the logarithms and all sums in FP32 / FP64 as above), n_az = 4096
+ * only.  The gradient pass scales G by a power of two taken from the largest
+ * |I|^2 of the entropy pass, so its FP16 operands stay in range; like the
+ * FP16 transforms, the mode expects unit-scale rc (|rc| well below 256) and a
+ * peak-normalised Ha.  Same workspace as above.
+ * Errors: as above; INVALID_ARG for another arith, UNSUPPORTED for another n_az.
+ */
+int sar_autofocus_entropy_arith(const void* rc, int rc_dtype, const float* phi, const void* ha, int64_t n_az,
+                                int64_t n_rg, void* stats_out, void* workspace, size_t ws_bytes, int arith,
+                                void* stream);
+int sar_autofocus_grad_arith(const void* rc, int rc_dtype, const float* phi, const void* ha, int64_t n_az,
+                             int64_t n_rg, float* grad_out, void* stats_out, void* workspace, size_t ws_bytes,
+                             int arith, void* stream);
+
 /* ---------------------------------------------------------------------------
  * FP64 metric reductions on the GPU (Section IV-B, Section VI).
  * ------------------------------------------------------------------------- */

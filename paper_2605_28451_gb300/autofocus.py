@@ -15,9 +15,12 @@ from . import bfpfft as B
 
 
 class Workspace:
-    """Device scratch for the autofocus calls at one azimuth length."""
+    """Device scratch for the autofocus calls at one azimuth length, and the
+    arithmetic they run in (BFPFFT_ARITH_F32, or ARITH_F16_MUL_F32_ACC for the
+    tensor-core transforms at n_az = 4096)."""
 
-    def __init__(self, n_az: int, device):
+    def __init__(self, n_az: int, device, arith: int = B.ARITH_F32):
+        self.arith = arith
         self.bytes = B.sar_autofocus_workspace_bytes(n_az)
         if self.bytes == 0:
             raise ValueError(f"unsupported azimuth length {n_az}")
@@ -37,7 +40,7 @@ class SarEntropy(torch.autograd.Function):
     def forward(ctx, phi, rc, ha, rc_dtype: int, ws: Workspace):
         n_rg, n_az = rc.shape[0], rc.shape[1]
         phi_c = phi.detach().contiguous()
-        B.sar_autofocus_entropy(rc, rc_dtype, phi_c, ha, n_az, n_rg, ws.stats, ws.buf, ws.bytes)
+        B.sar_autofocus_entropy(rc, rc_dtype, phi_c, ha, n_az, n_rg, ws.stats, ws.buf, ws.bytes, arith=ws.arith)
         ctx.save_for_backward(phi_c)
         ctx.rc, ctx.ha, ctx.rc_dtype, ctx.ws = rc, ha, rc_dtype, ws
         return ws.stats[2].clone()
@@ -48,7 +51,8 @@ class SarEntropy(torch.autograd.Function):
         rc, ha, ws = ctx.rc, ctx.ha, ctx.ws
         n_rg, n_az = rc.shape[0], rc.shape[1]
         grad = torch.empty(n_az, dtype=torch.float32, device=phi_c.device)
-        B.sar_autofocus_grad(rc, ctx.rc_dtype, phi_c, ha, n_az, n_rg, grad, ws.stats, ws.buf, ws.bytes)
+        B.sar_autofocus_grad(rc, ctx.rc_dtype, phi_c, ha, n_az, n_rg, grad, ws.stats, ws.buf, ws.bytes,
+                             arith=ws.arith)
         return (g_e.to(torch.float32) * grad), None, None, None, None
 
 

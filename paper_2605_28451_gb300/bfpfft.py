@@ -85,6 +85,10 @@ SIGNATURES = {
                                              ctypes.c_size_t, _vp]),
     "sar_autofocus_grad": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_int64, _c_int64, _vp, _vp, _vp,
                                           ctypes.c_size_t, _vp]),
+    "sar_autofocus_entropy_arith": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_int64, _c_int64, _vp, _vp,
+                                                   ctypes.c_size_t, ctypes.c_int, _vp]),
+    "sar_autofocus_grad_arith": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_int64, _c_int64, _vp, _vp, _vp,
+                                                ctypes.c_size_t, ctypes.c_int, _vp]),
     "sar_point_target_workspace_bytes": (ctypes.c_size_t, [_c_int64, _c_int64]),
     "sar_point_target_metrics": (ctypes.c_int, [_vp, ctypes.c_int, _c_int64, _c_int64, _vp, _c_int64, ctypes.c_int,
                                                 _vp, _vp, ctypes.c_size_t, _vp]),
@@ -341,17 +345,17 @@ def sar_autofocus_workspace_bytes(n_az: int) -> int:
 
 
 def sar_autofocus_entropy(rc, rc_dtype: int, phi, ha, n_az: int, n_rg: int, stats_out, workspace, ws_bytes: int,
-                          stream=None):
-    _check(lib().sar_autofocus_entropy(_ptr(rc), int(rc_dtype), _ptr(phi), _ptr(ha), int(n_az), int(n_rg),
-                                       _ptr(stats_out), _ptr(workspace), int(ws_bytes), _stream(stream)),
-           "sar_autofocus_entropy")
+                          stream=None, arith: int = ARITH_F32):
+    _check(lib().sar_autofocus_entropy_arith(_ptr(rc), int(rc_dtype), _ptr(phi), _ptr(ha), int(n_az), int(n_rg),
+                                             _ptr(stats_out), _ptr(workspace), int(ws_bytes), int(arith),
+                                             _stream(stream)), "sar_autofocus_entropy")
 
 
 def sar_autofocus_grad(rc, rc_dtype: int, phi, ha, n_az: int, n_rg: int, grad_out, stats_out, workspace,
-                       ws_bytes: int, stream=None):
-    _check(lib().sar_autofocus_grad(_ptr(rc), int(rc_dtype), _ptr(phi), _ptr(ha), int(n_az), int(n_rg),
-                                    _ptr(grad_out), _ptr(stats_out), _ptr(workspace), int(ws_bytes),
-                                    _stream(stream)), "sar_autofocus_grad")
+                       ws_bytes: int, stream=None, arith: int = ARITH_F32):
+    _check(lib().sar_autofocus_grad_arith(_ptr(rc), int(rc_dtype), _ptr(phi), _ptr(ha), int(n_az), int(n_rg),
+                                          _ptr(grad_out), _ptr(stats_out), _ptr(workspace), int(ws_bytes),
+                                          int(arith), _stream(stream)), "sar_autofocus_grad")
 
 
 def bfp_sqnr_sums_noalloc_max_count() -> int:

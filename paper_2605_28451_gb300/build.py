@@ -39,6 +39,7 @@ SOURCES = [
     "rows16.cu",
     "rda.cu",
     "twopass.cu",
+    "af_tc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -16,9 +16,9 @@
 // chip exactly as in fft_rows.cuh):
 //   af_phase_kernel     e^{-j phi[n]} table
 //   af_kernel<fwd>      per-CTA FP64 partials of S and sum q ln q
-//   af_stats_kernel     S, Q, E, ln S
+//   af_stats_kernel     S, Q, E, ln S (one block, FP64 tree over the partials)
 //   af_kernel<bwd>      per-CTA partial gradients (registers across rows)
-//   af_grad_kernel      sum of the partial gradients in FP64
+//   af_grad_kernel      sum of the partial gradients in FP64 (8 slices per 32 pulses)
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -231,12 +231,35 @@ af_kernel(const AfArgs a) {
   }
 }
 
-__global__ void af_stats_kernel(const double* __restrict__ sq_part, int grid, double* __restrict__ stats) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0, q = 0.0;
-    for (int b = 0; b < grid; ++b) {
-      s += sq_part[2 * b];
-      q += sq_part[2 * b + 1];
+// S and sum q ln q from the per-CTA partials: one block of kAfRedThreads, each
+// thread summing a strided share in FP64, then a shuffle and shared-memory
+// reduction.
+constexpr int kAfRedThreads = 256;
+
+__global__ void __launch_bounds__(kAfRedThreads) af_stats_kernel(const double* __restrict__ sq_part, int grid,
+                                                                 double* __restrict__ stats) {
+  __shared__ double red[2][kAfRedThreads / 32];
+  double s = 0.0, q = 0.0;
+  for (int b = threadIdx.x; b < grid; b += kAfRedThreads) {
+    s += sq_part[2 * b];
+    q += sq_part[2 * b + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, o);
+    q += __shfl_down_sync(0xffffffffu, q, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s;
+    red[1][threadIdx.x >> 5] = q;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s = 0.0;
+    q = 0.0;
+    for (int w = 0; w < kAfRedThreads / 32; ++w) {
+      s += red[0][w];
+      q += red[1][w];
     }
     stats[0] = s;
     stats[1] = q;
@@ -245,12 +268,26 @@ __global__ void af_stats_kernel(const double* __restrict__ sq_part, int grid, do
   }
 }
 
-__global__ void af_grad_kernel(const float* __restrict__ g_part, int grid, int n, float* __restrict__ grad) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
-    double acc = 0.0;
-    for (int b = 0; b < grid; ++b) acc += g_part[(long long)b * n + i];
-    grad[i] = float(acc);
+// grad[i] = sum over CTAs b of g_part[b][i], in FP64: a block covers 32
+// consecutive pulses (one per lane: coalesced rows) with 8 warps splitting
+// the CTAs between them, then adds the 8 partial sums.
+constexpr int kAfGradSlices = 8;
+
+__global__ void __launch_bounds__(32 * kAfGradSlices) af_grad_kernel(const float* __restrict__ g_part, int grid,
+                                                                    int n, float* __restrict__ grad) {
+  __shared__ double red[kAfGradSlices][32];
+  const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  double acc = 0.0;
+  if (i < n)
+    for (int b = slice; b < grid; b += kAfGradSlices) acc += g_part[(long long)b * n + i];
+  red[slice][lane] = acc;
+  __syncthreads();
+  if (slice == 0 && i < n) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < kAfGradSlices; ++k) t += red[k][lane];
+    grad[i] = float(t);
   }
 }
 
@@ -288,19 +325,48 @@ cudaError_t launch_af(int log2n, const AfArgs& a, int* grid, cudaStream_t s) {
 
 size_t af_workspace_bytes(long long n_az) {
   return size_t(kAfMaxCtas) * 2 * sizeof(double) + size_t(kAfMaxCtas) * size_t(n_az) * sizeof(float) +
-         size_t(n_az) * sizeof(float2) + 256;
+         size_t(n_az) * sizeof(float2) + size_t(kAfMaxCtas) * sizeof(float) + 256;
+}
+
+AfWorkspaceLayout af_workspace_layout(void* workspace, long long n_az) {
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  AfWorkspaceLayout l;
+  l.sq_part = reinterpret_cast<double*>(ws);
+  ws += size_t(kAfMaxCtas) * 2 * sizeof(double);
+  l.g_part = reinterpret_cast<float*>(ws);
+  ws += size_t(kAfMaxCtas) * size_t(n_az) * sizeof(float);
+  l.ph = reinterpret_cast<float2*>(ws);
+  ws += size_t(n_az) * sizeof(float2);
+  l.q_part = reinterpret_cast<float*>(ws);
+  ws += size_t(kAfMaxCtas) * sizeof(float);
+  l.qmax = reinterpret_cast<float*>(ws);
+  return l;
+}
+
+cudaError_t af_phase_table(const float* phi, float2* ph, long long n_az, cudaStream_t s) {
+  af_phase_kernel<<<int((n_az + 255) / 256), 256, 0, s>>>(phi, ph, int(n_az));
+  return cudaGetLastError();
+}
+
+cudaError_t af_entropy_stats(const double* sq_part, int grid, double* stats, cudaStream_t s) {
+  af_stats_kernel<<<1, kAfRedThreads, 0, s>>>(sq_part, grid, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t af_gradient_sum(const float* g_part, int grid, int n_az, float* grad, cudaStream_t s) {
+  af_grad_kernel<<<(n_az + 31) / 32, 32 * kAfGradSlices, 0, s>>>(g_part, grid, n_az, grad);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_autofocus(int log2n, bool rc16, const void* rc, const float* phi, const float2* ha,
                              const float2* tw, long long n_rg, double* stats, float* grad, void* workspace,
                              bool prefetch, cudaStream_t s) {
   const long long n_az = 1LL << log2n;
-  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  const AfWorkspaceLayout l = af_workspace_layout(workspace, n_az);
   AfArgs a;
-  a.sq_part = reinterpret_cast<double*>(ws);
-  a.g_part = reinterpret_cast<float*>(ws + size_t(kAfMaxCtas) * 2 * sizeof(double));
-  float2* ph = reinterpret_cast<float2*>(ws + size_t(kAfMaxCtas) * 2 * sizeof(double) +
-                                         size_t(kAfMaxCtas) * size_t(n_az) * sizeof(float));
+  a.sq_part = l.sq_part;
+  a.g_part = l.g_part;
+  float2* ph = l.ph;
   a.rc = rc;
   a.ph = ph;
   a.ha = ha;
@@ -308,19 +374,16 @@ cudaError_t launch_autofocus(int log2n, bool rc16, const void* rc, const float* 
   a.rows = n_rg;
   a.stats = stats;
   a.prefetch = prefetch;
-  af_phase_kernel<<<int((n_az + 255) / 256), 256, 0, s>>>(phi, ph, int(n_az));
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = af_phase_table(phi, ph, n_az, s);
   if (e != cudaSuccess) return e;
   int grid = 0;
   e = rc16 ? launch_af<__half2, false>(log2n, a, &grid, s) : launch_af<float2, false>(log2n, a, &grid, s);
   if (e != cudaSuccess) return e;
-  af_stats_kernel<<<1, 32, 0, s>>>(a.sq_part, grid, stats);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = af_entropy_stats(a.sq_part, grid, stats, s)) != cudaSuccess) return e;
   if (grad == nullptr) return cudaSuccess;
   e = rc16 ? launch_af<__half2, true>(log2n, a, &grid, s) : launch_af<float2, true>(log2n, a, &grid, s);
   if (e != cudaSuccess) return e;
-  af_grad_kernel<<<int((n_az + 255) / 256), 256, 0, s>>>(a.g_part, grid, int(n_az), grad);
-  return cudaGetLastError();
+  return af_gradient_sum(a.g_part, grid, int(n_az), grad, s);
 }
 
 }  // namespace bfp

@@ -23,6 +23,7 @@
 #include "bfpfft.h"
 #include "launch.h"
 #include "metrics.h"
+#include "af_tc.h"
 #include "autofocus.h"
 #include "uneven.h"
 #include "pt_metrics.h"
@@ -1498,10 +1499,12 @@ size_t sar_autofocus_workspace_bytes(int64_t n_az) {
 
 static int autofocus_common(const void* rc, int rc_dtype, const float* phi, const void* ha, int64_t n_az,
                             int64_t n_rg, float* grad_out, void* stats_out, void* workspace, size_t ws_bytes,
-                            void* stream) {
+                            int arith, void* stream) {
   if (n_rg < 0) return BFPFFT_ERR_INVALID_ARG;
+  if (arith != BFPFFT_ARITH_F32 && arith != BFPFFT_ARITH_F16_MUL_F32_ACC) return BFPFFT_ERR_INVALID_ARG;
   const int l = log2_exact(n_az);
   if (l < bfp::kAfMinLog2 || l > bfp::kAfMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
+  if (arith == BFPFFT_ARITH_F16_MUL_F32_ACC && l != 12) return BFPFFT_ERR_UNSUPPORTED;
   if (rc_dtype != BFPFFT_F32 && rc_dtype != BFPFFT_F16_BFP) return BFPFFT_ERR_UNSUPPORTED;
   if (rc == nullptr || phi == nullptr || ha == nullptr || stats_out == nullptr || workspace == nullptr)
     return BFPFFT_ERR_INVALID_ARG;
@@ -1513,22 +1516,50 @@ static int autofocus_common(const void* rc, int rc_dtype, const float* phi, cons
   bfp::RowArgs a;
   int st = row_args(l, &a);
   if (st != BFPFFT_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (arith == BFPFFT_ARITH_F16_MUL_F32_ACC) {
+    if ((st = get_tc_matrix(const_cast<void**>(&a.tc_b))) != BFPFFT_OK) return st;
+    const bfp::AfWorkspaceLayout wl = bfp::af_workspace_layout(workspace, n_az);
+    cudaError_t e = bfp::af_phase_table(phi, wl.ph, n_az, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    const bfp::AfTcWorkspace tw{wl.sq_part, wl.g_part, wl.q_part, wl.qmax, bfp::kAfMaxCtas};
+    e = bfp::launch_autofocus_tc(rc_dtype == BFPFFT_F16_BFP, rc, wl.ph, static_cast<const float2*>(ha), a, n_rg,
+                                 static_cast<double*>(stats_out), grad_out, tw, device_memory(rc), s);
+    return cuda_status(e);
+  }
   cudaError_t e = bfp::launch_autofocus(l, rc_dtype == BFPFFT_F16_BFP, rc, phi, static_cast<const float2*>(ha),
                                         a.tw, n_rg, static_cast<double*>(stats_out), grad_out, workspace,
-                                        device_memory(rc), static_cast<cudaStream_t>(stream));
+                                        device_memory(rc), s);
   return cuda_status(e);
+}
+
+int sar_autofocus_entropy_arith(const void* rc, int rc_dtype, const float* phi, const void* ha, int64_t n_az,
+                                int64_t n_rg, void* stats_out, void* workspace, size_t ws_bytes, int arith,
+                                void* stream) {
+  return autofocus_common(rc, rc_dtype, phi, ha, n_az, n_rg, nullptr, stats_out, workspace, ws_bytes, arith,
+                          stream);
+}
+
+int sar_autofocus_grad_arith(const void* rc, int rc_dtype, const float* phi, const void* ha, int64_t n_az,
+                             int64_t n_rg, float* grad_out, void* stats_out, void* workspace, size_t ws_bytes,
+                             int arith, void* stream) {
+  if (grad_out == nullptr) return BFPFFT_ERR_INVALID_ARG;
+  return autofocus_common(rc, rc_dtype, phi, ha, n_az, n_rg, grad_out, stats_out, workspace, ws_bytes, arith,
+                          stream);
 }
 
 int sar_autofocus_entropy(const void* rc, int rc_dtype, const float* phi, const void* ha, int64_t n_az,
                           int64_t n_rg, void* stats_out, void* workspace, size_t ws_bytes, void* stream) {
-  return autofocus_common(rc, rc_dtype, phi, ha, n_az, n_rg, nullptr, stats_out, workspace, ws_bytes, stream);
+  return autofocus_common(rc, rc_dtype, phi, ha, n_az, n_rg, nullptr, stats_out, workspace, ws_bytes,
+                          BFPFFT_ARITH_F32, stream);
 }
 
 int sar_autofocus_grad(const void* rc, int rc_dtype, const float* phi, const void* ha, int64_t n_az,
                        int64_t n_rg, float* grad_out, void* stats_out, void* workspace, size_t ws_bytes,
                        void* stream) {
   if (grad_out == nullptr) return BFPFFT_ERR_INVALID_ARG;
-  return autofocus_common(rc, rc_dtype, phi, ha, n_az, n_rg, grad_out, stats_out, workspace, ws_bytes, stream);
+  return autofocus_common(rc, rc_dtype, phi, ha, n_az, n_rg, grad_out, stats_out, workspace, ws_bytes,
+                          BFPFFT_ARITH_F32, stream);
 }
 
 size_t sar_point_target_workspace_bytes(int64_t n_az, int64_t n_rg) {

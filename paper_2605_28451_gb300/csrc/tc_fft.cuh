@@ -171,16 +171,17 @@ __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::aft
 // (Eq. 1), and written as the inverse transform's pass-0 input: butterfly j
 // of the inverse takes bins j + 256 r, so the 16 results form row rho_0(j)
 // of A, four 16-byte stores.
-template <int P, int MODE, bool FILTER = false>
-__device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsigned char* sA, uint64_t* bar,
-                                        uint32_t tmem, uint32_t lane_tmem, uint32_t a_base, uint32_t b_base,
-                                        uint32_t& phase, const float2* s_tw) {
+// The MMAs of one pass on the A tile as the CTA's threads left it: barrier,
+// four tcgen05.mma from one thread, commit, bounded wait.  Returns false
+// when the wait expired (all threads agree); after true the accumulators
+// may be read.
+__device__ __forceinline__ bool tc_issue_wait(int* status, uint64_t* bar, uint32_t tmem, uint32_t a_base,
+                                              uint32_t b_base, uint32_t& phase) {
   using namespace tc;
-  const int tid = threadIdx.x;
   fence_proxy_async_shared();
   fence_before();
   __syncthreads();
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     fence_after();
 #pragma unroll
     for (int t = 0; t < 2; ++t)
@@ -190,10 +191,51 @@ __device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsign
                 tc::smem_desc(b_base + 2 * kLbo * s), s > 0);
     tc::commit(bar);
   }
-  const bool arrived = mbar_wait_bounded(bar, phase, a.status);
+  const bool arrived = mbar_wait_bounded(bar, phase, status);
   if (__syncthreads_or(!arrived)) return false;
   phase ^= 1;
   fence_after();
+  return true;
+}
+
+// Sixteen FP16 pairs x[r] as the pass-0 input of butterfly j (row rho_0(j),
+// k-pairs r = 0..15): four 16-byte stores, conflict-free across a
+// quarter-warp of consecutive j.
+__device__ __forceinline__ void tc_store_row0(unsigned char* sA, int j, const uint32_t (&x)[16]) {
+  using namespace tc;
+  const int row = row_of<0>(j);
+  unsigned char* dst = sA + (row >> 3) * kSbo + (row & 7) * 16;
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    *reinterpret_cast<uint4*>(dst + c * kLbo) = make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+}
+
+// The last pass of a forward transform whose spectrum is filtered: output q
+// of butterfly rho is bin k = rho + 256 q; conj(X[k] H[k]) / N (H conjugated
+// first when CONJ_H) rounded to FP16 is the inverse's pass-0 input.
+template <bool CONJ_H>
+__device__ __forceinline__ void tc_filter_to_a(unsigned char* sA, int rho, const uint32_t (&d)[32],
+                                               const float2* __restrict__ hk) {
+  const float inv_n = 1.0f / float(tc::kN);
+  uint32_t x[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    float2 h = __ldg(hk + 256 * q);
+    if (CONJ_H) h.y = -h.y;
+    const float2 y = cmul(make_float2(__uint_as_float(d[2 * q]), __uint_as_float(d[2 * q + 1])), h);
+    const __half2 v = __floats2half2_rn(y.x * inv_n, -y.y * inv_n);
+    x[q] = *reinterpret_cast<const uint32_t*>(&v);
+  }
+  tc_store_row0(sA, rho, x);
+}
+
+template <int P, int MODE, bool FILTER = false>
+__device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsigned char* sA, uint64_t* bar,
+                                        uint32_t tmem, uint32_t lane_tmem, uint32_t a_base, uint32_t b_base,
+                                        uint32_t& phase, const float2* s_tw) {
+  using namespace tc;
+  const int tid = threadIdx.x;
+  if (!tc_issue_wait(a.status, bar, tmem, a_base, b_base, phase)) return false;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     uint32_t d[32];
@@ -241,23 +283,7 @@ __device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsign
         }
       }
     } else if constexpr (FILTER) {
-      const float2* hk = a.h + line * a.h_stride + rho;
-      const float inv_n = 1.0f / float(kN);
-      const int row = tc::row_of<0>(rho);
-      unsigned char* dst = sA + (row >> 3) * kSbo + (row & 7) * 16;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        uint32_t x[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int q = 4 * c + e;
-          const float2 y = cmul(make_float2(__uint_as_float(d[2 * q]), __uint_as_float(d[2 * q + 1])),
-                                __ldg(hk + 256 * q));
-          const __half2 v = __floats2half2_rn(y.x * inv_n, -y.y * inv_n);
-          x[e] = *reinterpret_cast<const uint32_t*>(&v);
-        }
-        *reinterpret_cast<uint4*>(dst + c * kLbo) = make_uint4(x[0], x[1], x[2], x[3]);
-      }
+      tc_filter_to_a<false>(sA, rho, d, a.h + line * a.h_stride + rho);
     } else {
       // The inverse's final conjugation is folded into the last pass's matrix.
       __half2* out = static_cast<__half2*>(a.out) + line * a.out_stride + rho;
@@ -273,30 +299,27 @@ __device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsign
   return true;
 }
 
-// 128 threads per CTA, eight CTAs per SM: eight lines in flight per SM (the
-// TMEM limit at 64 columns a line) while each CTA's passes run one after
-// another.  Persistent: CTA b takes lines b, b + grid, ...; thread 0 bulk-
-// prefetches the CTA's next line into L2.
-template <int MODE, class TIn>
-__global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(const RowArgs a) {
+// CTA set-up shared by the tensor-core kernels: the three B matrices, the
+// twiddle rows, the TMEM allocation (kTmemCols columns) and the mbarrier;
+// returns the TMEM base address.
+//   DFT-16 matrix in real form (prepared on the host in FP16, [n][k]) and two
+//   derived copies for the inverse (Eq. 1 as conj(DFT(conj(x) / N))):
+//     B_last  = B with the imaginary output rows n = 2 q + 1 negated (the
+//               final conjugation);
+//     B_first = B / N with the imaginary input columns k = 2 r + 1 negated
+//               (the conjugated, 1/N-shifted input; N = 2^12 keeps every
+//               coefficient normal in FP16, so the scaling is exact).
+//   Twiddle rows from the pass-major table: [rn][q] = W_256^{rn q} (entry
+//   16 (rn - 1) + q) and [16 + rn][t] = W_4096^{rn t} (entry
+//   240 + 256 (rn - 1) + t), rn = 1..15, q, t < 16; the rows rn = 0 are ones.
+__device__ __forceinline__ uint32_t tc_cta_setup(const void* tc_b, const float2* tw, unsigned char* smem) {
   using namespace tc;
-  extern __shared__ __align__(1024) unsigned char smem_tc[];
-  unsigned char* sA = smem_tc;
-  unsigned char* sB = smem_tc + kBOff;
-  float2* s_tw = reinterpret_cast<float2*>(smem_tc + kTwOff);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_tc + kBarOff);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_tc + kBarOff + 8);
+  unsigned char* sB = smem + kBOff;
+  float2* s_tw = reinterpret_cast<float2*>(smem + kTwOff);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kBarOff);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kBarOff + 8);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const TIn* in_lines = static_cast<const TIn*>(a.in);
-
-  // DFT-16 matrix in real form (prepared on the host in FP16, [n][k]) and two
-  // derived copies for the inverse (Eq. 1 as conj(DFT(conj(x) / N))):
-  //   B_last  = B with the imaginary output rows n = 2 q + 1 negated (the
-  //             final conjugation);
-  //   B_first = B / N with the imaginary input columns k = 2 r + 1 negated
-  //             (the conjugated, 1/N-shifted input; N = 2^12 keeps every
-  //             coefficient normal in FP16, so the scaling is exact).
-  const __half* b_src = static_cast<const __half*>(a.tc_b);
+  const __half* b_src = static_cast<const __half*>(tc_b);
   for (int i = tid; i < 32 * 32; i += kThreads) {
     const int n = i / 32, k = i % 32;
     const __half v = b_src[i];
@@ -305,13 +328,10 @@ __global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(co
     const __half vs = __float2half_rn(__half2float(v) * (1.0f / float(kN)));
     *reinterpret_cast<__half*>(sB + 2 * kBBytes + kmaj(n, k)) = (k & 1) ? __hneg(vs) : vs;
   }
-  // Twiddle rows from the pass-major table: [rn][q] = W_256^{rn q} (entry
-  // 16 (rn - 1) + q) and [16 + rn][t] = W_4096^{rn t} (entry
-  // 240 + 256 (rn - 1) + t), rn = 1..15, q, t < 16; the rows rn = 0 are ones.
   for (int i = tid; i < 2 * 256; i += kThreads) {
     const int tab = i / 256, rn = (i % 256) / 16, c = i % 16;
     s_tw[(16 * tab + rn) * kTwPitch + c] =
-        rn == 0 ? make_float2(1.0f, 0.0f) : a.tw[tab == 0 ? 16 * (rn - 1) + c : 240 + 256 * (rn - 1) + c];
+        rn == 0 ? make_float2(1.0f, 0.0f) : tw[tab == 0 ? 16 * (rn - 1) + c : 240 + 256 * (rn - 1) + c];
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
@@ -324,7 +344,39 @@ __global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(co
   fence_before();
   __syncthreads();
   fence_after();
-  const uint32_t tmem = *tslot;
+  return *tslot;
+}
+
+// CTA teardown: a wait that expired leaves `phase` at the commit it was
+// waiting for; that commit gets one more bounded wait before the tensor
+// memory is freed.
+__device__ __forceinline__ void tc_cta_teardown(bool ok, unsigned char* smem, uint32_t tmem, uint32_t phase) {
+  using namespace tc;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kBarOff);
+  if (!ok && threadIdx.x == 0) mbar_wait_bounded(bar, phase, nullptr);
+  fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  }
+}
+
+// 128 threads per CTA, eight CTAs per SM: eight lines in flight per SM (the
+// TMEM limit at 64 columns a line) while each CTA's passes run one after
+// another.  Persistent: CTA b takes lines b, b + grid, ...; thread 0 bulk-
+// prefetches the CTA's next line into L2.
+template <int MODE, class TIn>
+__global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(const RowArgs a) {
+  using namespace tc;
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  unsigned char* sA = smem_tc;
+  unsigned char* sB = smem_tc + kBOff;
+  float2* s_tw = reinterpret_cast<float2*>(smem_tc + kTwOff);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_tc + kBarOff);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const TIn* in_lines = static_cast<const TIn*>(a.in);
+
+  const uint32_t tmem = tc_cta_setup(a.tc_b, a.tw, smem_tc);
   const uint32_t lane_tmem = tmem + (uint32_t(32 * warp) << 16);
   const uint32_t a_base = smem_addr(sA), b_base = smem_addr(sB);
   const uint32_t b_first = MODE == kInverse ? b_base + 2 * kBBytes : b_base;
@@ -354,11 +406,7 @@ __global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(co
           x[r] = *reinterpret_cast<const uint32_t*>(&v);
         }
       }
-      const int row = tc::row_of<0>(j);
-      unsigned char* dst = sA + (row >> 3) * kSbo + (row & 7) * 16;
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-        *reinterpret_cast<uint4*>(dst + c * kLbo) = make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+      tc_store_row0(sA, j, x);
     }
     if constexpr (MODE == kCompress) {
       // Forward, filter (into A, conjugated and shifted), inverse: the inverse's
@@ -375,14 +423,7 @@ __global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(co
            tc_pass<2, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_last, phase, s_tw);
     }
   }
-  // A wait that expired leaves `phase` at the commit it was waiting for:
-  // give that commit one more bounded wait before the tensor memory goes.
-  if (!ok && tid == 0) mbar_wait_bounded(bar, phase, nullptr);
-  fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
-  }
+  tc_cta_teardown(ok, smem_tc, tmem, phase);
 }
 
 template <int MODE, class TIn>

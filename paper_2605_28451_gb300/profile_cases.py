@@ -10,7 +10,8 @@ Cases (FP16-BFP unless named otherwise, N = 4096 lines):
   rda16                  range-Doppler image with RCMC and range-dependent filters, 4096 x 4096, FP16
   range16                range compression of a 1024 x 4096 complex64 scene to FP16, corner-turned
   image16                range + azimuth compression of a 4096 x 4096 scene to an FP16 image
-  autofocus16            one autofocus gradient step on 4096 x 4096 FP16 range-compressed data
+  autofocus16            one autofocus gradient step on 4096 x 4096 FP16 range-compressed data (--arith
+                         f16mul: the transforms on the tensor cores)
   uneven16               a persistent uneven batch of B transforms (default 2000; lengths 256 .. 65536,
                          Zipf weights, seed 3), FP16, forward
 Inputs are seeded and synthetic.  Nothing is checked here; the tests do that.
@@ -113,13 +114,14 @@ def main():
         B.sar_make_filter(torch.from_numpy(synth.centred_reference(synth.azimuth_chirp(1024), n)
                                            .astype("complex64")).to(dev), n, True, ha, stream)
         phi = torch.from_numpy(synth.phase_error(n).astype("float32")).to(dev)
-        ws = GA.Workspace(n, dev)
+        af_arith = B.ARITH_F16_MUL_F32_ACC if args.arith == "f16mul" else B.ARITH_F32
+        ws = GA.Workspace(n, dev, af_arith)
         grad = torch.empty(n, dtype=torch.float32, device=dev)
         stats = torch.empty(4, dtype=torch.float64, device=dev)
         for _ in range(args.reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            B.sar_autofocus_grad(rc, B.F16_BFP, phi, ha, n, n, grad, stats, ws.buf, ws.bytes, stream)
+            B.sar_autofocus_grad(rc, B.F16_BFP, phi, ha, n, n, grad, stats, ws.buf, ws.bytes, stream, af_arith)
             e1.record(stream)
             times.append((e0, e1))
         bytes_per_rep = n * n * 12

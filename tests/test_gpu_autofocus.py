@@ -226,3 +226,72 @@ def test_config5_refocus_after_50_steps(config5):
     assert abs(m_fix[b]["width_azimuth_cells"] - m_true[b]["width_azimuth_cells"]) <= 0.1
     print("refocused PSLR", [round(m["pslr_db"], 2) for m in m_fix], "error-free",
           [round(m["pslr_db"], 2) for m in m_true])
+
+
+def gpu_entropy_grad_tc(u, ha, phi, dtype):
+    """gpu_entropy_grad with the transforms on the tensor cores (n_az = 4096)."""
+    import torch
+    n_az, n_rg = u.shape
+    stored = storage_round(u, dtype)
+    rc = to_device(np.ascontiguousarray(stored.T), dtype)
+    ha_d = to_device(storage_round(ha, B.F32), B.F32)
+    phi_d = torch.from_numpy(phi.astype(np.float32)).cuda()
+    ws = GA.Workspace(n_az, "cuda:0", B.ARITH_F16_MUL_F32_ACC)
+    grad = torch.empty(n_az, dtype=torch.float32, device="cuda:0")
+    B.sar_autofocus_grad(rc, dtype, phi_d, ha_d, n_az, n_rg, grad, ws.stats, ws.buf, ws.bytes,
+                         arith=B.ARITH_F16_MUL_F32_ACC)
+    torch.cuda.synchronize()
+    assert B.bfpfft_device_status() == B.OK
+    return ws.stats.cpu().numpy(), grad.cpu().numpy().astype(np.float64), stored
+
+
+@pytest.mark.parametrize("dtype", [B.F16_BFP, B.F32])
+@pytest.mark.parametrize("n_rg", [64, 1300])
+def test_tensor_core_gradient(dtype, n_rg):
+    """Entropy and adjoint with every transform on the tensor cores (FP16
+    operands, FP32 accumulation; n_az = 4096): the bars of the FP16-BFP mode
+    against the oracle's analytic adjoint (entropy 1e-3 relative, gradient
+    relative L2 <= 3e-2, cosine >= 0.999), FP64 central differences on 16
+    pulses within 3e-2, and the gradient's zero sum.  1300 range bins make the
+    persistent CTAs take several rows."""
+    _, u, ha, eps = make_sized_case(4096, n_rg)
+    phi = 0.3 * eps.astype(np.float32).astype(np.float64)
+    stats, g, stored = gpu_entropy_grad_tc(u, ha, phi, dtype)
+    ha32 = storage_round(ha, B.F32)
+    e_ref, g_ref = AF.entropy_and_grad(stored, phi, ha32)
+    assert np.all(np.isfinite(g))
+    assert stats[2] == pytest.approx(e_ref, rel=1e-3)
+    assert metrics.rel_l2(g_ref, g) <= 3e-2
+    assert np.dot(g, g_ref) / (np.linalg.norm(g) * np.linalg.norm(g_ref)) >= 0.999
+    assert abs(np.sum(g)) <= 1e-2 * np.linalg.norm(g) * np.sqrt(len(g))
+    if n_rg == 64:
+        pulses = np.random.default_rng(4).choice(4096, 16, replace=False)
+        fd = AF.central_difference(stored, phi, ha32, pulses, h=1e-4)
+        assert np.linalg.norm(g[pulses] - fd) <= 3e-2 * np.linalg.norm(fd)
+
+
+def test_config5_tensor_core_gradient_at_full_size(config5):
+    """Config 5 (4096 x 4096, FP16-BFP rc) with the tensor-core transforms,
+    against one evaluation of the oracle's adjoint at phi = 0."""
+    _, u, ha, _ = config5
+    phi = np.zeros(u.shape[0])
+    stats, g, stored = gpu_entropy_grad_tc(u, ha, phi, B.F16_BFP)
+    e_ref, g_ref = AF.entropy_and_grad(stored, phi, ha)
+    assert stats[2] == pytest.approx(e_ref, rel=1e-3)
+    assert metrics.rel_l2(g_ref, g) <= 3e-2
+    assert np.dot(g, g_ref) / (np.linalg.norm(g) * np.linalg.norm(g_ref)) >= 0.999
+
+
+def test_tensor_core_arith_checks():
+    import torch
+    ws = GA.Workspace(1024, "cuda:0")
+    rc = torch.zeros((8, 1024), dtype=torch.complex64, device="cuda:0")
+    ha = torch.zeros(1024, dtype=torch.complex64, device="cuda:0")
+    phi = torch.zeros(1024, dtype=torch.float32, device="cuda:0")
+    with pytest.raises(B.BfpfftError) as e:              # the tensor-core mode takes 4096 pulses only
+        B.sar_autofocus_entropy(rc, B.F32, phi, ha, 1024, 8, ws.stats, ws.buf, ws.bytes,
+                                arith=B.ARITH_F16_MUL_F32_ACC)
+    assert e.value.status == B.ERR_UNSUPPORTED
+    with pytest.raises(B.BfpfftError) as e:
+        B.sar_autofocus_entropy(rc, B.F32, phi, ha, 1024, 8, ws.stats, ws.buf, ws.bytes, arith=B.ARITH_F16)
+    assert e.value.status == B.ERR_INVALID_ARG
