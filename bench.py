@@ -275,22 +275,28 @@ def run_ours(args):
     small_x = x16[:256].contiguous()
     small_y = torch.empty_like(small_x)
     small_z = torch.empty_like(small_x)
-    pf = _tc_plan(B, 256, B.FORWARD)
-    pi = _tc_plan(B, 256, B.INVERSE)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    small = []
-    for i in range(30 + 5):
-        flush.fill_(i & 0xFF)
-        e0.record(stream)
-        B.bfpfft_exec(pf, small_x, small_y, stream)
-        B.bfpfft_exec(pi, small_y, small_z, stream)
-        e1.record(stream)
-        e1.synchronize()
-        if i >= 5:
-            small.append(e0.elapsed_time(e1))
-    t_small = statistics.median(small)
+
+    def small_batch(pf, pi):
+        small = []
+        for i in range(30 + 5):
+            flush.fill_(i & 0xFF)
+            e0.record(stream)
+            B.bfpfft_exec(pf, small_x, small_y, stream)
+            B.bfpfft_exec(pi, small_y, small_z, stream)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 5:
+                small.append(e0.elapsed_time(e1))
+        return statistics.median(small)
+
+    t_small = small_batch(_tc_plan(B, 256, B.FORWARD), _tc_plan(B, 256, B.INVERSE))
     gflops_small = 2.0 * FLOPS_PER_TRANSFORM * 256 / (t_small * 1e-3) / 1e9
+    # the FP32-arithmetic kernel (one 256-thread CTA per line) has the shorter per-line chain
+    t_small32 = small_batch(B.bfpfft_plan_create(N, 256, B.F16_BFP, B.FORWARD),
+                            B.bfpfft_plan_create(N, 256, B.F16_BFP, B.INVERSE))
+    gflops_small32 = 2.0 * FLOPS_PER_TRANSFORM * 256 / (t_small32 * 1e-3) / 1e9
     del flush
 
     # ---- precision modes and adaptive exponents on the same workload ------------------
@@ -349,7 +355,9 @@ def run_ours(args):
             "fp8_e4m3_storage": fp8_entry,
             "fp16_over_fp32": round(value / world / gflops32, 3),
             "inverse_launch_ms": round(inv_avg, 5),
-            "table2_batch256_l2_flushed": {"gflops": round(gflops_small, 1), "ms_median": round(t_small, 5)},
+            "table2_batch256_l2_flushed": {"gflops": round(gflops_small, 1), "ms_median": round(t_small, 5),
+                                           "fp32_arithmetic_gflops": round(gflops_small32, 1),
+                                           "fp32_arithmetic_ms_median": round(t_small32, 5)},
             "precision_modes": modes,
             "batch_sweep": sweep,
             "ms_per_step_median": round(statistics.median(step_ms), 4),
