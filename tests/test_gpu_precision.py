@@ -218,3 +218,23 @@ def test_tensor_core_rows_host_buffers_and_in_place():
     assert B.bfpfft_plan_status(fwd) == B.OK and B.bfpfft_plan_status(inv) == B.OK
     assert torch.equal(host_y, ref_y)
     assert torch.equal(inplace, ref_z)
+
+
+def test_tensor_core_rows_graph_replay():
+    """A tensor-core plan replayed through its CUDA graph gives the bits of a
+    direct call, on the first replay and after the input changes."""
+    import torch
+    n, batch = 4096, 700
+    fwd = _tc_plan(n, batch, B.FORWARD)
+    x = to_device(storage_round(synth.complex_gaussian(batch, n, seed=21), B.F16_BFP), B.F16_BFP)
+    direct, graphed = torch.empty_like(x), torch.empty_like(x)
+    B.bfpfft_exec(fwd, x, direct)
+    B.bfpfft_exec_graph(fwd, x, graphed)
+    torch.cuda.synchronize()
+    assert torch.equal(direct, graphed)
+    x.copy_(to_device(storage_round(synth.complex_gaussian(batch, n, seed=22), B.F16_BFP), B.F16_BFP))
+    B.bfpfft_exec(fwd, x, direct)
+    B.bfpfft_exec_graph(fwd, x, graphed)
+    torch.cuda.synchronize()
+    assert torch.equal(direct, graphed)
+    assert B.bfpfft_plan_status(fwd) == B.OK

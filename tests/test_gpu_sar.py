@@ -418,3 +418,23 @@ def test_tensor_core_arith_argument_checks():
     with pytest.raises(B.BfpfftError) as e:
         B.sar_azimuth_compress_arith(y, B.F32, 1, y, B.F16_BFP, h, 2048, 16, mode)
     assert e.value.status == B.ERR_UNSUPPORTED
+
+
+def test_tensor_core_range_compression_from_pinned_host_memory():
+    """A pinned host echo read in place by the tensor-core lines (no L2
+    prefetch of host memory): the bits of the device-memory call."""
+    import torch
+    n_az, n_rg = 300, 4096
+    sc = synth.point_target_scene(n_az, n_rg, aperture=16, targets=[(n_az // 2, n_rg // 2, 1.0)], noise_seed=9)
+    hr, _ = oracle_filter(synth.centred_reference(synth.range_chirp()[:480], n_rg), False)
+    dev_raw = to_device(storage_round(sc.raw, B.F32), B.F32)
+    host_raw = torch.empty(dev_raw.shape, dtype=dev_raw.dtype, pin_memory=True)
+    host_raw.copy_(dev_raw)
+    ref = empty_like_storage((n_az, n_rg), B.F16_BFP)
+    got = empty_like_storage((n_az, n_rg), B.F16_BFP)
+    mode = B.ARITH_F16_MUL_F32_ACC
+    B.sar_range_compress_arith(dev_raw, B.F32, ref, B.F16_BFP, hr, n_az, n_rg, False, mode)
+    B.sar_range_compress_arith(host_raw, B.F32, got, B.F16_BFP, hr, n_az, n_rg, False, mode)
+    torch.cuda.synchronize()
+    assert B.bfpfft_device_status() == B.OK
+    assert torch.equal(got, ref)

@@ -151,3 +151,22 @@ def test_spectral_entry_per_line_filters_other_lengths(n):
     got = spectral_entry(x, B.F16_BFP, B.F16_BFP, h, n, B.ARITH_F32)
     ok, worst = fp16_elementwise_ok(got, conv.spectral(x, h))
     assert ok, worst
+
+
+@pytest.mark.parametrize("arith,in_dtype,out_dtype,floor", MODES)
+def test_spectral_entry_in_place(arith, in_dtype, out_dtype, floor):
+    """x and out the same buffer (same storage type): the bits of the out-of-place call."""
+    import torch
+    if in_dtype != out_dtype:
+        pytest.skip("in place needs one storage type")
+    n, batch = 4096, 300
+    x = storage_round(synth.complex_gaussian(batch, n, seed=31), in_dtype)
+    h = storage_round(conv.correlation_filter(synth.complex_gaussian(1, n, seed=32)[0] / np.sqrt(n)), B.F32)
+    hd = to_device(h, B.F32)
+    src = to_device(x, in_dtype)
+    ref = torch.empty_like(src)
+    B.bfp_spectral_filter(src, in_dtype, hd, 0, ref, out_dtype, n, batch, arith)
+    buf = src.clone()
+    B.bfp_spectral_filter(buf, in_dtype, hd, 0, buf, out_dtype, n, batch, arith)
+    torch.cuda.synchronize()
+    assert torch.equal(buf, ref)
