@@ -548,6 +548,19 @@ def _bench_sar(B, torch, dev, stream):
             out["table4_modes_4096x4096"] = _bench_sar_modes(B, torch, dev, stream, raw, hr, ha, sc.targets,
                                                              n_az, n_rg, flush)
         if not full:
+            # the same call in Table IV's 16-bit modes (FP16 out, corner-turned)
+            for mname, marith in (("pure_fp16", B.ARITH_F16), ("fp16_mul_fp32_acc_tensor_cores",
+                                                                   B.ARITH_F16_MUL_F32_ACC)):
+                tm = []
+                for i in range(23):
+                    flush.fill_(i & 0xFF)
+                    e0.record(stream)
+                    B.sar_range_compress_arith(raw, B.F32, rc, B.F16_BFP, hr, n_az, n_rg, True, marith, stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if i >= 3:
+                        tm.append(e0.elapsed_time(e1))
+                out[name][mname + "_ms_median_l2_flushed"] = round(statistics.median(tm), 4)
             naive = torch.empty((n_az, n_rg, 2), dtype=torch.float16, device=dev)
             B.sar_range_compress(raw, B.F32, naive, B.F16_NAIVE, hr, n_az, n_rg, False, stream)
             torch.cuda.synchronize()

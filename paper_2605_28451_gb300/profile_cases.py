@@ -10,6 +10,7 @@ Cases (FP16-BFP unless named otherwise, N = 4096 lines):
   rda16                  range-Doppler image with RCMC and range-dependent filters, 4096 x 4096, FP16
   range16                range compression of a 1024 x 4096 complex64 scene to FP16, corner-turned
   image16                range + azimuth compression of a 4096 x 4096 scene to an FP16 image
+                         (range16, image16: --arith f16 | f16mul for Table IV's pure-FP16 and tensor-core modes)
   autofocus16            one autofocus gradient step on 4096 x 4096 FP16 range-compressed data (--arith
                          f16mul: the transforms on the tensor cores)
   uneven16               a persistent uneven batch of B transforms (default 2000; lengths 256 .. 65536,
@@ -98,12 +99,13 @@ def main():
         B.sar_make_filter(torch.from_numpy(sc.ref_azimuth.astype("complex64")).to(dev), n_az, True, ha, stream)
         rc = torch.empty((n, n_az, 2), dtype=torch.float16, device=dev)
         img = torch.empty((n_az, n, 2), dtype=torch.float16, device=dev)
+        sar_arith = {"f32": B.ARITH_F32, "f16": B.ARITH_F16, "f16mul": B.ARITH_F16_MUL_F32_ACC}[args.arith]
         for _ in range(args.reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            B.sar_range_compress(raw, B.F32, rc, B.F16_BFP, hr, n_az, n, True, stream)
+            B.sar_range_compress_arith(raw, B.F32, rc, B.F16_BFP, hr, n_az, n, True, sar_arith, stream)
             if args.case == "image16":
-                B.sar_azimuth_compress(rc, B.F16_BFP, 1, img, B.F16_BFP, ha, n_az, n, stream)
+                B.sar_azimuth_compress_arith(rc, B.F16_BFP, 1, img, B.F16_BFP, ha, n_az, n, sar_arith, stream)
             e1.record(stream)
             times.append((e0, e1))
         bytes_per_rep = n_az * n * (12 if args.case == "range16" else 20)
