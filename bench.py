@@ -746,7 +746,8 @@ def _bench_uneven(B, torch, dev, stream):
     sums = torch.empty(8, dtype=torch.float64, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     scale = None
-    for name, dtype in (("f32", B.F32), ("f16_bfp", B.F16_BFP), ("e4m3", B.E4M3_BFP), ("e5m2", B.E5M2_BFP)):
+    for name, dtype in (("f32", B.F32), ("f16_bfp", B.F16_BFP), ("f16_bfp_tuned_fp16_exchange", B.F16_BFP),
+                        ("e4m3", B.E4M3_BFP), ("e5m2", B.E5M2_BFP)):
         if dtype == B.F32:
             xin = x32
         elif dtype == B.F16_BFP:
@@ -756,6 +757,11 @@ def _bench_uneven(B, torch, dev, stream):
             xin = x32.to(f8).view(torch.uint8)
         yout = y32 if dtype == B.F32 else torch.empty_like(xin)
         plan = B.bfpfft_plan_create_many(lengths, offsets, dtype, B.FORWARD)
+        code = None
+        if name == "f16_bfp_tuned_fp16_exchange":
+            # The tuner's pick among cluster counts, two-pass long lines and the
+            # FP16 row exchange of four-step lines.
+            code, _ = B.bfpfft_plan_tune(plan, allow_fp16_exchange=True)
         for _ in range(3):
             B.bfpfft_exec_graph(plan, xin, yout, stream)
         ts = []
@@ -768,6 +774,9 @@ def _bench_uneven(B, torch, dev, stream):
         t = statistics.median(ts)
         entry = {"ms_median": round(t, 4), "gflops": round(flops / (t * 1e-3) / 1e9, 1),
                  "alg_gbs": round(total * 2 * xin.element_size() * xin.shape[-1] / (t * 1e-3) / 1e9, 1)}
+        if code is not None:
+            entry["tuned"] = {"clusters": code & 0xffff, "two_pass_long_lines": bool((code >> 16) & 1),
+                              "fp16_row_exchange": bool(code >> 17)}
         if dtype == B.F16_BFP:
             B.bfp_sqnr_sums(torch.view_as_complex(y32), B.F32, yout, B.F16_BFP, total, sums, ws, ws_bytes, stream)
             entry["sqnr_vs_f32_db"] = round(B.sqnr_from_sums(sums[:5].cpu().tolist())["aligned_db"], 2)

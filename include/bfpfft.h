@@ -150,12 +150,21 @@ int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, c
  * without an L2 prefetch one wave ahead, at 3 or 4 CTAs per SM, or bulk-copy
  * pipelined; one or two FP32 exchange buffers; with allow_fp16_exchange != 0
  * and FP16 storage also the FP16 shared-memory exchanges, which round at
- * every pass and so change the results within the FP16 error budget); an
- * uneven plan: the number of persistent clusters -- on scratch buffers it
- * allocates and frees (synchronous), keeps the fastest in the plan, and
- * writes it to the tuning cache (file named by BFPFFT_TUNE_CACHE, default
- * $HOME/.cache/bfpfft/tune.txt, keyed by GPU name and shape).  chosen: the
- * variant code or cluster count; best_ms (may be NULL): its median time.
+ * every pass and so change the results within the FP16 error budget; lines
+ * of 32768 and 65536 points: the four-step kernel or the two-pass kernels,
+ * and with allow_fp16_exchange the four-step kernel with its row exchange in
+ * FP16 words); an uneven plan: the number of persistent clusters, whether
+ * lines of 32768 / 65536 points run inside the persistent kernel or in the
+ * two-pass kernels before it, and with allow_fp16_exchange and FP16 storage
+ * whether lines of 8192 points or more exchange their rows in FP16 words --
+ * on scratch buffers it allocates and frees (synchronous), keeps the fastest
+ * in the plan, and writes it to the tuning cache (file named by
+ * BFPFFT_TUNE_CACHE, default $HOME/.cache/bfpfft/tune.txt, keyed by GPU name
+ * and shape).  chosen: a uniform plan's variant code, or an uneven plan's
+ * clusters + 65536 * (two-pass long lines) + 131072 * (FP16 row exchange);
+ * best_ms (may be NULL): its median time.  An FP16 row exchange is one more
+ * FP16 storage point: every output stays within the FP16 error budget, not
+ * within one rounding of the FP32 result.
  * Plans created while BFPFFT_TUNE=cached apply a cached choice;
  * BFPFFT_TUNE=full also tunes shapes missing from the cache.  The variable
  * BFPFFT_ROWS, when set, overrides any tuned row variant.

@@ -75,6 +75,8 @@ struct RowArgs {
   int no_prefetch;         // nonzero: the input is not device memory; no bulk L2 prefetch of it
   int* finite_flag;        // non-null: dense-row stores record non-finite outputs here (BFPFFT_CHECK_FINITE)
   const void* tw16;        // 16-bit arithmetic rows: pass-major table of (w, -i conj w) 16-bit pairs
+  int fs_h16;              // FP16 storage, lines of 8192 points or more by the four-step kernel: nonzero sends
+                           // the row exchange between the column and row transforms as FP16 words
   const int* in_exp;       // adaptive exponents: per-line input exponents (value = stored * 2^e), or null
   int* out_exp;            // adaptive exponents: per-line output exponents written by the kernel
 };
@@ -840,7 +842,7 @@ __host__ __device__ constexpr size_t fourstep_smem_bytes() {
   return size_t(pad16(4096)) * sizeof(float2) + (N1 >= 8 ? size_t(N1) * (4096 / N1 + kPad) * sizeof(Word) : 0);
 }
 
-template <int N1, class TS, int MODE, bool SCALED>
+template <int N1, class TS, int MODE, bool SCALED, bool H16ROW = false>
 __device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS* out, float2* smem, uint64_t* bar,
                                               uint64_t* bar_out, uint32_t& phase, int& pending, int c,
                                               int base_rank, bool active) {
@@ -852,8 +854,11 @@ __device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS
   constexpr bool kOutXch = N1 >= 8;
   using Word = typename FsSend<TS>::Word;
   constexpr int kPadOut = sizeof(Word) == 4 ? 2 : 1;    // conflict-free gather
+  // H16ROW with FP16 storage: the row arrives as FP16 words (one more FP16
+  // storage point, half the exchange bytes); otherwise as FP32 pairs.
+  constexpr bool h16row = H16ROW && std::is_same<TS, __half2>::value;
   if (t == 0) {
-    mbar_arrive_expect_tx(bar, 4096 * sizeof(float2));
+    mbar_arrive_expect_tx(bar, 4096u * uint32_t(h16row ? sizeof(uint32_t) : sizeof(float2)));
     if constexpr (kOutXch) mbar_arrive_expect_tx(bar_out, 4096 * sizeof(Word));
   }
   float2* smem_out = smem + pad16(4096);
@@ -879,17 +884,22 @@ __device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS
 #pragma unroll
     for (int i = 0; i < N1; ++i) u[i] = v[b * N1 + i];
     Dft<N1>::run(u);
-    const uint32_t slot = smem_base + uint32_t(pad16(n2)) * sizeof(float2);
+    const uint32_t slot = h16row ? smem_base + uint32_t(n2) * 4u : smem_base + uint32_t(pad16(n2)) * sizeof(float2);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) {
       const float2 z = k1 == 0 ? u[0] : cmul(u[k1], __ldg(a.tw_4step + k1 * 4096 + n2));
-      st_async_f2(mapa(slot, base_rank + k1), z, mapa(bar_local, base_rank + k1));
+      if constexpr (h16row) {
+        st_async_b32(mapa(slot, base_rank + k1), half2_bits(z), mapa(bar_local, base_rank + k1));
+      } else {
+        st_async_f2(mapa(slot, base_rank + k1), z, mapa(bar_local, base_rank + k1));
+      }
     }
   }
   // The row is complete when all 32 KB have landed (bounded wait).
   const bool row_ok = mbar_wait_bounded(bar, phase, a.status);
 #pragma unroll
-  for (int m = 0; m < P; ++m) v[m] = smem[pad16(t + 256 * m)];
+  for (int m = 0; m < P; ++m)
+    v[m] = h16row ? bits_half2(reinterpret_cast<const uint32_t*>(smem)[t + 256 * m]) : smem[pad16(t + 256 * m)];
   if (__syncthreads_or(!row_ok)) {
     pending = kOutXch ? 3 : 1;
     return false;
@@ -971,7 +981,7 @@ __device__ __forceinline__ void fourstep_drain(uint64_t* bar, uint64_t* bar_out,
 
 // Uniform plans with N >= 8192: one line per group of N / 4096 CTAs, a
 // cluster per line.
-template <int N, class TS, int MODE, bool SCALED>
+template <int N, class TS, int MODE, bool SCALED, bool H16ROW>
 // Four CTAs per SM (64 registers) where their shared memory fits, else three.
 __global__ void __launch_bounds__(256, fourstep_smem_bytes<TS, N / 4096>() * 4 <= 220 * 1024 ? 4 : 3)
     fft_fourstep_kernel(const RowArgs a) {
@@ -1000,18 +1010,18 @@ __global__ void __launch_bounds__(256, fourstep_smem_bytes<TS, N / 4096>() * 4 <
   cluster_wait_acquire();
   uint32_t phase = 0;
   int pending = 0;
-  if (!fourstep_line<N1, TS, MODE, SCALED>(a, in, out, smem_fs, &bar, &bar_out, phase, pending, c, 0, true))
+  if (!fourstep_line<N1, TS, MODE, SCALED, H16ROW>(a, in, out, smem_fs, &bar, &bar_out, phase, pending, c, 0, true))
     fourstep_drain(&bar, &bar_out, phase, pending);
   // No CTA leaves while a peer's asynchronous stores may still be in flight:
   // every CTA has received what it waited for (or drained it) before arriving.
   cluster_barrier_relaxed();
 }
 
-template <int N, class TS, int MODE, bool SCALED>
+template <int N, class TS, int MODE, bool SCALED, bool H16ROW = false>
 cudaError_t launch_fourstep_n(const RowArgs& a, cudaStream_t stream) {
   constexpr int N1 = N / 4096;
   constexpr size_t kBytes = fourstep_smem_bytes<TS, N / 4096>();
-  auto kern = fft_fourstep_kernel<N, TS, MODE, SCALED>;
+  auto kern = fft_fourstep_kernel<N, TS, MODE, SCALED, H16ROW>;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = kBytes;
@@ -1157,8 +1167,12 @@ cudaError_t launch_rows_n(const RowArgs& a, cudaStream_t stream) {
   // cluster kernel.
   if constexpr (!TLOAD && !TSTORE && N >= 32768) {
     if constexpr (MODE != kCompress && !NAIVE && std::is_same<TIn, TOut>::value) {
-      if (a.tw_4step != nullptr && a.in_stride == N && a.out_stride == N)
+      if (a.tw_4step != nullptr && a.in_stride == N && a.out_stride == N) {
+        if constexpr (std::is_same<TIn, __half2>::value) {
+          if (a.fs_h16) return launch_fourstep_n<N, TIn, MODE, SCALED, true>(a, stream);
+        }
         return launch_fourstep_n<N, TIn, MODE, SCALED>(a, stream);
+      }
     }
   }
   if constexpr (!TLOAD && !TSTORE && N > 16384) {

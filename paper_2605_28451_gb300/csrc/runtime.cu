@@ -74,6 +74,22 @@ int without_l2(int variant) {
   }
 }
 
+// Variants whose exchanges round to FP16 (FP16 storage only); with one of
+// them, lines of 8192 points or more by the four-step kernel also exchange
+// their rows as FP16 words.
+bool fp16_exchange_variant(int variant) {
+  switch (variant) {
+    case bfp::kRowsPlainH:
+    case bfp::kRowsPlainHPP:
+    case bfp::kRowsTmaH:
+    case bfp::kRowsTmaHPP:
+    case bfp::kRowsPlainHL2:
+    case bfp::kRowsPlainH4L2:
+    case bfp::kRowsPlainHS4L2: return true;
+    default: return false;
+  }
+}
+
 // Host-side fault injection for the error paths: BFPFFT_FAULT=plan|alloc|launch
 // makes the named step fail without touching the GPU.
 bool fault(const char* step) {
@@ -401,6 +417,8 @@ struct bfpfft_plan_s {
   int tuned_clusters = 0;               // persistent clusters chosen by the tuner (0: all resident)
   int long_twopass = 0;                 // lines of 32768 / 65536 points by the two-pass kernels (1) or in the
                                         // persistent kernel's four-step lines (0)
+  int fs_h16 = 0;                       // FP16 storage: four-step lines exchange their rows as FP16 words (1)
+  int has_fourstep = 0;                 // some line has 8192 points or more
   int first_short_task = 0;             // first task of a length below 32768
   long long long_first[2] = {0, 0};     // lines of 65536 / 32768 points: first index into d_line_off ...
   long long long_count[2] = {0, 0};     // ... and count
@@ -543,6 +561,10 @@ static int exec_many(bfpfft_plan plan, const void* in, void* out, cudaStream_t s
   a.counter = plan->d_counter;
   a.status = plan->status;
   a.finite_flag = (plan->flags & BFPFFT_CHECK_FINITE) ? plan->status : nullptr;
+  // BFPFFT_ROWS naming an FP16-exchange variant forces the FP16 row exchange
+  // of four-step lines (tests); otherwise the tuner's choice.
+  a.fs_h16 = plan->kind == 1 && (plan->fs_h16 || (std::getenv("BFPFFT_ROWS") != nullptr &&
+                                                  fp16_exchange_variant(variant)));
   a.prefetch = (variant == bfp::kRowsPlainL2 || variant == bfp::kRowsPlain4L2 || variant == bfp::kRowsPlainHL2 ||
                 variant == bfp::kRowsPlainH4L2 || variant == bfp::kRowsPlainHS4L2 || variant == bfp::kRowsTwoPass) &&
                device_memory(in);
@@ -679,17 +701,26 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
   if (!plan->many) plan->batch = sample_batch;
   std::vector<int> candidates;
   const int saved_long = plan->long_twopass;
+  const int saved_fs_h16 = plan->fs_h16;
   if (plan->many) {
-    // Uneven plans: the persistent cluster count, and whether lines of 32768 /
+    // Uneven plans: the persistent cluster count; whether lines of 32768 /
     // 65536 points run as four-step lines inside the persistent kernel or as
-    // the two-pass kernels before it (code = clusters + 65536 * two-pass).
+    // the two-pass kernels before it; with allow_fp16_exchange and FP16
+    // storage, whether four-step lines exchange their rows as FP16 words
+    // (code = clusters + 65536 * two-pass + 131072 * FP16 row exchange).
     const bool has_long = plan->first_short_task > 0;
-    for (int c = plan->clusters; c >= 1 && candidates.size() < 8; c = c * 3 / 4) {
-      candidates.push_back(c);
-      if (has_long) candidates.push_back(c + 65536);
+    const bool h16 = allow_fp16_exchange && plan->kind == 1 && plan->has_fourstep;
+    const size_t per_count = size_t(1 + (has_long ? 1 : 0)) * (h16 ? 2 : 1);
+    for (int c = plan->clusters; c >= 1 && candidates.size() + per_count <= (h16 ? 12u : 8u); c = c * 3 / 4) {
+      for (int mode = 0; mode < 4; ++mode) {
+        if (((mode & 1) && !has_long) || ((mode & 2) && !h16)) continue;
+        candidates.push_back(c + 65536 * mode);
+      }
     }
   } else if (plan->log2n >= 15) {
     candidates = {bfp::kRowsPlain4L2, bfp::kRowsTwoPass};
+    // four-step lines with the FP16 row exchange
+    if (allow_fp16_exchange && plan->dtype == BFPFFT_F16_BFP) candidates.push_back(bfp::kRowsPlainHL2);
   } else {
     candidates = {bfp::kRowsPlain4L2, bfp::kRowsPlainL2, bfp::kRowsPlain, bfp::kRowsPlain4,
                   bfp::kRowsTma,        bfp::kRowsPlainPP, bfp::kRowsTmaPP};
@@ -709,7 +740,8 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
   for (int c : candidates) {
     if (plan->many) {
       plan->tuned_clusters = c & 0xffff;
-      plan->long_twopass = c >> 16;
+      plan->long_twopass = (c >> 16) & 1;
+      plan->fs_h16 = (c >> 17) & 1;
     } else {
       plan->variant = c;
     }
@@ -732,6 +764,7 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
   if (plan->many) {
     plan->tuned_clusters = saved_clusters;
     plan->long_twopass = saved_long;
+    plan->fs_h16 = saved_fs_h16;
   } else {
     plan->variant = saved_variant;
   }
@@ -742,7 +775,8 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
   if (st != BFPFFT_OK) return st;
   if (plan->many) {
     plan->tuned_clusters = best & 0xffff;
-    plan->long_twopass = best >> 16;
+    plan->long_twopass = (best >> 16) & 1;
+    plan->fs_h16 = (best >> 17) & 1;
   } else {
     plan->variant = best;
   }
@@ -769,7 +803,8 @@ void tune_on_create(bfpfft_plan p) {
     if (it != g_tune.end()) {
       if (p->many) {
         p->tuned_clusters = it->second.first & 0xffff;
-        p->long_twopass = it->second.first >> 16;
+        p->long_twopass = (it->second.first >> 16) & 1;
+        p->fs_h16 = p->kind == 1 ? (it->second.first >> 17) & 1 : 0;
       } else {
         p->variant = it->second.first;
       }
@@ -889,6 +924,8 @@ int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, c
   p->num_tasks = int(tasks.size());
   // Tasks are sorted longest first: lines of 65536 and 32768 points come first.
   p->first_short_task = 0;
+  for (const auto& t : tasks)
+    if (t.log2n >= 13) p->has_fourstep = 1;
   for (const auto& t : tasks) {
     if (t.log2n < 15) break;
     ++p->first_short_task;
@@ -973,6 +1010,7 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
     a.variant = without_l2(a.variant);
     a.no_prefetch = 1;
   }
+  a.fs_h16 = plan->dtype == BFPFFT_F16_BFP && fp16_exchange_variant(a.variant);
   if (plan->log2n >= 15 && a.variant == bfp::kRowsTwoPass && plan->dtype != BFPFFT_F16_NAIVE &&
       plan->dtype != BFPFFT_BF16 && plan->dtype != BFPFFT_F16_ADAPTIVE) {
     return run_twopass(uneven_kind(plan->dtype), plan->log2n,

@@ -31,7 +31,7 @@ constexpr int kSlab = 4096;     // points of one line per CTA (N >= 4096)
 
 // Returns false when a bounded wait of a four-step line expired (the CTA
 // then stops working, see uneven_kernel); `pending` as in fourstep_line.
-template <class TS, int MODE, bool SCALED, int LOG2N>
+template <class TS, int MODE, bool SCALED, bool H16ROW, int LOG2N>
 __device__ __noinline__ bool run_task(const UnevenArgs& a, const UnevenTask& tk, int rank, float2* smem,
                                       uint64_t* bar, uint32_t& phase, int& pending) {
   constexpr int N = 1 << LOG2N;
@@ -75,7 +75,7 @@ __device__ __noinline__ bool run_task(const UnevenArgs& a, const UnevenTask& tk,
     const long long off = active ? a.line_off[tk.first + idx] : 0;
     ra.tw_line = a.tw[12];
     ra.tw_4step = a.tw4[LOG2N];
-    return fourstep_line<C, TS, MODE, SCALED>(ra, static_cast<const TS*>(a.in) + off,
+    return fourstep_line<C, TS, MODE, SCALED, H16ROW>(ra, static_cast<const TS*>(a.in) + off,
                                               static_cast<TS*>(a.out) + off, smem, bar, bar + 1, phase, pending,
                                               rank - base, base, active);
   }
@@ -105,7 +105,9 @@ __device__ __forceinline__ void prefetch_task(const UnevenArgs& a, int task, int
   }
 }
 
-template <class TS, int MODE, bool SCALED>
+// H16ROW (FP16 storage only): four-step lines exchange their rows as FP16
+// words.
+template <class TS, int MODE, bool SCALED, bool H16ROW>
 // Four CTAs per SM (64 registers) where their shared memory fits (FP16
 // storage), else three.
 __global__ void __launch_bounds__(kCta, uneven_smem_bytes<TS>() * 4 <= 220 * 1024 ? 4 : 3)
@@ -143,19 +145,19 @@ __global__ void __launch_bounds__(kCta, uneven_smem_bytes<TS>() * 4 <= 220 * 102
       if (a.prefetch) prefetch_task<TS>(a, task + clusters, rank);
       bool ok = true;
       switch (tk.log2n) {
-        case 4: ok = run_task<TS, MODE, SCALED, 4>(a, tk, rank, smem_u, bar, phase, pending); break;
-        case 5: ok = run_task<TS, MODE, SCALED, 5>(a, tk, rank, smem_u, bar, phase, pending); break;
-        case 6: ok = run_task<TS, MODE, SCALED, 6>(a, tk, rank, smem_u, bar, phase, pending); break;
-        case 7: ok = run_task<TS, MODE, SCALED, 7>(a, tk, rank, smem_u, bar, phase, pending); break;
-        case 8: ok = run_task<TS, MODE, SCALED, 8>(a, tk, rank, smem_u, bar, phase, pending); break;
-        case 9: ok = run_task<TS, MODE, SCALED, 9>(a, tk, rank, smem_u, bar, phase, pending); break;
-        case 10: ok = run_task<TS, MODE, SCALED, 10>(a, tk, rank, smem_u, bar, phase, pending); break;
-        case 11: ok = run_task<TS, MODE, SCALED, 11>(a, tk, rank, smem_u, bar, phase, pending); break;
-        case 12: ok = run_task<TS, MODE, SCALED, 12>(a, tk, rank, smem_u, bar, phase, pending); break;
-        case 13: ok = run_task<TS, MODE, SCALED, 13>(a, tk, rank, smem_u, bar, phase, pending); break;
-        case 14: ok = run_task<TS, MODE, SCALED, 14>(a, tk, rank, smem_u, bar, phase, pending); break;
-        case 15: ok = run_task<TS, MODE, SCALED, 15>(a, tk, rank, smem_u, bar, phase, pending); break;
-        case 16: ok = run_task<TS, MODE, SCALED, 16>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 4: ok = run_task<TS, MODE, SCALED, H16ROW, 4>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 5: ok = run_task<TS, MODE, SCALED, H16ROW, 5>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 6: ok = run_task<TS, MODE, SCALED, H16ROW, 6>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 7: ok = run_task<TS, MODE, SCALED, H16ROW, 7>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 8: ok = run_task<TS, MODE, SCALED, H16ROW, 8>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 9: ok = run_task<TS, MODE, SCALED, H16ROW, 9>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 10: ok = run_task<TS, MODE, SCALED, H16ROW, 10>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 11: ok = run_task<TS, MODE, SCALED, H16ROW, 11>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 12: ok = run_task<TS, MODE, SCALED, H16ROW, 12>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 13: ok = run_task<TS, MODE, SCALED, H16ROW, 13>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 14: ok = run_task<TS, MODE, SCALED, H16ROW, 14>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 15: ok = run_task<TS, MODE, SCALED, H16ROW, 15>(a, tk, rank, smem_u, bar, phase, pending); break;
+        case 16: ok = run_task<TS, MODE, SCALED, H16ROW, 16>(a, tk, rank, smem_u, bar, phase, pending); break;
         default: break;
       }
       aborted = !ok;
@@ -180,9 +182,9 @@ __global__ void __launch_bounds__(kCta, uneven_smem_bytes<TS>() * 4 <= 220 * 102
   if (aborted) fourstep_drain(&bar[0], &bar[1], phase, pending);
 }
 
-template <class TS, int MODE, bool SCALED>
+template <class TS, int MODE, bool SCALED, bool H16ROW = false>
 cudaError_t launch_typed(const UnevenArgs& a, int clusters, cudaStream_t s) {
-  auto kern = uneven_kernel<TS, MODE, SCALED>;
+  auto kern = uneven_kernel<TS, MODE, SCALED, H16ROW>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(clusters * kClusterCtas));
   cfg.blockDim = dim3(kCta);
@@ -198,13 +200,25 @@ cudaError_t launch_typed(const UnevenArgs& a, int clusters, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-template <class TS, int MODE, bool SCALED>
-cudaError_t configure_typed(int* max_clusters) {
-  auto kern = uneven_kernel<TS, MODE, SCALED>;
+template <class TS, int MODE, bool SCALED, bool H16ROW>
+cudaError_t set_attributes() {
+  auto kern = uneven_kernel<TS, MODE, SCALED, H16ROW>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
-  if (uneven_smem_bytes<TS>() > 48 * 1024) {
+  if (uneven_smem_bytes<TS>() > 48 * 1024)
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(uneven_smem_bytes<TS>()));
+  return e;
+}
+
+// Attributes of the kernel (both exchange forms for FP16 storage, which share
+// their shared memory size and so their occupancy) and its resident clusters.
+template <class TS, int MODE, bool SCALED>
+cudaError_t configure_typed(int* max_clusters) {
+  auto kern = uneven_kernel<TS, MODE, SCALED, false>;
+  cudaError_t e = set_attributes<TS, MODE, SCALED, false>();
+  if (e != cudaSuccess) return e;
+  if constexpr (std::is_same<TS, __half2>::value) {
+    e = set_attributes<TS, MODE, SCALED, true>();
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg = {};
@@ -230,8 +244,10 @@ cudaError_t dispatch(int kind, bool configure, const UnevenArgs* a, int clusters
   switch (kind) {
     case 0: return configure ? configure_typed<float2, MODE, false>(max_clusters)
                              : launch_typed<float2, MODE, false>(*a, clusters, s);
-    case 1: return configure ? configure_typed<__half2, MODE, false>(max_clusters)
-                             : launch_typed<__half2, MODE, false>(*a, clusters, s);
+    case 1:
+      if (configure) return configure_typed<__half2, MODE, false>(max_clusters);
+      return a->fs_h16 ? launch_typed<__half2, MODE, false, true>(*a, clusters, s)
+                       : launch_typed<__half2, MODE, false>(*a, clusters, s);
     case 2: return configure ? configure_typed<A, MODE, true>(max_clusters)
                              : launch_typed<A, MODE, true>(*a, clusters, s);
     case 3: return configure ? configure_typed<B, MODE, true>(max_clusters)

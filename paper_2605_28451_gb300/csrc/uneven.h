@@ -26,6 +26,7 @@ struct UnevenArgs {
   int* status;
   int prefetch;                  // nonzero: prefetch each CTA's lines of the next task into L2
   int* finite_flag;              // non-null: record non-finite outputs here (BFPFFT_CHECK_FINITE)
+  int fs_h16;                    // FP16 storage: four-step lines exchange their rows as FP16 words
 };
 
 // Row and output buffers of the longest four-step line (N1 = 16), for the

@@ -50,21 +50,27 @@ def run_many(data, lengths, offsets, dtype, direction, graph=False, reps=1):
 MIXED = [65536, 16, 4096, 256, 16384, 1024, 8192, 32, 4096, 32768, 512, 2048, 64, 128, 65536, 256, 4096] * 2
 
 
-@pytest.fixture(params=["fourstep", "twopass"])
+@pytest.fixture(params=["fourstep", "twopass", "fourstep_h16"])
 def long_lines(request, monkeypatch):
     """Lines of 32768 / 65536 points inside the persistent kernel (four-step) or
-    split off to the two-pass kernels (BFPFFT_ROWS=twopass forces the split)."""
+    split off to the two-pass kernels (BFPFFT_ROWS=twopass forces the split);
+    fourstep_h16: four-step lines with their row exchange in FP16 words
+    (BFPFFT_ROWS naming an FP16-exchange variant forces it)."""
     if request.param == "twopass":
         monkeypatch.setenv("BFPFFT_ROWS", "twopass")
+    elif request.param == "fourstep_h16":
+        monkeypatch.setenv("BFPFFT_ROWS", "h16_l2")
     else:
         monkeypatch.delenv("BFPFFT_ROWS", raising=False)
     return request.param
 
 
 def fp16_line_ok(g, ref, n, long_lines):
-    """FP16 parity of one line; the two-pass intermediate is one more FP16
-    storage point (the FP16-exchange bound of the uniform row tests)."""
-    if long_lines == "twopass" and n >= 32768:
+    """FP16 parity of one line.  The two-pass intermediate (lines of 32768
+    points or more) and the FP16 row exchange of four-step lines (8192 points
+    or more) are one more FP16 storage point: the FP16-exchange bound of the
+    uniform row tests."""
+    if (long_lines == "twopass" and n >= 32768) or (long_lines == "fourstep_h16" and n >= 8192):
         rms = np.sqrt(np.mean(np.abs(ref) ** 2))
         bound = 2.0 ** -11 * (np.abs(ref) + 6.0 * rms)
         return (np.all(np.abs(g.real - ref.real) <= bound) and np.all(np.abs(g.imag - ref.imag) <= bound)
@@ -216,3 +222,34 @@ def test_tuner_with_fp16_exchanges_allowed(tmp_path, monkeypatch):
     assert B.bfpfft_device_status() == B.OK
     got = from_device(y, B.F16_BFP)[:16]
     assert metrics.sqnr_db(F.fft(x[:16]), got) >= 60.0, chosen
+    # Uneven plan: the FP16 row exchange of four-step lines is a candidate too
+    # (code bit 17); every line stays within the FP16 budget of its mode.
+    lengths = np.array(MIXED)
+    data, offsets = packed(lengths, B.F16_BFP, seed=35)
+    many = B.bfpfft_plan_create_many(lengths, offsets, B.F16_BFP, B.FORWARD)
+    code, _ = B.bfpfft_plan_tune(many, allow_fp16_exchange=True)
+    assert 1 <= (code & 0xffff) <= B.bfpfft_plan_info(many)[1] and (code >> 16) in (0, 1, 2, 3)
+    x_many = to_device(data, B.F16_BFP)
+    y_many = torch.empty_like(x_many)
+    B.bfpfft_exec(many, x_many, y_many)
+    torch.cuda.synchronize()
+    assert B.bfpfft_device_status() == B.OK
+    out = from_device(y_many, B.F16_BFP)
+    mode = "fourstep_h16" if code >> 17 else ("twopass" if (code >> 16) & 1 else "fourstep")
+    for n, o in zip(lengths, offsets):
+        ok, worst = fp16_line_ok(out[o:o + n], F.fft(data[o:o + n]), n, mode)
+        assert ok, (n, code, worst)
+    # Uniform lines of 65536 points: four-step (FP32 or FP16 row exchange) or two-pass.
+    long_plan = B.bfpfft_plan_create(65536, 8, B.F16_BFP, B.FORWARD)
+    chosen_long, _ = B.bfpfft_plan_tune(long_plan, allow_fp16_exchange=True)
+    assert chosen_long in (11, 12, 15)
+    xl = storage_round(synth.complex_gaussian(8, 65536, seed=11), B.F16_BFP)
+    xl_d = to_device(xl, B.F16_BFP)
+    yl = torch.empty_like(xl_d)
+    B.bfpfft_exec(long_plan, xl_d, yl)
+    torch.cuda.synchronize()
+    assert B.bfpfft_device_status() == B.OK
+    gl = from_device(yl, B.F16_BFP)
+    for i in range(8):
+        ok, worst = fp16_line_ok(gl[i], F.fft(xl[i]), 65536, "fourstep" if chosen_long == 11 else "fourstep_h16")
+        assert ok, (chosen_long, worst)
