@@ -726,8 +726,9 @@ def _bench_autofocus(B, torch, dev, stream):
 
 def _bench_uneven(B, torch, dev, stream):
     """20,000 transforms with lengths drawn from {256, 1024, 4096, 16384, 65536}
-    (Zipf weights, seed 3), forward, one persistent launch replayed through a
-    CUDA graph, in FP16-BFP, FP32, E4M3 and E5M2 storage; the SQNR of each
+    (Zipf weights, seed 3), forward, in FP16-BFP, FP32, E4M3 and E5M2 storage,
+    each plan on the schedule the tuner picks (the persistent launch, or one
+    launch per length) and replayed through a CUDA graph; the SQNR of each
     against the FP32 path by the library's FP64 reduction."""
     import numpy as np
 
@@ -757,11 +758,10 @@ def _bench_uneven(B, torch, dev, stream):
             xin = x32.to(f8).view(torch.uint8)
         yout = y32 if dtype == B.F32 else torch.empty_like(xin)
         plan = B.bfpfft_plan_create_many(lengths, offsets, dtype, B.FORWARD)
-        code = None
-        if name == "f16_bfp_tuned_fp16_exchange":
-            # The tuner's pick among cluster counts, two-pass long lines and the
-            # FP16 row exchange of four-step lines.
-            code, _ = B.bfpfft_plan_tune(plan, allow_fp16_exchange=True)
+        # The tuner's pick among cluster counts, two-pass long lines, one launch
+        # per length and (FP16 exchanges allowed) the FP16 row exchange of
+        # four-step lines.
+        code, _ = B.bfpfft_plan_tune(plan, allow_fp16_exchange=name == "f16_bfp_tuned_fp16_exchange")
         for _ in range(3):
             B.bfpfft_exec_graph(plan, xin, yout, stream)
         ts = []
@@ -774,9 +774,8 @@ def _bench_uneven(B, torch, dev, stream):
         t = statistics.median(ts)
         entry = {"ms_median": round(t, 4), "gflops": round(flops / (t * 1e-3) / 1e9, 1),
                  "alg_gbs": round(total * 2 * xin.element_size() * xin.shape[-1] / (t * 1e-3) / 1e9, 1)}
-        if code is not None:
-            entry["tuned"] = {"clusters": code & 0xffff, "two_pass_long_lines": bool((code >> 16) & 1),
-                              "fp16_row_exchange": bool(code >> 17)}
+        entry["tuned"] = {"clusters": code & 0xffff, "two_pass_long_lines": bool((code >> 16) & 1),
+                          "fp16_row_exchange": bool((code >> 17) & 1), "one_launch_per_length": bool((code >> 18) & 1)}
         if dtype == B.F16_BFP:
             B.bfp_sqnr_sums(torch.view_as_complex(y32), B.F32, yout, B.F16_BFP, total, sums, ws, ws_bytes, stream)
             entry["sqnr_vs_f32_db"] = round(B.sqnr_from_sums(sums[:5].cpu().tolist())["aligned_db"], 2)

@@ -128,21 +128,47 @@ int bfpfft_plan_destroy(bfpfft_plan plan);
 /*
  * Uneven batch: `count` transforms of lengths n[i] (powers of two in
  * [16, 65536], mixed freely) at point offsets offset_pts[i] of the in / out
- * buffers, all computed by ONE persistent launch.  The plan sorts the lines
- * into tasks of 65,536 points of one length, largest length first; thread-
- * block clusters of 16 CTAs take tasks from a counter (a line of 65536 spans
- * the whole cluster, shorter lines one CTA or part of one) and never wait on
- * each other.  dtype: BFPFFT_F32, BFPFFT_F16_BFP, BFPFFT_E4M3_BFP or
+ * buffers, by default all computed by ONE persistent launch.  The plan sorts
+ * the lines into tasks of 65,536 points of one length, largest length first;
+ * thread-block clusters of 16 CTAs take every clusters-th task in turn (a
+ * line of 65536 spans the whole cluster, shorter lines one CTA or part of
+ * one) and never wait on each other.  bfpfft_plan_tune or
+ * bfpfft_plan_set_many_schedule may choose another schedule (two-pass long
+ * lines, FP16 row exchanges, one launch per length).  Offsets must be
+ * multiples of 16 points.  dtype: BFPFFT_F32, BFPFFT_F16_BFP, BFPFFT_E4M3_BFP or
  * BFPFFT_E5M2_BFP (FP8 transforms of length n use the block exponents of a
  * uniform plan of that length); direction as for bfpfft_plan_create.
  * Transforms must not overlap each other in `out`; in == out is allowed.
  * The arrays n and offset_pts are host memory, read during the call only.
- * Errors: INVALID_ARG, UNSUPPORTED (a length, BFPFFT_F16_NAIVE, or no room for
- * a 16-CTA cluster on this device), OOM, CUDA.  Execute with bfpfft_exec or
- * bfpfft_exec_graph.
+ * Errors: INVALID_ARG (also an offset that is not a multiple of 16), UNSUPPORTED
+ * (a length, BFPFFT_F16_NAIVE, or no room for a 16-CTA cluster on this device),
+ * OOM, CUDA.  Execute with bfpfft_exec or bfpfft_exec_graph.
  */
 int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, const int64_t* offset_pts,
                             int dtype, int direction);
+
+/* Schedule flags of an uneven plan (bfpfft_plan_set_many_schedule; the tuner's
+ * code carries them as clusters + 65536 * flags). */
+enum bfpfft_many_schedule {
+  BFPFFT_MANY_TWO_PASS = 1,    /* lines of 32768 / 65536 points by the two-pass kernels, before the
+                                  persistent launch */
+  BFPFFT_MANY_FP16_ROWS = 2,   /* FP16 storage: four-step lines exchange their rows as FP16 words (one more
+                                  FP16 rounding inside the transform, within the FP16 error budget) */
+  BFPFFT_MANY_PER_LENGTH = 4   /* one launch per length over its listed lines, each with the dense-row kernel
+                                  of a uniform plan of that length, instead of the persistent kernel (the
+                                  four-step lines still follow BFPFFT_MANY_FP16_ROWS; TWO_PASS does not apply) */
+};
+
+/*
+ * Set an uneven plan's schedule by hand (what bfpfft_plan_tune chooses):
+ * clusters = persistent clusters (0: all resident ones), flags = OR of enum
+ * bfpfft_many_schedule.  The arithmetic of every transform stays FP32; only
+ * BFPFFT_MANY_FP16_ROWS changes results (one more FP16 storage point).  A graph
+ * captured by bfpfft_exec_graph is captured again.
+ * Errors: INVALID_ARG (NULL or uniform plan, clusters < 0, unknown flag bits,
+ * BFPFFT_MANY_FP16_ROWS without FP16 storage).
+ */
+int bfpfft_plan_set_many_schedule(bfpfft_plan plan, int clusters, int flags);
 
 /*
  * Autotuner (not in the paper).  Times the candidate kernels of this plan on

@@ -43,6 +43,11 @@ INVERSE = +1
 
 CHECK_FINITE = 1   # plan flag (enum bfpfft_flags)
 
+# Uneven-plan schedule flags (enum bfpfft_many_schedule).
+MANY_TWO_PASS = 1
+MANY_FP16_ROWS = 2
+MANY_PER_LENGTH = 4
+
 BYTES_PER_POINT = {F32: 8, F16_BFP: 4, F16_NAIVE: 4, E4M3_BFP: 2, E5M2_BFP: 2, F16_ADAPTIVE: 4, BF16: 4}
 
 _c_int64 = ctypes.c_int64
@@ -63,6 +68,7 @@ SIGNATURES = {
     "bfpfft_device_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
     "bfpfft_plan_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "bfpfft_plan_set_flags": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "bfpfft_plan_set_many_schedule": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "bfpfft_plan_selftest_wait": (ctypes.c_int, [_vp, _vp]),
     "bfpfft_plan_set_arith": (ctypes.c_int, [_vp, ctypes.c_int]),
     "bfpfft_exec_adaptive": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -246,6 +252,12 @@ def bfpfft_plan_status(plan: Plan) -> int:
 
 def bfpfft_plan_set_flags(plan: Plan, flags: int):
     _check(lib().bfpfft_plan_set_flags(plan.handle, int(flags)), "bfpfft_plan_set_flags")
+
+
+def bfpfft_plan_set_many_schedule(plan: Plan, clusters: int = 0, flags: int = 0):
+    """Uneven plan: persistent clusters (0: all resident) and MANY_* flags."""
+    _check(lib().bfpfft_plan_set_many_schedule(plan.handle, int(clusters), int(flags)),
+           "bfpfft_plan_set_many_schedule")
 
 
 def bfpfft_plan_set_arith(plan: Plan, arith: int):

@@ -79,7 +79,16 @@ struct RowArgs {
                            // the row exchange between the column and row transforms as FP16 words
   const int* in_exp;       // adaptive exponents: per-line input exponents (value = stored * 2^e), or null
   int* out_exp;            // adaptive exponents: per-line output exponents written by the kernel
+  const long long* line_off;   // non-null: line l starts at point line_off[l] of both in and out (the lines
+                               // of one length in an uneven batch); dense rows of the plain and generic row
+                               // kernels and of the four-step kernel only.  Offsets are multiples of 16 points.
 };
+
+// First point of a dense line: at line_off[line] when the lines are listed,
+// else at line * stride.
+__device__ __forceinline__ long long line_start(const RowArgs& a, long long line, long long stride) {
+  return a.line_off != nullptr ? a.line_off[line] : line * stride;
+}
 
 // Row-kernel variants for dense rows of length <= 4096 (chosen by
 // BFPFFT_ROWS or the tuner): bulk-copy pipelined persistent kernel or plain
@@ -519,14 +528,20 @@ fft_rows_kernel(const RowArgs a) {
     }
     __syncthreads();
   } else if (active) {
-    if (a.pf_ahead > 0 && threadIdx.x == 0) {
+    if (a.pf_ahead > 0) {
       // Dense rows: one bulk L2 prefetch of the lines of the CTA that will
-      // take this one's slot about one resident wave later.
+      // take this one's slot about one resident wave later (listed lines:
+      // one prefetch per line, by its group's first thread).
       const long long l0 = ((long long)blockIdx.x + a.pf_ahead) * S::G;
-      const long long cnt = a.lines - l0 < S::G ? a.lines - l0 : S::G;
-      if (cnt > 0) prefetch_l2_bulk(static_cast<const TIn*>(a.in) + l0 * N, uint32_t(cnt * N * sizeof(TIn)));
+      if (a.line_off == nullptr) {
+        const long long cnt = a.lines - l0 < S::G ? a.lines - l0 : S::G;
+        if (threadIdx.x == 0 && cnt > 0)
+          prefetch_l2_bulk(static_cast<const TIn*>(a.in) + l0 * N, uint32_t(cnt * N * sizeof(TIn)));
+      } else if (t == 0 && l0 + g < a.lines) {
+        prefetch_l2_bulk(static_cast<const TIn*>(a.in) + a.line_off[l0 + g], uint32_t(N * sizeof(TIn)));
+      }
     }
-    const TIn* in = static_cast<const TIn*>(a.in) + line * a.in_stride + t;
+    const TIn* in = static_cast<const TIn*>(a.in) + line_start(a, line, a.in_stride) + t;
 #pragma unroll
     for (int m = 0; m < P; ++m) v[m] = Storage<TIn>::load(in + T * m);
   } else {
@@ -646,7 +661,7 @@ fft_rows_kernel(const RowArgs a) {
       __syncthreads();
     }
   } else if (active) {
-    TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + t;
+    TOut* out = static_cast<TOut*>(a.out) + line_start(a, line, a.out_stride) + t;
 #pragma unroll
     for (int m = 0; m < P; ++m) Storage<TOut>::store(out + T * m, v[m]);
     check_finite<Storage<TOut>, P>(a.finite_flag, [&](int m) { return v[m]; });
@@ -991,8 +1006,8 @@ __global__ void __launch_bounds__(256, fourstep_smem_bytes<TS, N / 4096>() * 4 <
   auto cluster = cooperative_groups::this_cluster();
   const int c = int(cluster.block_rank());
   const long long line = blockIdx.x / N1;
-  const TS* in = static_cast<const TS*>(a.in) + line * a.in_stride;
-  TS* out = static_cast<TS*>(a.out) + line * a.out_stride;
+  const TS* in = static_cast<const TS*>(a.in) + line_start(a, line, a.in_stride);
+  TS* out = static_cast<TS*>(a.out) + line_start(a, line, a.out_stride);
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     mbar_init(&bar_out, 1);
@@ -1000,7 +1015,7 @@ __global__ void __launch_bounds__(256, fourstep_smem_bytes<TS, N / 4096>() * 4 <
     // Dense lines: prefetch this CTA's share of the line one resident wave
     // of clusters later into L2.
     if (a.pf_ahead > 0 && line + a.pf_ahead < a.lines)
-      prefetch_l2_bulk(static_cast<const TS*>(a.in) + (line + a.pf_ahead) * N + c * 4096,
+      prefetch_l2_bulk(static_cast<const TS*>(a.in) + line_start(a, line + a.pf_ahead, N) + c * 4096,
                        uint32_t(4096 * sizeof(TS)));
   }
   // Every CTA running, every mbarrier initialised: the initialisation is

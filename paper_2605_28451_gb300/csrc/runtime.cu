@@ -418,7 +418,12 @@ struct bfpfft_plan_s {
   int long_twopass = 0;                 // lines of 32768 / 65536 points by the two-pass kernels (1) or in the
                                         // persistent kernel's four-step lines (0)
   int fs_h16 = 0;                       // FP16 storage: four-step lines exchange their rows as FP16 words (1)
+  int per_length = 0;                   // one dense-row launch per length over its listed lines (1) instead of
+                                        // the persistent kernel
   int has_fourstep = 0;                 // some line has 8192 points or more
+  long long len_first[kMaxLog2 + 1] = {};   // lines of 2^l points: first index into d_line_off ...
+  long long len_count[kMaxLog2 + 1] = {};   // ... and count
+  const float2* tw_len[kMaxLog2 + 1] = {};  // per-length twiddle tables (device pointers, shared cache)
   int first_short_task = 0;             // first task of a length below 32768
   long long long_first[2] = {0, 0};     // lines of 65536 / 32768 points: first index into d_line_off ...
   long long long_count[2] = {0, 0};     // ... and count
@@ -528,7 +533,48 @@ static int run_twopass(int kind, int log2n, int mode, const void* in, void* out,
 }
 
 extern "C" int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream);
+
+// An uneven plan as one launch per length, longest first: each length's
+// lines, listed by their offsets, run the dense-row kernel of a uniform plan
+// of that length (the four-step kernel for 32768 / 65536 points, one CTA per
+// line for 8192 / 16384, CTA-local groups below), which the persistent
+// kernel cannot use because its CTAs are sized for every length at once.
+// With FP8 storage each length keeps the block exponents of its uniform plan.
+static int exec_per_length(bfpfft_plan plan, const void* in, void* out, cudaStream_t s) {
+  const bool dev_mem = device_memory(in);
+  const int mode = plan->direction == BFPFFT_INVERSE ? bfp::kInverse : bfp::kForward;
+  for (int l = kMaxLog2; l >= kMinLog2; --l) {
+    if (plan->len_count[l] == 0) continue;
+    bfp::RowArgs a{};
+    a.in = in;
+    a.out = out;
+    a.tw = plan->tw_len[l];
+    a.status = plan->status;
+    a.finite_flag = (plan->flags & BFPFFT_CHECK_FINITE) ? plan->status : nullptr;
+    a.variant = dev_mem ? bfp::kRowsPlain4L2 : bfp::kRowsPlain4;
+    a.no_prefetch = dev_mem ? 0 : 1;
+    a.lines = plan->len_count[l];
+    a.in_stride = a.out_stride = 1LL << l;
+    a.line_off = plan->d_line_off + plan->len_first[l];
+    a.fs_h16 = plan->kind == 1 && plan->fs_h16;
+    const float sc = float(1 << ((l + 1) / 2));       // FP8 block exponent of a uniform plan of this length
+    a.in_scale = plan->kind >= 2 && mode == bfp::kInverse ? sc : 1.f;
+    a.out_scale = plan->kind >= 2 && mode == bfp::kForward ? 1.f / sc : 1.f;
+    int st = fourstep_tables(l, &a);
+    if (st != BFPFFT_OK) return st;
+    cudaError_t e;
+    switch (plan->kind) {
+      case 0: e = bfp::launch_rows_f32(l, mode, a, s); break;
+      case 1: e = bfp::launch_rows_f16(l, mode, false, a, s); break;
+      default: e = bfp::launch_rows_fp8(l, mode, plan->kind - 2, a, s); break;
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return BFPFFT_OK;
+}
+
 static int exec_many(bfpfft_plan plan, const void* in, void* out, cudaStream_t s) {
+  if (plan->per_length) return exec_per_length(plan, in, out, s);
   bfp::UnevenArgs a{};
   a.in = in;
   a.out = out;
@@ -702,6 +748,7 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
   std::vector<int> candidates;
   const int saved_long = plan->long_twopass;
   const int saved_fs_h16 = plan->fs_h16;
+  const int saved_per_length = plan->per_length;
   if (plan->many) {
     // Uneven plans: the persistent cluster count; whether lines of 32768 /
     // 65536 points run as four-step lines inside the persistent kernel or as
@@ -717,6 +764,9 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
         candidates.push_back(c + 65536 * mode);
       }
     }
+    // One launch per length (code bit 18; the cluster count does not apply).
+    candidates.push_back(plan->clusters + 262144);
+    if (h16) candidates.push_back(plan->clusters + 262144 + 131072);
   } else if (plan->log2n >= 15) {
     candidates = {bfp::kRowsPlain4L2, bfp::kRowsTwoPass};
     // four-step lines with the FP16 row exchange
@@ -742,6 +792,7 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
       plan->tuned_clusters = c & 0xffff;
       plan->long_twopass = (c >> 16) & 1;
       plan->fs_h16 = (c >> 17) & 1;
+      plan->per_length = (c >> 18) & 1;
     } else {
       plan->variant = c;
     }
@@ -765,6 +816,7 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
     plan->tuned_clusters = saved_clusters;
     plan->long_twopass = saved_long;
     plan->fs_h16 = saved_fs_h16;
+    plan->per_length = saved_per_length;
   } else {
     plan->variant = saved_variant;
   }
@@ -777,8 +829,13 @@ extern "C" int bfpfft_plan_tune(bfpfft_plan plan, int allow_fp16_exchange, int* 
     plan->tuned_clusters = best & 0xffff;
     plan->long_twopass = (best >> 16) & 1;
     plan->fs_h16 = (best >> 17) & 1;
+    plan->per_length = (best >> 18) & 1;
   } else {
     plan->variant = best;
+  }
+  if (plan->graph) {   // a captured graph holds the old schedule
+    cudaGraphExecDestroy(plan->graph);
+    plan->graph = nullptr;
   }
   *chosen = best;
   if (best_ms) *best_ms = best_t;
@@ -805,6 +862,7 @@ void tune_on_create(bfpfft_plan p) {
         p->tuned_clusters = it->second.first & 0xffff;
         p->long_twopass = (it->second.first >> 16) & 1;
         p->fs_h16 = p->kind == 1 ? (it->second.first >> 17) & 1 : 0;
+        p->per_length = (it->second.first >> 18) & 1;
       } else {
         p->variant = it->second.first;
       }
@@ -890,7 +948,7 @@ int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, c
   for (int64_t i = 0; i < count; ++i) {
     const int l = log2_exact(n[i]);
     if (l < kMinLog2 || l > kMaxLog2) return BFPFFT_ERR_UNSUPPORTED;
-    if (offset_pts[i] < 0) return BFPFFT_ERR_INVALID_ARG;
+    if (offset_pts[i] < 0 || offset_pts[i] % 16 != 0) return BFPFFT_ERR_INVALID_ARG;
     by_class[l].push_back(i);
   }
   if (fault("plan")) return BFPFFT_ERR_CUDA;
@@ -924,8 +982,11 @@ int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, c
   p->num_tasks = int(tasks.size());
   // Tasks are sorted longest first: lines of 65536 and 32768 points come first.
   p->first_short_task = 0;
-  for (const auto& t : tasks)
+  for (const auto& t : tasks) {
     if (t.log2n >= 13) p->has_fourstep = 1;
+    if (p->len_count[t.log2n] == 0) p->len_first[t.log2n] = t.first;
+    p->len_count[t.log2n] += t.count;
+  }
   for (const auto& t : tasks) {
     if (t.log2n < 15) break;
     ++p->first_short_task;
@@ -944,6 +1005,7 @@ int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, c
     float2* t = nullptr;
     st = get_twiddles(l, &t);
     tw_host[l] = t;
+    p->tw_len[l] = t;
     if (st == BFPFFT_OK && l >= 13) {
       bfp::RowArgs tmp{};
       st = fourstep_tables(l, &tmp);
@@ -1124,6 +1186,22 @@ int bfpfft_plan_status(bfpfft_plan plan, int* status) {
   if (e == cudaSuccess) e = cudaMemcpy(status, plan->status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(plan->status, 0, sizeof(int));
   return cuda_status(e);
+}
+
+int bfpfft_plan_set_many_schedule(bfpfft_plan plan, int clusters, int flags) {
+  if (plan == nullptr || !plan->many || clusters < 0) return BFPFFT_ERR_INVALID_ARG;
+  if ((flags & ~(BFPFFT_MANY_TWO_PASS | BFPFFT_MANY_FP16_ROWS | BFPFFT_MANY_PER_LENGTH)) != 0)
+    return BFPFFT_ERR_INVALID_ARG;
+  if ((flags & BFPFFT_MANY_FP16_ROWS) && plan->kind != 1) return BFPFFT_ERR_INVALID_ARG;
+  plan->tuned_clusters = std::min(clusters, plan->clusters);
+  plan->long_twopass = (flags & BFPFFT_MANY_TWO_PASS) ? 1 : 0;
+  plan->fs_h16 = (flags & BFPFFT_MANY_FP16_ROWS) ? 1 : 0;
+  plan->per_length = (flags & BFPFFT_MANY_PER_LENGTH) ? 1 : 0;
+  if (plan->graph) {
+    cudaGraphExecDestroy(plan->graph);
+    plan->graph = nullptr;
+  }
+  return BFPFFT_OK;
 }
 
 int bfpfft_plan_set_flags(bfpfft_plan plan, int flags) {

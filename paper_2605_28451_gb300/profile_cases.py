@@ -14,7 +14,8 @@ Cases (FP16-BFP unless named otherwise, N = 4096 lines):
   autofocus16            one autofocus gradient step on 4096 x 4096 FP16 range-compressed data (--arith
                          f16mul: the transforms on the tensor cores)
   uneven16               a persistent uneven batch of B transforms (default 2000; lengths 256 .. 65536,
-                         Zipf weights, seed 3), FP16, forward
+                         Zipf weights, seed 3), FP16, forward; --many-flags 4: one launch per length
+                         (| 2: FP16 four-step row exchanges)
 Inputs are seeded and synthetic.  Nothing is checked here; the tests do that.
 """
 
@@ -36,6 +37,7 @@ def main():
     ap.add_argument("--n", type=int, default=4096, help="transform length of the fft* cases")
     ap.add_argument("--time", action="store_true", help="print the median ms per rep (CUDA events)")
     ap.add_argument("--arith", default="f32", choices=["f32", "f16", "f16mul", "bf16"])
+    ap.add_argument("--many-flags", type=int, default=0, help="uneven16: schedule flags (MANY_*)")
     args = ap.parse_args()
     times = []
     build.build()
@@ -137,6 +139,8 @@ def main():
         x = torch.randn((total, 2), device=dev, generator=g).to(torch.float16)
         y = torch.empty_like(x)
         plan = B.bfpfft_plan_create_many(lengths, offsets, B.F16_BFP, B.FORWARD)
+        if args.many_flags:
+            B.bfpfft_plan_set_many_schedule(plan, 0, args.many_flags)
         for _ in range(args.reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)

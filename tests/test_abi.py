@@ -99,6 +99,16 @@ def test_fault_injection_alloc(lib, monkeypatch):
     assert e.value.status == B.ERR_OOM
 
 
+def test_uneven_offsets_must_be_multiples_of_16(lib):
+    """Uneven plans refuse a line offset that is not a multiple of 16 points
+    (the kernels' bulk L2 prefetches need 16-byte-aligned lines) before any
+    device work."""
+    import numpy as np
+    with pytest.raises(B.BfpfftError) as e:
+        B.bfpfft_plan_create_many(np.array([256, 4096]), np.array([0, 264]), B.F16_BFP, B.FORWARD)
+    assert e.value.status == B.ERR_INVALID_ARG
+
+
 def test_fault_injection_launch(lib, monkeypatch):
     """BFPFFT_FAULT=launch: every plan-less call fails its launch with ERR_CUDA after
     checking its arguments and before any device work (addresses 16 are fake)."""
@@ -121,6 +131,7 @@ def test_status_and_flag_argument_checks(lib):
     st = ctypes.c_int(-1)
     assert lib.bfpfft_plan_status(None, ctypes.byref(st)) == B.ERR_INVALID_ARG
     assert lib.bfpfft_plan_set_flags(None, B.CHECK_FINITE) == B.ERR_INVALID_ARG
+    assert lib.bfpfft_plan_set_many_schedule(None, 0, B.MANY_PER_LENGTH) == B.ERR_INVALID_ARG
     assert lib.bfpfft_plan_selftest_wait(None, None) == B.ERR_INVALID_ARG
     assert lib.bfpfft_device_status(None) == B.ERR_INVALID_ARG
 

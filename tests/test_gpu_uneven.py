@@ -35,9 +35,23 @@ def packed(lengths, dtype, seed):
     return storage_round(data, dtype), offsets
 
 
+# Schedule flags the long_lines fixture applies to every uneven plan a test makes.
+SCHEDULE = {"flags": 0}
+
+
+def create_many(lengths, offsets, dtype, direction):
+    plan = B.bfpfft_plan_create_many(lengths, offsets, dtype, direction)
+    flags = SCHEDULE["flags"]
+    if flags:
+        if dtype != B.F16_BFP:
+            flags &= ~B.MANY_FP16_ROWS
+        B.bfpfft_plan_set_many_schedule(plan, 0, flags)
+    return plan
+
+
 def run_many(data, lengths, offsets, dtype, direction, graph=False, reps=1):
     import torch
-    plan = B.bfpfft_plan_create_many(lengths, offsets, dtype, direction)
+    plan = create_many(lengths, offsets, dtype, direction)
     x = to_device(data, dtype)
     y = torch.empty_like(x)
     for _ in range(reps):
@@ -50,18 +64,23 @@ def run_many(data, lengths, offsets, dtype, direction, graph=False, reps=1):
 MIXED = [65536, 16, 4096, 256, 16384, 1024, 8192, 32, 4096, 32768, 512, 2048, 64, 128, 65536, 256, 4096] * 2
 
 
-@pytest.fixture(params=["fourstep", "twopass", "fourstep_h16"])
+@pytest.fixture(params=["fourstep", "twopass", "fourstep_h16", "per_length", "per_length_h16"])
 def long_lines(request, monkeypatch):
     """Lines of 32768 / 65536 points inside the persistent kernel (four-step) or
     split off to the two-pass kernels (BFPFFT_ROWS=twopass forces the split);
     fourstep_h16: four-step lines with their row exchange in FP16 words
-    (BFPFFT_ROWS naming an FP16-exchange variant forces it)."""
+    (BFPFFT_ROWS naming an FP16-exchange variant forces it); per_length: one
+    dense-row launch per length over its listed lines (schedule flag), with
+    FP32 or FP16 (per_length_h16) four-step row exchanges."""
+    monkeypatch.delenv("BFPFFT_ROWS", raising=False)
     if request.param == "twopass":
         monkeypatch.setenv("BFPFFT_ROWS", "twopass")
     elif request.param == "fourstep_h16":
         monkeypatch.setenv("BFPFFT_ROWS", "h16_l2")
-    else:
-        monkeypatch.delenv("BFPFFT_ROWS", raising=False)
+    elif request.param == "per_length":
+        monkeypatch.setitem(SCHEDULE, "flags", B.MANY_PER_LENGTH)
+    elif request.param == "per_length_h16":
+        monkeypatch.setitem(SCHEDULE, "flags", B.MANY_PER_LENGTH | B.MANY_FP16_ROWS)
     return request.param
 
 
@@ -69,8 +88,11 @@ def fp16_line_ok(g, ref, n, long_lines):
     """FP16 parity of one line.  The two-pass intermediate (lines of 32768
     points or more) and the FP16 row exchange of four-step lines (8192 points
     or more) are one more FP16 storage point: the FP16-exchange bound of the
-    uniform row tests."""
-    if (long_lines == "twopass" and n >= 32768) or (long_lines == "fourstep_h16" and n >= 8192):
+    uniform row tests.  One launch per length runs lines of 8192 and 16384
+    points on one CTA (FP32 exchanges), so there only lines of 32768 points or
+    more carry the FP16 row exchange."""
+    if ((long_lines == "twopass" and n >= 32768) or (long_lines == "fourstep_h16" and n >= 8192)
+            or (long_lines == "per_length_h16" and n >= 32768)):
         rms = np.sqrt(np.mean(np.abs(ref) ** 2))
         bound = 2.0 ** -11 * (np.abs(ref) + 6.0 * rms)
         return (np.all(np.abs(g.real - ref.real) <= bound) and np.all(np.abs(g.imag - ref.imag) <= bound)
@@ -143,7 +165,7 @@ def test_config4_full_size_sampled_lines(long_lines):
     g = torch.Generator(device="cuda:0").manual_seed(3)
     x = torch.randn((total, 2), device="cuda:0", generator=g).to(torch.float16)
     y = torch.empty_like(x)
-    plan = B.bfpfft_plan_create_many(lengths, offsets, B.F16_BFP, B.FORWARD)
+    plan = create_many(lengths, offsets, B.F16_BFP, B.FORWARD)
     B.bfpfft_exec_graph(plan, x, y)
     torch.cuda.synchronize()
     assert B.bfpfft_device_status() == B.OK
@@ -180,18 +202,19 @@ def test_tuner_uniform_and_uneven(tmp_path, monkeypatch):
     lengths = np.array(MIXED)
     data, offsets = packed(lengths, B.F16_BFP, seed=34)
     many = B.bfpfft_plan_create_many(lengths, offsets, B.F16_BFP, B.FORWARD)
-    code, _ = B.bfpfft_plan_tune(many)          # clusters + 65536 * (long lines by the two-pass kernels)
-    assert 1 <= (code & 0xffff) <= B.bfpfft_plan_info(many)[1] and (code >> 16) in (0, 1)
+    code, _ = B.bfpfft_plan_tune(many)          # clusters + 65536 * (two-pass long lines, or 4: per length)
+    assert 1 <= (code & 0xffff) <= B.bfpfft_plan_info(many)[1] and (code >> 16) in (0, 1, 4)
     got, _ = run_many(data, lengths, offsets, B.F16_BFP, B.FORWARD)
     tuned = B.bfpfft_plan_create_many(lengths, offsets, B.F16_BFP, B.FORWARD)
-    B.bfpfft_plan_tune(tuned)
+    code_t, _ = B.bfpfft_plan_tune(tuned)
     x_many = to_device(data, B.F16_BFP)
     y_many = torch.empty_like(x_many)
     B.bfpfft_exec(tuned, x_many, y_many)
     torch.cuda.synchronize()
     out = from_device(y_many, B.F16_BFP)
     for n, o in zip(lengths, offsets):
-        ok, worst = fp16_line_ok(out[o:o + n], F.fft(data[o:o + n]), n, "twopass" if code >> 16 else "fourstep")
+        ok, worst = fp16_line_ok(out[o:o + n], F.fft(data[o:o + n]), n,
+                                 "twopass" if (code_t >> 16) & 1 else "fourstep")
         assert ok, (n, worst)
     long_plan = B.bfpfft_plan_create(65536, 8, B.F16_BFP, B.FORWARD)
     chosen_long, _ = B.bfpfft_plan_tune(long_plan)
@@ -228,14 +251,16 @@ def test_tuner_with_fp16_exchanges_allowed(tmp_path, monkeypatch):
     data, offsets = packed(lengths, B.F16_BFP, seed=35)
     many = B.bfpfft_plan_create_many(lengths, offsets, B.F16_BFP, B.FORWARD)
     code, _ = B.bfpfft_plan_tune(many, allow_fp16_exchange=True)
-    assert 1 <= (code & 0xffff) <= B.bfpfft_plan_info(many)[1] and (code >> 16) in (0, 1, 2, 3)
+    assert 1 <= (code & 0xffff) <= B.bfpfft_plan_info(many)[1] and (code >> 16) in (0, 1, 2, 3, 4, 6)
     x_many = to_device(data, B.F16_BFP)
     y_many = torch.empty_like(x_many)
     B.bfpfft_exec(many, x_many, y_many)
     torch.cuda.synchronize()
     assert B.bfpfft_device_status() == B.OK
     out = from_device(y_many, B.F16_BFP)
-    mode = "fourstep_h16" if code >> 17 else ("twopass" if (code >> 16) & 1 else "fourstep")
+    flags = code >> 16
+    mode = {0: "fourstep", 1: "twopass", 2: "fourstep_h16", 3: "fourstep_h16", 4: "per_length",
+            6: "per_length_h16"}[flags]
     for n, o in zip(lengths, offsets):
         ok, worst = fp16_line_ok(out[o:o + n], F.fft(data[o:o + n]), n, mode)
         assert ok, (n, code, worst)
