@@ -424,6 +424,9 @@ struct bfpfft_plan_s {
   long long len_first[kMaxLog2 + 1] = {};   // lines of 2^l points: first index into d_line_off ...
   long long len_count[kMaxLog2 + 1] = {};   // ... and count
   const float2* tw_len[kMaxLog2 + 1] = {};  // per-length twiddle tables (device pointers, shared cache)
+  cudaStream_t side = nullptr;          // one launch per length: the shorter lengths' stream (owned) ...
+  cudaEvent_t ev_fork = nullptr;        // ... forked from the caller's stream ...
+  cudaEvent_t ev_join = nullptr;        // ... and joined back into it
   int first_short_task = 0;             // first task of a length below 32768
   long long long_first[2] = {0, 0};     // lines of 65536 / 32768 points: first index into d_line_off ...
   long long long_count[2] = {0, 0};     // ... and count
@@ -452,6 +455,9 @@ void free_plan_resources(bfpfft_plan p) {
   if (p->d_tw) cudaFree(p->d_tw);
   if (p->d_tw4) cudaFree(p->d_tw4);
   if (p->d_counter) cudaFree(p->d_counter);
+  if (p->side) cudaStreamDestroy(p->side);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
 }
 
 // The plan's status word: one device int, zeroed.
@@ -540,11 +546,25 @@ extern "C" int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* st
 // line for 8192 / 16384, CTA-local groups below), which the persistent
 // kernel cannot use because its CTAs are sized for every length at once.
 // With FP8 storage each length keeps the block exponents of its uniform plan.
+// Lines of 32768 / 65536 points run on the caller's stream, the shorter
+// lengths on the plan's side stream forked from it (an event each way, so a
+// stream capture takes both branches), so that their launches overlap.
 static int exec_per_length(bfpfft_plan plan, const void* in, void* out, cudaStream_t s) {
   const bool dev_mem = device_memory(in);
   const int mode = plan->direction == BFPFFT_INVERSE ? bfp::kInverse : bfp::kForward;
-  for (int l = kMaxLog2; l >= kMinLog2; --l) {
+  bool has_long = false, has_short = false;
+  for (int l = kMinLog2; l <= kMaxLog2; ++l)
+    if (plan->len_count[l] > 0) (l >= 15 ? has_long : has_short) = true;
+  const bool fork = has_long && has_short && plan->side != nullptr;
+  if (fork) {
+    cudaError_t e = cudaEventRecord(plan->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->side, plan->ev_fork, 0);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  int result = BFPFFT_OK;
+  for (int l = kMaxLog2; l >= kMinLog2 && result == BFPFFT_OK; --l) {
     if (plan->len_count[l] == 0) continue;
+    const cudaStream_t ls = fork && l < 15 ? plan->side : s;
     bfp::RowArgs a{};
     a.in = in;
     a.out = out;
@@ -560,17 +580,22 @@ static int exec_per_length(bfpfft_plan plan, const void* in, void* out, cudaStre
     const float sc = float(1 << ((l + 1) / 2));       // FP8 block exponent of a uniform plan of this length
     a.in_scale = plan->kind >= 2 && mode == bfp::kInverse ? sc : 1.f;
     a.out_scale = plan->kind >= 2 && mode == bfp::kForward ? 1.f / sc : 1.f;
-    int st = fourstep_tables(l, &a);
-    if (st != BFPFFT_OK) return st;
+    result = fourstep_tables(l, &a);
+    if (result != BFPFFT_OK) break;
     cudaError_t e;
     switch (plan->kind) {
-      case 0: e = bfp::launch_rows_f32(l, mode, a, s); break;
-      case 1: e = bfp::launch_rows_f16(l, mode, false, a, s); break;
-      default: e = bfp::launch_rows_fp8(l, mode, plan->kind - 2, a, s); break;
+      case 0: e = bfp::launch_rows_f32(l, mode, a, ls); break;
+      case 1: e = bfp::launch_rows_f16(l, mode, false, a, ls); break;
+      default: e = bfp::launch_rows_fp8(l, mode, plan->kind - 2, a, ls); break;
     }
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) result = cuda_status(e);
   }
-  return BFPFFT_OK;
+  if (fork) {   // joined whatever happened, so that a capture stays well formed
+    cudaError_t e = cudaEventRecord(plan->ev_join, plan->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->ev_join, 0);
+    if (e != cudaSuccess && result == BFPFFT_OK) result = cuda_status(e);
+  }
+  return result;
 }
 
 static int exec_many(bfpfft_plan plan, const void* in, void* out, cudaStream_t s) {
@@ -1026,6 +1051,9 @@ int bfpfft_plan_create_many(bfpfft_plan* out, int64_t count, const int64_t* n, c
     if (e == cudaSuccess) e = cudaMemcpy(p->d_tw, tw_host, sizeof(tw_host), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_tw4, tw4_host, sizeof(tw4_host), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = bfp::uneven_max_clusters(kind, direction == BFPFFT_INVERSE, &p->clusters);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) st = cuda_status(e);
     if (st == BFPFFT_OK && p->clusters <= 0) st = BFPFFT_ERR_UNSUPPORTED;
   }
