@@ -72,7 +72,9 @@ enum bfpfft_arith {
                                        shared-memory exchange (F16_BFP / F16_NAIVE, n <= 16384) */
   BFPFFT_ARITH_F16_MUL_F32_ACC = 2, /* FP16 operands, FP32 accumulation: each radix-16 DFT block on the
                                        tensor cores (tcgen05.mma kind::f16), twiddles FP32 (F16_BFP,
-                                       n = 4096) */
+                                       E4M3_BFP or E5M2_BFP, n = 4096; FP8 values convert exactly to
+                                       FP16 operands and the block exponent scales the first pass's FP32
+                                       results, so the stored scale is the FP8 plan's own) */
   BFPFFT_ARITH_BF16 = 3             /* bfloat16 arithmetic; the one mode of BFPFFT_BF16 plans */
 };
 

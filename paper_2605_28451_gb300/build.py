@@ -40,6 +40,7 @@ SOURCES = [
     "rda.cu",
     "twopass.cu",
     "af_tc.cu",
+    "rows_tc8.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

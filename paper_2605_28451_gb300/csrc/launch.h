@@ -38,6 +38,9 @@ cudaError_t launch_twiddles16(void* tw, int n, bool bf16);
 // operands, FP32 accumulation; in32 reads a complex64 input; FP16 output rows.
 // a.tc_b holds the DFT-16 matrix, a.h the filter spectrum.
 cudaError_t launch_tc_compress(bool in32, const RowArgs& a, cudaStream_t s);
+// Dense FP8 rows of 4096 points on the tensor cores (fmt 0: E4M3, 1: E5M2),
+// with the block exponents in a.in_scale / a.out_scale.
+cudaError_t launch_tc_fp8(int mode, int fmt, const RowArgs& a, cudaStream_t s);
 
 // SAR compression lines (Section VI, Fig. 1): float2 or __half2 in and out,
 // optional naive FP16 output, optional cluster corner turn on load / store.

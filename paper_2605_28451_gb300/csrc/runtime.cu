@@ -1122,7 +1122,8 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
     return cuda_status(bf16 ? bfp::launch_rows16_bf16(plan->log2n, mode16, a, s16)
                             : bfp::launch_rows16_f16(plan->log2n, mode16, plan->dtype == BFPFFT_F16_NAIVE, a, s16));
   }
-  if (a.variant == bfp::kRowsTc && plan->log2n == 12 && plan->dtype == BFPFFT_F16_BFP) {
+  if (a.variant == bfp::kRowsTc && plan->log2n == 12 &&
+      (plan->dtype == BFPFFT_F16_BFP || plan->dtype == BFPFFT_E4M3_BFP || plan->dtype == BFPFFT_E5M2_BFP)) {
     const int stc = get_tc_matrix(const_cast<void**>(&a.tc_b));
     if (stc != BFPFFT_OK) return stc;
   }
@@ -1142,8 +1143,13 @@ int bfpfft_exec(bfpfft_plan plan, const void* in, void* out, void* stream) {
     case BFPFFT_F32: e = bfp::launch_rows_f32(plan->log2n, mode, a, s); break;
     case BFPFFT_F16_BFP: e = bfp::launch_rows_f16(plan->log2n, mode, false, a, s); break;
     case BFPFFT_F16_NAIVE: e = bfp::launch_rows_f16(plan->log2n, mode, true, a, s); break;
-    case BFPFFT_E4M3_BFP: e = bfp::launch_rows_fp8(plan->log2n, mode, 0, a, s); break;
-    case BFPFFT_E5M2_BFP: e = bfp::launch_rows_fp8(plan->log2n, mode, 1, a, s); break;
+    case BFPFFT_E4M3_BFP:
+    case BFPFFT_E5M2_BFP: {
+      const int fmt = plan->dtype == BFPFFT_E4M3_BFP ? 0 : 1;
+      e = plan->arith == BFPFFT_ARITH_F16_MUL_F32_ACC ? bfp::launch_tc_fp8(mode, fmt, a, s)
+                                                      : bfp::launch_rows_fp8(plan->log2n, mode, fmt, a, s);
+      break;
+    }
     default: return BFPFFT_ERR_UNSUPPORTED;
   }
   return cuda_status(e);
@@ -1250,7 +1256,10 @@ int bfpfft_plan_set_arith(bfpfft_plan plan, int arith) {
   switch (arith) {
     case BFPFFT_ARITH_F32: ok = plan->dtype != BFPFFT_BF16; break;
     case BFPFFT_ARITH_F16: ok = !plan->many && f16 && plan->log2n <= bfp::kRows16MaxLog2; break;
-    case BFPFFT_ARITH_F16_MUL_F32_ACC: ok = !plan->many && plan->dtype == BFPFFT_F16_BFP && plan->log2n == 12; break;
+    case BFPFFT_ARITH_F16_MUL_F32_ACC:
+      ok = !plan->many && plan->log2n == 12 &&
+           (plan->dtype == BFPFFT_F16_BFP || plan->dtype == BFPFFT_E4M3_BFP || plan->dtype == BFPFFT_E5M2_BFP);
+      break;
     case BFPFFT_ARITH_BF16: ok = plan->dtype == BFPFFT_BF16; break;
     default: break;
   }

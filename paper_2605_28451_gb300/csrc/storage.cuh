@@ -22,6 +22,11 @@ struct E5M2 {};
 
 template <class Fmt> struct alignas(2) Fp8x2 { __nv_fp8x2_storage_t bits; };
 
+// The conversion intrinsics' name for each FP8 pair type.
+template <class T> struct Fp8Format;
+template <> struct Fp8Format<Fp8x2<E4M3>> { static constexpr __nv_fp8_interpretation_t kInterp = __NV_E4M3; };
+template <> struct Fp8Format<Fp8x2<E5M2>> { static constexpr __nv_fp8_interpretation_t kInterp = __NV_E5M2; };
+
 template <class T> struct Storage;
 
 template <> struct Storage<float2> {

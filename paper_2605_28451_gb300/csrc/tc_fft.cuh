@@ -105,6 +105,11 @@ __device__ __forceinline__ uint32_t ld_once_b32(const void* p) {
   asm volatile("ld.global.L1::no_allocate.b32 %0, [%1];" : "=r"(r) : "l"(p));
   return r;
 }
+__device__ __forceinline__ uint16_t ld_once_b16(const void* p) {
+  uint16_t r;
+  asm volatile("ld.global.L1::no_allocate.b16 %0, [%1];" : "=h"(r) : "l"(p));
+  return r;
+}
 __device__ __forceinline__ float2 ld_once_f2(const void* p) {
   float2 r;
   asm volatile("ld.global.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
@@ -229,12 +234,18 @@ __device__ __forceinline__ void tc_filter_to_a(unsigned char* sA, int rho, const
   tc_store_row0(sA, rho, x);
 }
 
-template <int P, int MODE, bool FILTER = false>
+// FP8 storage (TOut an FP8 pair): the line's static block exponent,
+// in_scale * out_scale (one of them is 1), scales the first pass's results in
+// FP32 -- an exact power of two -- so the FP16 operands of the later passes
+// stay in range and the last pass writes the stored scale directly.
+template <int P, int MODE, bool FILTER = false, class TOut = __half2>
 __device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsigned char* sA, uint64_t* bar,
                                         uint32_t tmem, uint32_t lane_tmem, uint32_t a_base, uint32_t b_base,
                                         uint32_t& phase, const float2* s_tw) {
   using namespace tc;
+  constexpr bool kFp8 = !std::is_same<TOut, __half2>::value;
   const int tid = threadIdx.x;
+  const float sc = kFp8 && P == 0 ? a.in_scale * a.out_scale : 1.0f;
   if (!tc_issue_wait(a.status, bar, tmem, a_base, b_base, phase)) return false;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
@@ -262,7 +273,8 @@ __device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsign
           for (int e = 0; e < 2; ++e) {
             const int q = 2 * q2 + e;
             const float2 w = e ? make_float2(wp.z, wp.w) : make_float2(wp.x, wp.y);
-            const float2 y = cmul(make_float2(__uint_as_float(d[2 * q]), __uint_as_float(d[2 * q + 1])), w);
+            float2 y = cmul(make_float2(__uint_as_float(d[2 * q]), __uint_as_float(d[2 * q + 1])), w);
+            if constexpr (kFp8) y = cscale(y, sc);
             *reinterpret_cast<__half2*>(sA + (q & 1 ? base_odd : base_even) + 512 * (q >> 1)) =
                 __float22half2_rn(y);
           }
@@ -286,11 +298,17 @@ __device__ __forceinline__ bool tc_pass(const RowArgs& a, long long line, unsign
       tc_filter_to_a<false>(sA, rho, d, a.h + line * a.h_stride + rho);
     } else {
       // The inverse's final conjugation is folded into the last pass's matrix.
-      __half2* out = static_cast<__half2*>(a.out) + line * a.out_stride + rho;
+      TOut* out = static_cast<TOut*>(a.out) + line * a.out_stride + rho;
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
-        out[256 * q] = __float22half2_rn(make_float2(__uint_as_float(d[2 * q]), __uint_as_float(d[2 * q + 1])));
-      check_finite<Storage<__half2>, 16>(a.finite_flag, [&](int m) {
+      for (int q = 0; q < 16; ++q) {
+        const float2 y = make_float2(__uint_as_float(d[2 * q]), __uint_as_float(d[2 * q + 1]));
+        if constexpr (kFp8) {
+          Storage<TOut>::store(out + 256 * q, y);
+        } else {
+          out[256 * q] = __float22half2_rn(y);
+        }
+      }
+      check_finite<Storage<TOut>, 16>(a.finite_flag, [&](int m) {
         return make_float2(__uint_as_float(d[2 * m]), __uint_as_float(d[2 * m + 1]));
       });
     }
@@ -365,7 +383,7 @@ __device__ __forceinline__ void tc_cta_teardown(bool ok, unsigned char* smem, ui
 // TMEM limit at 64 columns a line) while each CTA's passes run one after
 // another.  Persistent: CTA b takes lines b, b + grid, ...; thread 0 bulk-
 // prefetches the CTA's next line into L2.
-template <int MODE, class TIn>
+template <int MODE, class TIn, class TOut = __half2>
 __global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(const RowArgs a) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
@@ -391,7 +409,7 @@ __global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(co
     // Pass-0 inputs: butterfly j takes x[j + 256 r]; its row of A is four
     // 16-byte core-matrix rows, one st.shared.v4 per four points (the eight
     // lanes of a quarter-warp have distinct row % 8).  Complex64 inputs are
-    // rounded to FP16 operands here.
+    // rounded to FP16 operands here; FP8 pairs convert exactly.
     const TIn* in = in_lines + line * a.in_stride + tid;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -401,6 +419,10 @@ __global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(co
       for (int r = 0; r < 16; ++r) {
         if constexpr (sizeof(TIn) == 4) {
           x[r] = ld_once_b32(in + 128 * h + 256 * r);
+        } else if constexpr (sizeof(TIn) == 2) {
+          const __half2_raw v = __nv_cvt_fp8x2_to_halfraw2(
+              __nv_fp8x2_storage_t(ld_once_b16(in + 128 * h + 256 * r)), Fp8Format<TIn>::kInterp);
+          x[r] = uint32_t(v.x) | (uint32_t(v.y) << 16);
         } else {
           const __half2 v = __float22half2_rn(ld_once_f2(in + 128 * h + 256 * r));
           x[r] = *reinterpret_cast<const uint32_t*>(&v);
@@ -418,17 +440,17 @@ __global__ void __launch_bounds__(tc::kThreads, tc::kCtasPerSm) fft_tc_kernel(co
            tc_pass<1, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_base, phase, s_tw) &&
            tc_pass<2, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_last, phase, s_tw);
     } else {
-      ok = tc_pass<0, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_first, phase, s_tw) &&
-           tc_pass<1, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_base, phase, s_tw) &&
-           tc_pass<2, MODE>(a, line, sA, bar, tmem, lane_tmem, a_base, b_last, phase, s_tw);
+      ok = tc_pass<0, MODE, false, TOut>(a, line, sA, bar, tmem, lane_tmem, a_base, b_first, phase, s_tw) &&
+           tc_pass<1, MODE, false, TOut>(a, line, sA, bar, tmem, lane_tmem, a_base, b_base, phase, s_tw) &&
+           tc_pass<2, MODE, false, TOut>(a, line, sA, bar, tmem, lane_tmem, a_base, b_last, phase, s_tw);
     }
   }
   tc_cta_teardown(ok, smem_tc, tmem, phase);
 }
 
-template <int MODE, class TIn>
+template <int MODE, class TIn, class TOut = __half2>
 cudaError_t launch_tc_kernel(const RowArgs& a, cudaStream_t stream) {
-  auto kern = fft_tc_kernel<MODE, TIn>;
+  auto kern = fft_tc_kernel<MODE, TIn, TOut>;
   // kCtasPerSm CTAs per SM: the register limit of __launch_bounds__; tensor
   // memory holds exactly that many 64-column allocations, so the persistent
   // CTAs never wait on each other's allocation.  Computed once,

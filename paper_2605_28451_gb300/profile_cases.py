@@ -6,6 +6,7 @@ Cases (FP16-BFP unless named otherwise, N = 4096 lines):
   fft16_fwd, fft16_inv   batched transform, batch B (default 16384: 256 MiB in); --arith f16 | f16mul | bf16
                          selects pure FP16, FP16 operands / FP32 accumulation (tensor cores) or bfloat16
   fft32_fwd              the same in FP32 storage
+  fft8_fwd               the same in E4M3 storage (--arith f16mul: on the tensor cores)
   adaptive16_fwd         FP16 with adaptive per-line exponents, batch B
   rda16                  range-Doppler image with RCMC and range-dependent filters, 4096 x 4096, FP16
   range16                range compression of a 1024 x 4096 complex64 scene to FP16, corner-turned
@@ -45,11 +46,15 @@ def main():
     stream = torch.cuda.current_stream()
     n = args.n if args.case.startswith("fft") else 4096
     g = torch.Generator(device=dev).manual_seed(0)
-    if args.case in ("fft16_fwd", "fft16_inv", "fft32_fwd"):
+    if args.case in ("fft16_fwd", "fft16_inv", "fft32_fwd", "fft8_fwd"):
         dtype = B.F32 if args.case == "fft32_fwd" else (B.BF16 if args.arith == "bf16" else B.F16_BFP)
+        dtype = B.E4M3_BFP if args.case == "fft8_fwd" else dtype
         direction = B.INVERSE if args.case == "fft16_inv" else B.FORWARD
         x = torch.randn((args.batch, n, 2), device=dev, generator=g)
-        x = x if dtype == B.F32 else x.to(torch.bfloat16 if dtype == B.BF16 else torch.float16)
+        if dtype == B.E4M3_BFP:
+            x = x.to(torch.float8_e4m3fn).view(torch.uint8)
+        elif dtype != B.F32:
+            x = x.to(torch.bfloat16 if dtype == B.BF16 else torch.float16)
         y = torch.empty_like(x)
         plan = B.bfpfft_plan_create(n, args.batch, dtype, direction)
         arith = {"f32": None, "f16": B.ARITH_F16, "f16mul": B.ARITH_F16_MUL_F32_ACC, "bf16": None}[args.arith]
@@ -61,7 +66,7 @@ def main():
             B.bfpfft_exec(plan, x, y, stream)
             e1.record(stream)
             times.append((e0, e1))
-        bytes_per_rep = args.batch * n * (16 if dtype == B.F32 else 8)
+        bytes_per_rep = args.batch * n * {B.F32: 16, B.E4M3_BFP: 4}.get(dtype, 8)
     elif args.case == "adaptive16_fwd":
         x = torch.randn((args.batch, n, 2), device=dev, generator=g).to(torch.float16)
         y = torch.empty_like(x)

@@ -104,3 +104,22 @@ def fp8_close(got, exact, fmt, max_frac=1e-3):
         hi = quant.round_fp8(x[bad] + d, fmt)
         assert np.all((g[bad] == lo) | (g[bad] == hi)), (g[bad][:5], e[bad][:5], x[bad][:5])
         assert bad.mean() <= max_frac
+
+
+def fp8_within(got, exact, fmt, rel, rms_frac):
+    """FP8 parity of a path whose value before the final rounding may differ
+    from the exact x by up to delta = rel |x| + rms_frac rms(x): rounding is
+    monotonic, so every stored value lies between the oracle's roundings of
+    x - delta and x + delta (equal to RN(x) unless that interval crosses a
+    rounding boundary).  Returns the fraction of stored values that differ
+    from RN(x)."""
+    from oracle import quant
+    rms = float(np.sqrt(np.mean(np.abs(exact) ** 2)))
+    differ = 0
+    for g, x in ((got.real, exact.real), (got.imag, exact.imag)):
+        d = rel * np.abs(x) + rms_frac * rms
+        lo = quant.round_fp8(x - d, fmt)
+        hi = quant.round_fp8(x + d, fmt)
+        assert np.all((g >= lo) & (g <= hi)), (g[(g < lo) | (g > hi)][:5], x[(g < lo) | (g > hi)][:5])
+        differ += int(np.count_nonzero(g != quant.round_fp8(x, fmt)))
+    return differ / (2 * got.size)

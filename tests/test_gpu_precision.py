@@ -12,6 +12,9 @@ Section IV-C's bfloat16) against the oracle's rounding schedules.
 - FP16 operands / FP32 accumulation (the tensor-core DFT blocks): against
   oracle.emulate.fft_radix16_mma, which the GPU matches far more closely
   (>= 6 dB) than either matches the exact DFT.
+- The same tensor-core rows with FP8 storage: every stored value is the FP8
+  rounding of a value within the tensor-core bound of the exact scaled
+  transform, and the SQNR equals the FP32-arithmetic FP8 path's.
 """
 
 import numpy as np
@@ -24,7 +27,7 @@ from oracle import quant as Q
 from paper_2605_28451_gb300 import bfpfft as B
 from paper_2605_28451_gb300 import build, synth
 
-from _helpers import from_device, storage_round, to_device
+from _helpers import fp8_within, from_device, storage_round, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -142,6 +145,10 @@ def test_set_arith_combinations():
     assert status(4096, B.E4M3_BFP, B.ARITH_F16) == B.ERR_UNSUPPORTED
     assert status(4096, B.F16_BFP, B.ARITH_F16_MUL_F32_ACC) == B.OK
     assert status(8192, B.F16_BFP, B.ARITH_F16_MUL_F32_ACC) == B.ERR_UNSUPPORTED
+    assert status(4096, B.E4M3_BFP, B.ARITH_F16_MUL_F32_ACC) == B.OK
+    assert status(4096, B.E5M2_BFP, B.ARITH_F16_MUL_F32_ACC, B.INVERSE) == B.OK
+    assert status(1024, B.E4M3_BFP, B.ARITH_F16_MUL_F32_ACC) == B.ERR_UNSUPPORTED
+    assert status(4096, B.F32, B.ARITH_F16_MUL_F32_ACC) == B.ERR_UNSUPPORTED
     assert status(4096, B.BF16, B.ARITH_F32) == B.ERR_UNSUPPORTED
     assert status(4096, B.F16_BFP, B.ARITH_BF16) == B.ERR_UNSUPPORTED
     assert status(4096, B.F16_BFP, 9) == B.ERR_INVALID_ARG
@@ -238,3 +245,54 @@ def test_tensor_core_rows_graph_replay():
     torch.cuda.synchronize()
     assert torch.equal(direct, graphed)
     assert B.bfpfft_plan_status(fwd) == B.OK
+
+
+# Error of the tensor-core rows before their final rounding: FP16 rounding of
+# the operands at each of the three passes (and of the DFT-16 coefficients),
+# noise of rms about 1.1 * 2^-11 rms(y) per component; 8 * 2^-11 rms(y) is
+# more than 7 sigma (the FP16-row bound without its final FP16 rounding).
+TC_RMS_BOUND = 8 * 2.0 ** -11
+
+
+@pytest.mark.parametrize("dtype,fmt", [(B.E4M3_BFP, "e4m3"), (B.E5M2_BFP, "e5m2")])
+@pytest.mark.parametrize("batch", [1, 7, 2 * 1216 + 7])
+def test_fp8_storage_on_the_tensor_cores(dtype, fmt, batch):
+    """FP8 storage (Section VII) with FP16 operands and FP32 accumulation on
+    the tensor cores, N = 4096, forward and the inverse of the stored
+    spectrum; the stored scale is the FP8 plan's (2^-6 forward, 2^6 back)."""
+    n = 4096
+    x = Q.round_fp8(synth.complex_gaussian(batch, n, seed=40 + batch), fmt)
+    p = B.bfpfft_plan_create(n, batch, dtype, B.FORWARD)
+    _, s = B.bfpfft_plan_scale_exp(p)
+    assert s == 6
+    got = gpu_run(x, n, dtype, B.FORWARD, B.ARITH_F16_MUL_F32_ACC)
+    ref = gpu_run(x, n, dtype, B.FORWARD, B.ARITH_F32)
+    exact = F.fft(x) * 2.0 ** -s
+    assert fp8_within(got, exact, fmt, 1e-5, TC_RMS_BOUND) <= 0.05
+    assert abs(metrics.sqnr_db(exact, got) - metrics.sqnr_db(exact, ref)) <= 0.05
+    got_i = gpu_run(got, n, dtype, B.INVERSE, B.ARITH_F16_MUL_F32_ACC)
+    ref_i = gpu_run(got, n, dtype, B.INVERSE, B.ARITH_F32)
+    exact_i = F.ifft(got * 2.0 ** s)
+    assert fp8_within(got_i, exact_i, fmt, 1e-5, TC_RMS_BOUND) <= 0.05
+    assert abs(metrics.sqnr_db(exact_i, got_i) - metrics.sqnr_db(exact_i, ref_i)) <= 0.05
+
+
+def test_fp8_tensor_core_rows_host_buffers_and_in_place():
+    """FP8 tensor-core rows from pinned host memory and in place give the bits
+    of device buffers out of place."""
+    import torch
+    n, batch = 4096, 1300
+    x = Q.round_fp8(synth.complex_gaussian(batch, n, seed=12), "e4m3")
+    dev_in = to_device(x, B.E4M3_BFP)
+    host_in = torch.empty(dev_in.shape, dtype=dev_in.dtype, pin_memory=True)
+    host_in.copy_(dev_in)
+    fwd = B.bfpfft_plan_create(n, batch, B.E4M3_BFP, B.FORWARD)
+    B.bfpfft_plan_set_arith(fwd, B.ARITH_F16_MUL_F32_ACC)
+    ref, from_host = torch.empty_like(dev_in), torch.empty_like(dev_in)
+    B.bfpfft_exec(fwd, dev_in, ref)
+    B.bfpfft_exec(fwd, host_in, from_host)
+    inplace = dev_in.clone()
+    B.bfpfft_exec(fwd, inplace, inplace)
+    torch.cuda.synchronize()
+    assert B.bfpfft_plan_status(fwd) == B.OK
+    assert torch.equal(from_host, ref) and torch.equal(inplace, ref)
