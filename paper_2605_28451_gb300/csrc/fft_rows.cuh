@@ -842,19 +842,36 @@ cudaError_t launch_rows_tma_n(const RowArgs& a, cudaStream_t stream) {
 // must then stop sending and waiting (no further line on these barriers) and,
 // before the CTA exits, call fourstep_drain so that peers' stores still in
 // flight land before its shared memory goes away.
-template <class TS> struct FsSend {           // step-3 send type: float2, or half2 words for FP16 storage
+// The FP8 pair (satfinite RN) of v as the low 16 bits of a word.
+template <class TS>
+__device__ __forceinline__ uint32_t fp8_pair_bits(float2 v) {
+  return uint32_t(__nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, Fp8Format<TS>::kInterp));
+}
+
+// Step-3 send words: FP32 pairs; for FP16 storage the rounded half2; for FP8
+// storage two rounded FP8 pairs, those of consecutive k2 (the values are
+// rounded where they are computed, as the owner would round them).  kPad
+// words pad each segment of the owner's buffer so that its gather is
+// conflict-free.
+template <class TS> struct FsSend {
   using Word = float2;
+  static constexpr int kPts = 1, kPad = 1;
 };
 template <> struct FsSend<__half2> {
   using Word = uint32_t;
+  static constexpr int kPts = 1, kPad = 2;
+};
+template <class F> struct FsSend<Fp8x2<F>> {
+  using Word = uint32_t;
+  static constexpr int kPts = 2, kPad = 1;
 };
 // Shared memory of a four-step line: the row buffer, and for N1 >= 8 the
-// output buffer of N1 padded segments of S = 4096 / N1 words.
+// output buffer of N1 padded segments of S / kPts words, S = 4096 / N1.
 template <class TS, int N1>
 __host__ __device__ constexpr size_t fourstep_smem_bytes() {
-  using Word = typename FsSend<TS>::Word;
-  constexpr int kPad = sizeof(Word) == 4 ? 2 : 1;
-  return size_t(pad16(4096)) * sizeof(float2) + (N1 >= 8 ? size_t(N1) * (4096 / N1 + kPad) * sizeof(Word) : 0);
+  using X = FsSend<TS>;
+  return size_t(pad16(4096)) * sizeof(float2) +
+         (N1 >= 8 ? size_t(N1) * (4096 / N1 / X::kPts + X::kPad) * sizeof(typename X::Word) : 0);
 }
 
 template <int N1, class TS, int MODE, bool SCALED, bool H16ROW = false>
@@ -868,13 +885,14 @@ __device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS
   // each, from all N1 CTAs.
   constexpr bool kOutXch = N1 >= 8;
   using Word = typename FsSend<TS>::Word;
-  constexpr int kPadOut = sizeof(Word) == 4 ? 2 : 1;    // conflict-free gather
+  constexpr int kPts = FsSend<TS>::kPts;                // points per send word
+  constexpr int kSeg = S / kPts + FsSend<TS>::kPad;     // words per padded segment of the owner's buffer
   // H16ROW with FP16 storage: the row arrives as FP16 words (one more FP16
   // storage point, half the exchange bytes); otherwise as FP32 pairs.
   constexpr bool h16row = H16ROW && std::is_same<TS, __half2>::value;
   if (t == 0) {
     mbar_arrive_expect_tx(bar, 4096u * uint32_t(h16row ? sizeof(uint32_t) : sizeof(float2)));
-    if constexpr (kOutXch) mbar_arrive_expect_tx(bar_out, 4096 * sizeof(Word));
+    if constexpr (kOutXch) mbar_arrive_expect_tx(bar_out, uint32_t(4096 / kPts * sizeof(Word)));
   }
   float2* smem_out = smem + pad16(4096);
   const uint32_t smem_base = smem_addr(smem), bar_local = smem_addr(bar);
@@ -934,19 +952,31 @@ __device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS
     }
     return true;
   } else {
-    // The owner's buffer holds the values as [k1][k2 mod S] with kPadOut
-    // padding slots per segment, so a warp's 32 sends are contiguous; the
-    // owner gathers output position j = (k2 mod S) N1 + k1 from slot
-    // k1 (S + kPadOut) + j / N1.
+    // The owner's buffer holds the values as [k1][k2 mod S] in segments of
+    // kSeg words, so a warp's sends are contiguous; the owner gathers output
+    // position j = (k2 mod S) N1 + k1 from segment k1, point j / N1.  FP8
+    // words hold the points of k2 and k2 + 1 (k2 even): for even m the even
+    // thread of each lane pair sends its value and its odd partner's, for odd
+    // m the odd thread does.
 #pragma unroll
     for (int m = 0; m < P; ++m) {
       const int k2 = t + 256 * m;
-      const uint32_t slot = out_base + uint32_t(c * (S + kPadOut) + k2 % S) * uint32_t(sizeof(Word));
       const uint32_t dst = uint32_t(base_rank + k2 / S);
-      if constexpr (sizeof(Word) == 4) {
-        st_async_b32(mapa(slot, dst), half2_bits(v[m]), mapa(bar_out_local, dst));
+      if constexpr (kPts == 2) {
+        const uint32_t own = fp8_pair_bits<TS>(v[m]);
+        const uint32_t other = __shfl_xor_sync(0xffffffffu, own, 1);
+        if ((t & 1) == (m & 1)) {
+          const uint32_t w = t & 1 ? other | (own << 16) : own | (other << 16);
+          const uint32_t slot = out_base + uint32_t(c * kSeg + (k2 % S) / 2) * uint32_t(sizeof(Word));
+          st_async_b32(mapa(slot, dst), w, mapa(bar_out_local, dst));
+        }
       } else {
-        st_async_f2(mapa(slot, dst), v[m], mapa(bar_out_local, dst));
+        const uint32_t slot = out_base + uint32_t(c * kSeg + k2 % S) * uint32_t(sizeof(Word));
+        if constexpr (sizeof(Word) == 4) {
+          st_async_b32(mapa(slot, dst), half2_bits(v[m]), mapa(bar_out_local, dst));
+        } else {
+          st_async_f2(mapa(slot, dst), v[m], mapa(bar_out_local, dst));
+        }
       }
     }
     const bool out_ok = mbar_wait_bounded(bar_out, phase, a.status);
@@ -957,26 +987,41 @@ __device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS
     phase ^= 1;
     if (active) {
       const Word* ob = reinterpret_cast<const Word*>(smem_out);
+      if constexpr (kPts == 2) {
+        auto bits = [&](int m) -> uint16_t {
+          const int j = t + 256 * m, q = j / N1;
+          return uint16_t(ob[(j % N1) * kSeg + q / 2] >> (16 * (q & 1)));
+        };
 #pragma unroll
-      for (int m = 0; m < P; ++m) {
-        const int j = t + 256 * m;
-        const Word w = ob[(j % N1) * (S + kPadOut) + j / N1];
-        if constexpr (sizeof(Word) == 4) {
-          __stcs(reinterpret_cast<unsigned int*>(out + c * 4096 + j), w);
-        } else {
-          Storage<TS>::store(out + c * 4096 + j, w);
-        }
-      }
-      if constexpr (sizeof(Word) == 4) {
+        for (int m = 0; m < P; ++m)
+          __stcs(reinterpret_cast<unsigned short*>(out + c * 4096 + t + 256 * m), bits(m));
         check_finite<Storage<TS>, P>(a.finite_flag, [&](int m) {
-          const int j = t + 256 * m;
-          return bits_half2(ob[(j % N1) * (S + kPadOut) + j / N1]);
+          TS pair;
+          pair.bits = bits(m);
+          return Storage<TS>::load_smem(&pair);
         });
       } else {
-        check_finite<Storage<TS>, P>(a.finite_flag, [&](int m) {
+#pragma unroll
+        for (int m = 0; m < P; ++m) {
           const int j = t + 256 * m;
-          return ob[(j % N1) * (S + kPadOut) + j / N1];
-        });
+          const Word w = ob[(j % N1) * kSeg + j / N1];
+          if constexpr (sizeof(Word) == 4) {
+            __stcs(reinterpret_cast<unsigned int*>(out + c * 4096 + j), w);
+          } else {
+            Storage<TS>::store(out + c * 4096 + j, w);
+          }
+        }
+        if constexpr (sizeof(Word) == 4) {
+          check_finite<Storage<TS>, P>(a.finite_flag, [&](int m) {
+            const int j = t + 256 * m;
+            return bits_half2(ob[(j % N1) * kSeg + j / N1]);
+          });
+        } else {
+          check_finite<Storage<TS>, P>(a.finite_flag, [&](int m) {
+            const int j = t + 256 * m;
+            return ob[(j % N1) * kSeg + j / N1];
+          });
+        }
       }
     }
     return true;

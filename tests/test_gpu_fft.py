@@ -198,10 +198,14 @@ def test_large_batch_sampled_lines():
 
 
 @pytest.mark.parametrize("dtype,fmt", [(B.E4M3_BFP, "e4m3"), (B.E5M2_BFP, "e5m2")])
-@pytest.mark.parametrize("n", [256, 4096])
+@pytest.mark.parametrize("n", [256, 4096, 32768, 65536])
 def test_fp8_storage_matches_oracle_rounding(dtype, fmt, n, rows_variant):
-    x = quant.round_fp8(synth.complex_gaussian(16, n, seed=n), fmt)
-    plan = B.bfpfft_plan_create(n, 16, dtype, B.FORWARD)
+    """FP8 storage against the oracle's rounding of the exact scaled values;
+    lines of 32768 / 65536 points run four-step (their outputs exchanged as
+    rounded FP8 pairs) or as two passes."""
+    batch = 16 if n <= 4096 else 3
+    x = quant.round_fp8(synth.complex_gaussian(batch, n, seed=n), fmt)
+    plan = B.bfpfft_plan_create(n, batch, dtype, B.FORWARD)
     in_exp, out_exp = B.bfpfft_plan_scale_exp(plan)
     assert in_exp == 0 and out_exp == (int(np.log2(n)) + 1) // 2
     got = run_fft(x, dtype, B.FORWARD)                   # stored = true * 2^-out_exp
