@@ -917,7 +917,7 @@ __device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS
 #pragma unroll
     for (int i = 0; i < N1; ++i) u[i] = v[b * N1 + i];
     Dft<N1>::run(u);
-    const uint32_t slot = h16row ? smem_base + uint32_t(n2) * 4u : smem_base + uint32_t(pad16(n2)) * sizeof(float2);
+    const uint32_t slot = h16row ? smem_base + uint32_t(n2) * 4u : smem_base + uint32_t(n2) * uint32_t(sizeof(float2));
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) {
       const float2 z = k1 == 0 ? u[0] : cmul(u[k1], __ldg(a.tw_4step + k1 * 4096 + n2));
@@ -928,11 +928,14 @@ __device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS
       }
     }
   }
-  // The row is complete when all 32 KB have landed (bounded wait).
+  // The row is complete when all of it has landed (bounded wait).  It sits
+  // unpadded at n2: each warp's sends then fill aligned 128- or 256-byte
+  // segments of the owner's buffer (padded slots measured 8-10 % slower),
+  // and the reads below are conflict-free without padding.
   const bool row_ok = mbar_wait_bounded(bar, phase, a.status);
 #pragma unroll
   for (int m = 0; m < P; ++m)
-    v[m] = h16row ? bits_half2(reinterpret_cast<const uint32_t*>(smem)[t + 256 * m]) : smem[pad16(t + 256 * m)];
+    v[m] = h16row ? bits_half2(reinterpret_cast<const uint32_t*>(smem)[t + 256 * m]) : smem[t + 256 * m];
   if (__syncthreads_or(!row_ok)) {
     pending = kOutXch ? 3 : 1;
     return false;
