@@ -850,28 +850,33 @@ __device__ __forceinline__ uint32_t fp8_pair_bits(float2 v) {
 
 // Step-3 send words: FP32 pairs; for FP16 storage the rounded half2; for FP8
 // storage two rounded FP8 pairs, those of consecutive k2 (the values are
-// rounded where they are computed, as the owner would round them).  kPad
-// words pad each segment of the owner's buffer so that its gather is
-// conflict-free.
+// rounded where they are computed, as the owner would round them).  In the
+// owner's buffer, segment k1 holds word w at w ^ (k1 * kSwz(N1)): a warp's
+// sends stay one aligned block (the XOR stays below 32) and the owner's
+// gather, which reads the same w of up to 16 segments at once, spreads over
+// distinct banks (16 lanes a wavefront for 8-byte words, 32 for 4-byte).
 template <class TS> struct FsSend {
   using Word = float2;
-  static constexpr int kPts = 1, kPad = 1;
+  static constexpr int kPts = 1;
+  __host__ __device__ static constexpr int swz(int n1) { return 16 / n1; }
 };
 template <> struct FsSend<__half2> {
   using Word = uint32_t;
-  static constexpr int kPts = 1, kPad = 2;
+  static constexpr int kPts = 1;
+  __host__ __device__ static constexpr int swz(int n1) { return 32 / n1; }
 };
 template <class F> struct FsSend<Fp8x2<F>> {
   using Word = uint32_t;
-  static constexpr int kPts = 2, kPad = 1;
+  static constexpr int kPts = 2;
+  __host__ __device__ static constexpr int swz(int n1) { return 32 / n1; }
 };
 // Shared memory of a four-step line: the row buffer, and for N1 >= 8 the
-// output buffer of N1 padded segments of S / kPts words, S = 4096 / N1.
+// output buffer of N1 segments of S / kPts words, S = 4096 / N1.
 template <class TS, int N1>
 __host__ __device__ constexpr size_t fourstep_smem_bytes() {
   using X = FsSend<TS>;
   return size_t(pad16(4096)) * sizeof(float2) +
-         (N1 >= 8 ? size_t(N1) * (4096 / N1 / X::kPts + X::kPad) * sizeof(typename X::Word) : 0);
+         (N1 >= 8 ? size_t(4096 / X::kPts) * sizeof(typename X::Word) : 0);
 }
 
 template <int N1, class TS, int MODE, bool SCALED, bool H16ROW = false>
@@ -886,7 +891,9 @@ __device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS
   constexpr bool kOutXch = N1 >= 8;
   using Word = typename FsSend<TS>::Word;
   constexpr int kPts = FsSend<TS>::kPts;                // points per send word
-  constexpr int kSeg = S / kPts + FsSend<TS>::kPad;     // words per padded segment of the owner's buffer
+  constexpr int kSeg = S / kPts;                        // words per segment of the owner's buffer
+  constexpr int kSwz = FsSend<TS>::swz(N1);
+  static_assert(!kOutXch || (kSwz * (N1 - 1) < 32 && kSwz * (N1 - 1) < kSeg), "swizzle within a block");
   // H16ROW with FP16 storage: the row arrives as FP16 words (one more FP16
   // storage point, half the exchange bytes); otherwise as FP32 pairs.
   constexpr bool h16row = H16ROW && std::is_same<TS, __half2>::value;
@@ -956,8 +963,9 @@ __device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS
     return true;
   } else {
     // The owner's buffer holds the values as [k1][k2 mod S] in segments of
-    // kSeg words, so a warp's sends are contiguous; the owner gathers output
-    // position j = (k2 mod S) N1 + k1 from segment k1, point j / N1.  FP8
+    // kSeg words (swizzled, see FsSend), so a warp's sends fill one aligned
+    // block; the owner gathers output position j = (k2 mod S) N1 + k1 from
+    // segment k1, point j / N1.  FP8
     // words hold the points of k2 and k2 + 1 (k2 even): for even m the even
     // thread of each lane pair sends its value and its odd partner's, for odd
     // m the odd thread does.
@@ -970,11 +978,11 @@ __device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS
         const uint32_t other = __shfl_xor_sync(0xffffffffu, own, 1);
         if ((t & 1) == (m & 1)) {
           const uint32_t w = t & 1 ? other | (own << 16) : own | (other << 16);
-          const uint32_t slot = out_base + uint32_t(c * kSeg + (k2 % S) / 2) * uint32_t(sizeof(Word));
+          const uint32_t slot = out_base + uint32_t(c * kSeg + (((k2 % S) / 2) ^ (kSwz * c))) * uint32_t(sizeof(Word));
           st_async_b32(mapa(slot, dst), w, mapa(bar_out_local, dst));
         }
       } else {
-        const uint32_t slot = out_base + uint32_t(c * kSeg + k2 % S) * uint32_t(sizeof(Word));
+        const uint32_t slot = out_base + uint32_t(c * kSeg + ((k2 % S) ^ (kSwz * c))) * uint32_t(sizeof(Word));
         if constexpr (sizeof(Word) == 4) {
           st_async_b32(mapa(slot, dst), half2_bits(v[m]), mapa(bar_out_local, dst));
         } else {
@@ -993,7 +1001,7 @@ __device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS
       if constexpr (kPts == 2) {
         auto bits = [&](int m) -> uint16_t {
           const int j = t + 256 * m, q = j / N1;
-          return uint16_t(ob[(j % N1) * kSeg + q / 2] >> (16 * (q & 1)));
+          return uint16_t(ob[(j % N1) * kSeg + ((q / 2) ^ (kSwz * (j % N1)))] >> (16 * (q & 1)));
         };
 #pragma unroll
         for (int m = 0; m < P; ++m)
@@ -1007,7 +1015,7 @@ __device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS
 #pragma unroll
         for (int m = 0; m < P; ++m) {
           const int j = t + 256 * m;
-          const Word w = ob[(j % N1) * kSeg + j / N1];
+          const Word w = ob[(j % N1) * kSeg + ((j / N1) ^ (kSwz * (j % N1)))];
           if constexpr (sizeof(Word) == 4) {
             __stcs(reinterpret_cast<unsigned int*>(out + c * 4096 + j), w);
           } else {
@@ -1017,12 +1025,12 @@ __device__ __forceinline__ bool fourstep_line(const RowArgs& a, const TS* in, TS
         if constexpr (sizeof(Word) == 4) {
           check_finite<Storage<TS>, P>(a.finite_flag, [&](int m) {
             const int j = t + 256 * m;
-            return bits_half2(ob[(j % N1) * kSeg + j / N1]);
+            return bits_half2(ob[(j % N1) * kSeg + ((j / N1) ^ (kSwz * (j % N1)))]);
           });
         } else {
           check_finite<Storage<TS>, P>(a.finite_flag, [&](int m) {
             const int j = t + 256 * m;
-            return ob[(j % N1) * kSeg + j / N1];
+            return ob[(j % N1) * kSeg + ((j / N1) ^ (kSwz * (j % N1)))];
           });
         }
       }
