@@ -757,8 +757,8 @@ def _bench_uneven(B, torch, dev, stream):
     sums = torch.empty(8, dtype=torch.float64, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     scale = None
-    for name, dtype in (("f32", B.F32), ("f16_bfp", B.F16_BFP), ("f16_bfp_tuned_fp16_exchange", B.F16_BFP),
-                        ("e4m3", B.E4M3_BFP), ("e5m2", B.E5M2_BFP)):
+    for name, dtype in (("f32", B.F32), ("f16_bfp", B.F16_BFP), ("f16_bfp_persistent_kernel", B.F16_BFP),
+                        ("f16_bfp_tuned_fp16_exchange", B.F16_BFP), ("e4m3", B.E4M3_BFP), ("e5m2", B.E5M2_BFP)):
         if dtype == B.F32:
             xin = x32
         elif dtype == B.F16_BFP:
@@ -770,8 +770,11 @@ def _bench_uneven(B, torch, dev, stream):
         plan = B.bfpfft_plan_create_many(lengths, offsets, dtype, B.FORWARD)
         # The tuner's pick among cluster counts, two-pass long lines, one launch
         # per length and (FP16 exchanges allowed) the FP16 row exchange of
-        # four-step lines.
-        code, _ = B.bfpfft_plan_tune(plan, allow_fp16_exchange=name == "f16_bfp_tuned_fp16_exchange")
+        # four-step lines; one FP16 plan keeps the untuned persistent kernel.
+        if name == "f16_bfp_persistent_kernel":
+            code = 0
+        else:
+            code, _ = B.bfpfft_plan_tune(plan, allow_fp16_exchange=name == "f16_bfp_tuned_fp16_exchange")
         for _ in range(3):
             B.bfpfft_exec_graph(plan, xin, yout, stream)
         ts = []
@@ -784,8 +787,10 @@ def _bench_uneven(B, torch, dev, stream):
         t = statistics.median(ts)
         entry = {"ms_median": round(t, 4), "gflops": round(flops / (t * 1e-3) / 1e9, 1),
                  "alg_gbs": round(total * 2 * xin.element_size() * xin.shape[-1] / (t * 1e-3) / 1e9, 1)}
-        entry["tuned"] = {"clusters": code & 0xffff, "two_pass_long_lines": bool((code >> 16) & 1),
-                          "fp16_row_exchange": bool((code >> 17) & 1), "one_launch_per_length": bool((code >> 18) & 1)}
+        if code:
+            entry["tuned"] = {"clusters": code & 0xffff, "two_pass_long_lines": bool((code >> 16) & 1),
+                              "fp16_row_exchange": bool((code >> 17) & 1),
+                              "one_launch_per_length": bool((code >> 18) & 1)}
         if dtype == B.F16_BFP:
             B.bfp_sqnr_sums(torch.view_as_complex(y32), B.F32, yout, B.F16_BFP, total, sums, ws, ws_bytes, stream)
             entry["sqnr_vs_f32_db"] = round(B.sqnr_from_sums(sums[:5].cpu().tolist())["aligned_db"], 2)
