@@ -546,7 +546,9 @@ int sar_autofocus_grad_arith(const void* rc, int rc_dtype, const float* phi, con
  *   PSLR = 20 log10(max sidelobe / peak), ISLR = 10 log10(sidelobe / mainlobe
  *   energy), 3 dB width in cells (linear interpolation of the half-power
  *   crossings); SNR = 10 log10(peak^2 / mean |I|^2 over every cell at least
- *   `guard` cells from every target in both axes).
+ *   `guard` cells from every target in both axes; each |I|^2 is formed in
+ *   FP32 -- exact products of FP16 pixels -- and summed in FP64).  Targets
+ *   go through in chunks of 16, with their FP64 intermediates in `workspace`.
  *   img       [n_az][n_rg], dtype BFPFFT_F32 or BFPFFT_F16_*, n_az, n_rg >= 64
  *   targets   device int32 [k][2] = (eta, r)
  *   out       device double [k][12] = PSLR range, PSLR azimuth, ISLR range,
